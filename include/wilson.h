@@ -1,0 +1,212 @@
+/*
+ * wilson.h -- C ABI of the GB300 (sm_103a) Wilson-fermion multi-mass solver.
+ *
+ * Method: Alexandru, Pelissier, Gamari & Lee, "Multi-mass solvers for lattice
+ * QCD on GPUs" (arXiv:1103.5103).  The library solves M(m_i) x_i = b for
+ * several bare masses m_i with the Wilson-Dirac operator
+ *     M_p(m) = (m + 4) - D/2                                 (Eq. 3)
+ *     (D psi)_n = sum_mu [ U_mu(n) psi_{n+mu} (1 - gamma_mu)
+ *                        + U_mu(n-mu)^dag psi_{n-mu} (1 + gamma_mu) ]  (Eq. 4)
+ * where psi_n is a 3x4 matrix (colour rows, spin columns) and the spin matrix
+ * multiplies from the right, with the gamma matrices of Section 2.  The
+ * library works in the kappa normalisation
+ *     M_k = 1 - kappa D,  kappa = 1 / (2 m0 + 8),   M_p = (m0 + 4) M_k,
+ * so a solution x of M_k x = b is (m0 + 4) times the paper's psi; relative
+ * residuals are identical in both normalisations.  Hops across the time
+ * boundary carry -1 when the lattice is antiperiodic in time; space is
+ * periodic.
+ *
+ * Conventions for every call
+ *  - Returns an int status (WL_OK = 0); wl_last_error() gives a thread-local
+ *    message for the last failing call on this thread.  No C++ exception
+ *    crosses this interface.
+ *  - "stream" is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *    asynchronous on that stream unless stated otherwise.
+ *  - Field arrays are caller-owned DEVICE pointers; the library never frees
+ *    them.  Handles (wl_lattice, wl_gauge) are library-owned: the caller
+ *    destroys them.  A wl_gauge also owns the solver workspace, allocated on
+ *    first use with cudaMalloc and released by wl_gauge_destroy.
+ *  - Canonical external layout (complex128, interleaved re/im):
+ *      site index  n = x + X*(y + Y*(z + Z*t))
+ *      spinor      [n][spin 4][colour 3]                (12 complex per site)
+ *      links       [mu 4][n][row 3][col 3], mu = 0..3 <-> x, y, z, t
+ *                  (the paper's gamma_1..gamma_4 directions)
+ *    Sources and solutions are full-lattice vectors; the even/odd split is
+ *    internal.  Site parity = (x+y+z+t) mod 2; site 0 is even.
+ *  - Precisions: WL_F64, WL_F32 and WL_F16 (FP16 storage with one FP32 norm
+ *    per site, arithmetic in FP32).  Links are stored as their first two rows
+ *    (12 reals) and the third row is rebuilt as conj(row0 x row1), which is
+ *    exact for SU(3) links.
+ */
+#ifndef WILSON_H
+#define WILSON_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status codes */
+#define WL_OK            0
+#define WL_ERR_ARG       1  /* bad dims, odd extent, NULL pointer, duplicate masses, bad enum */
+#define WL_ERR_CUDA      2  /* a CUDA runtime call failed                                    */
+#define WL_ERR_OOM       3  /* device allocation failed                                      */
+#define WL_ERR_NOCONV    4  /* iteration cap reached; outputs hold the last iterate           */
+#define WL_ERR_BREAKDOWN 5  /* Krylov breakdown that restarts could not cure                  */
+#define WL_ERR_TIMEOUT   6  /* a bounded device wait ran out                                  */
+#define WL_ERR_CHECKED   7  /* a bounds check of a checked build recorded a violation         */
+
+/* ------------------------------------------------------------- precisions */
+#define WL_F64 1
+#define WL_F32 2
+#define WL_F16 4
+
+/* ----------------------------------------------------------------- parity */
+#define WL_EVEN 0
+#define WL_ODD  1
+
+/* ----------------------------------------------------- dslash operator ids */
+#define WL_OP_HOP   0  /* out = D in                        (full lattice)     */
+#define WL_OP_M     1  /* out = in - kappa D in             (full lattice)     */
+#define WL_OP_MPREC 2  /* out_e = in_e - kappa^2 D_eo D_oe in_e, out_o = 0     */
+
+/* ------------------------------------------------------ solver parameters */
+#define WL_GUESS_ZERO 0  /* zero initial guess for every mass                     */
+#define WL_GUESS_POLY 1  /* Lagrange extrapolation through all previous masses    */
+
+#define WL_MODE_HOST  0  /* one host round trip per iteration                      */
+#define WL_MODE_GRAPH 1  /* iterations captured in a CUDA graph, scalars on device */
+
+typedef struct wl_lattice wl_lattice;
+typedef struct wl_gauge wl_gauge;
+
+typedef struct {
+    double tol;          /* target true relative residual ||b - M x|| / ||b||        */
+    int    max_iter;     /* cap on Krylov iterations per mass (all restarts)          */
+    int    inner_prec;   /* WL_F64, WL_F32 or WL_F16: precision of the Krylov loop    */
+    double inner_tol;    /* defect-correction inner relative tolerance; 0 = default   */
+    int    max_restarts; /* cap on outer FP64 restarts per mass                        */
+    int    guess;        /* WL_GUESS_*  (multimass_solve)                              */
+    int    mode;         /* WL_MODE_*                                                   */
+    int    rhs_block;    /* right-hand sides per thread in batched hops; 0 = autotune  */
+    int    graph_iters;  /* iterations per captured graph (WL_MODE_GRAPH)               */
+    int    eo;           /* 1: even-odd preconditioned solve (bicgstab_solve)           */
+} wl_solver_params;
+
+typedef struct {
+    double mass;         /* bare mass m0 of this solve                                 */
+    int    status;       /* WL_OK, WL_ERR_NOCONV or WL_ERR_BREAKDOWN                    */
+    int    iterations;   /* Krylov iterations (sum over restarts)                       */
+    int    matvecs;      /* applications of the solved operator                         */
+    int    restarts;     /* outer FP64 restarts (defect-correction steps)               */
+    double true_relres;  /* FP64 ||b - M_k x|| / ||b|| on the full lattice at exit      */
+    double seconds;      /* wall time of this mass's solve (host clock, stream synced)  */
+} wl_solver_stats;
+
+/* Fill *p with defaults: tol 1e-10, max_iter 100000, inner WL_F32,
+ * inner_tol 0 (1e-5 for FP32, 3e-3 for FP16, tol for FP64), max_restarts 100,
+ * WL_GUESS_POLY, WL_MODE_GRAPH, rhs_block 0, graph_iters 8, eo 1. */
+int wl_params_default(wl_solver_params *p);
+
+/* Thread-local message describing the last failing call on this thread. */
+const char *wl_last_error(void);
+
+/* --------------------------------------------------------------- geometry */
+
+/* Create a lattice of extents dims = {X, Y, Z, T}.  Every extent must be even
+ * and >= 2 (the even/odd split of Section 6.2.3 needs it) and the volume
+ * below 2^31.  antiperiodic_t: 1 gives -1 on hops across the time boundary.
+ * Host-only; no device work. */
+int wl_lattice_create(const int dims[4], int antiperiodic_t, wl_lattice **out);
+int wl_lattice_destroy(wl_lattice *lat);
+
+/* Bytes of one internal half-lattice (one parity) spinor of precision prec.
+ * Internal spinors are site-blocked structure-of-arrays per parity
+ * (Section 4, Eq. 7, re-laid for 128-bit loads). */
+int wl_spinor_bytes(const wl_lattice *lat, int prec, size_t *bytes);
+
+/* Convert one parity of a canonical full-lattice complex128 spinor (device)
+ * to the internal format of precision prec (device, wl_spinor_bytes bytes),
+ * and back.  Export writes only the sites of the given parity. */
+int wl_spinor_import(const wl_lattice *lat, const void *canon_c128, void *internal, int prec,
+                     int parity, void *stream);
+int wl_spinor_export(const wl_lattice *lat, const void *internal, void *canon_c128, int prec,
+                     int parity, void *stream);
+
+/* Pack canonical complex128 links (device, [4][V][3][3]) into the internal
+ * 12-real per-parity layout (Section 4, Eq. 8, compressed to two rows) for
+ * every precision set in prec_mask (WL_F64 | WL_F32 | WL_F16).  The links
+ * must be SU(3) to rounding.  The gauge handle keeps a reference to lat,
+ * which must outlive it.  Synchronises the stream before returning. */
+int wl_gauge_create(wl_lattice *lat, const void *U_canon_c128, unsigned prec_mask, void *stream,
+                    wl_gauge **out);
+int wl_gauge_destroy(wl_gauge *g);
+
+/* ---------------------------------------------------------------- dslash */
+
+/* One parity hop on internal spinors (Section 2, Eq. 4; Algorithm 1 without
+ * the diagonal term):  out = x + coef * D_{p,1-p} in,  or out = coef * D in
+ * when x is NULL.  out_parity p selects D_eo (p = WL_EVEN) or D_oe.
+ * dagger = 1 applies D^dag = gamma5 D gamma5.  in, x, out are internal
+ * spinors of precision prec (in has the other parity); out must not alias
+ * in.  The gauge handle must hold links of precision prec. */
+int wilson_hop(wl_gauge *g, const void *in, void *out, const void *x, double coef, int prec,
+               int out_parity, int dagger, void *stream);
+
+/* Canonical full-lattice operator application (complex128 in and out):
+ *   WL_OP_HOP   out = D in
+ *   WL_OP_M     out = in - kappa D in                        (Eq. 3, kappa form)
+ *   WL_OP_MPREC out_e = in_e - kappa^2 D_eo D_oe in_e, out_o = 0   (Eq. eo4)
+ * computed in precision prec through the internal layout.  Scratch comes
+ * from the gauge handle's workspace.  in and out must not alias. */
+int wilson_dslash(wl_gauge *g, const void *in, void *out, double kappa, int prec, int op,
+                  void *stream);
+/* The adjoint of the same operator: D^dag = gamma5 D gamma5. */
+int wilson_dslash_dag(wl_gauge *g, const void *in, void *out, double kappa, int prec, int op,
+                      void *stream);
+
+/* --------------------------------------------------------------- solvers */
+
+/* Solve M_k(m0) x = b (Section 6) with BiCGstab.  b, x: canonical
+ * full-lattice complex128 device vectors; x holds the initial guess on entry
+ * and the solution on exit.  With p->eo = 1 the even-odd preconditioned
+ * system M_prec x_e = b_e + kappa D_eo b_o is solved and x_o is rebuilt
+ * (Section 6.2.3); with p->inner_prec below FP64 each outer step recomputes
+ * the FP64 residual and runs a reduced-precision inner BiCGstab
+ * (defect correction, Section 6.2.4).  Stops when the FP64 preconditioned
+ * residual is below tol * ||b||; stats->true_relres is the FP64 full-lattice
+ * residual of the returned x.  Synchronises the stream.
+ * Returns WL_OK, WL_ERR_NOCONV or WL_ERR_BREAKDOWN (x = best iterate). */
+int bicgstab_solve(wl_gauge *g, const void *b, void *x, double m0, const wl_solver_params *p,
+                   wl_solver_stats *stats, void *stream);
+
+/* Multi-shift BiCGstab-M baseline (Section 6.1): one Krylov space built on
+ * the full-lattice unshifted system M_p(m_s), m_s = min m0[i], shifts
+ * sigma_i = m0[i] - m_s, converged shifts frozen, loop ends when the
+ * unshifted residual is below tol * ||b||.  Always FP64, no even-odd
+ * preconditioning (the paper: multi-shift cannot use it).  x[i] receives the
+ * kappa-form solution (m0[i] + 4) psi_i as a canonical complex128 vector.
+ * A shift whose FP64 true residual is still above tol afterwards is polished
+ * by a single-mass FP64 BiCGstab from x[i]; its extra iterations are counted
+ * in stats[i].restarts.  Masses must be distinct.  Synchronises the stream. */
+int bicgstab_m_solve(wl_gauge *g, const void *b, void *const *x, const double *m0, int n_mass,
+                     const wl_solver_params *p, wl_solver_stats *stats, void *stream);
+
+/* The paper's single-mass multi-mass scheme (Sections 6.2 and 7): masses
+ * sorted heaviest first; each solved with even-odd preconditioned,
+ * mixed-precision BiCGstab; initial guess for mass k by Lagrange
+ * extrapolation through all k-1 previous solutions (Eq. Poly, extrapolating
+ * the paper-normalised psi = x / (m0 + 4)).  b[r] (r < n_rhs) are canonical
+ * sources; x[r * n_mass + i] receives the solution for source r and mass
+ * m0[i]; stats[r * n_mass + i] its statistics.  All right-hand sides of one
+ * mass are solved together by batched kernels.  Masses must be distinct.
+ * Synchronises the stream. */
+int multimass_solve(wl_gauge *g, const void *const *b, void *const *x, int n_rhs, const double *m0,
+                    int n_mass, const wl_solver_params *p, wl_solver_stats *stats, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WILSON_H */

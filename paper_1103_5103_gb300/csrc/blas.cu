@@ -1,0 +1,394 @@
+// Fused vector kernels of the solvers (Section 5): each BiCGstab update is one
+// pass over the site-blocked vectors, with its inner products reduced in the
+// same pass (per-site FP32/FP64 partials, FP64 across sites and blocks) and
+// the scalar recurrences evaluated on the device by the last block.
+//
+// Grid convention of every kernel here: blockIdx.x = site_block * nrhs + rhs,
+// kBlock threads, one site per thread.
+#include "internal.h"
+
+namespace wl {
+
+template <int P>
+using RT = typename PrecTraits<P>::R;
+
+struct SiteIdx {
+    int r, sb, nsb, i;
+};
+
+__device__ __forceinline__ SiteIdx site_idx(int nrhs)
+{
+    SiteIdx s;
+    s.r = blockIdx.x % nrhs;
+    s.sb = blockIdx.x / nrhs;
+    s.nsb = gridDim.x / nrhs;
+    s.i = s.sb * blockDim.x + threadIdx.x;
+    return s;
+}
+
+template <int P>
+__device__ __forceinline__ void ld(const Vec &v, int r, int stride, int i, cx<RT<P>> (&o)[12])
+{
+    SpinorIO<P>::load(v.rhs(r), stride, i, o);
+}
+
+template <int P>
+__device__ __forceinline__ void st(const Vec &v, int r, int stride, int i, const cx<RT<P>> (&o)[12])
+{
+    SpinorIO<P>::store(v.rhs(r), stride, i, o);
+}
+
+static inline int grid_of(const Geom &g, int nrhs) { return site_blocks(g) * nrhs; }
+
+// ------------------------------------------------------------ s = r - alpha v
+
+template <int P>
+__global__ void __launch_bounds__(kBlock) k_s_update(Geom g, Vec r, Vec v, Vec s, const BiState *state)
+{
+    const SiteIdx q = site_idx(r.nrhs);
+    if (__ldcg(&state[q.r].done) || q.i >= g.Vh) return;
+    using R = RT<P>;
+    const cx<R> al = {(R)__ldcg(&state[q.r].alpha_re), (R)__ldcg(&state[q.r].alpha_im)};
+    cx<R> a[12], b[12];
+    ld<P>(r, q.r, g.stride, q.i, a);
+    ld<P>(v, q.r, g.stride, q.i, b);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) a[k] = a[k] - al * b[k];
+    st<P>(s, q.r, g.stride, q.i, a);
+}
+
+int blas_s_update(const Geom &g, const Vec &r, const Vec &v, const Vec &s_out, BiState *state, cudaStream_t s)
+{
+    switch (r.prec) {
+    case WL_F64: k_s_update<WL_F64><<<grid_of(g, r.nrhs), kBlock, 0, s>>>(g, r, v, s_out, state); break;
+    case WL_F32: k_s_update<WL_F32><<<grid_of(g, r.nrhs), kBlock, 0, s>>>(g, r, v, s_out, state); break;
+    case WL_F16: k_s_update<WL_F16><<<grid_of(g, r.nrhs), kBlock, 0, s>>>(g, r, v, s_out, state); break;
+    }
+    WL_CUDA_TRY(cudaGetLastError());
+    return WL_OK;
+}
+
+// ------------------------------- x += alpha p + omega s;  r = s - omega t
+// reductions: <rhat, r> and ||r||^2 -> beta, rho, convergence
+
+template <int P, int PX>
+__global__ void __launch_bounds__(kBlock) k_xr_update(Geom g, Vec x, Vec p, Vec sv, Vec t, Vec r, Vec rhat,
+                                                      BiState *state, double *partials)
+{
+    const SiteIdx q = site_idx(r.nrhs);
+    BiState &S = state[q.r];
+    if (__ldcg(&S.done)) return;
+    using R = RT<P>;
+    using RX = RT<PX>;
+    double red[3] = {0.0, 0.0, 0.0};
+    if (q.i < g.Vh) {
+        const double are = __ldcg(&S.alpha_re), aim = __ldcg(&S.alpha_im);
+        const double ore = __ldcg(&S.omega_re), oim = __ldcg(&S.omega_im);
+        cx<R> pv[12], sv_[12], tv[12];
+        ld<P>(p, q.r, g.stride, q.i, pv);
+        ld<P>(sv, q.r, g.stride, q.i, sv_);
+        ld<P>(t, q.r, g.stride, q.i, tv);
+        {
+            cx<RX> xv[12];
+            SpinorIO<PX>::load(x.rhs(q.r), g.stride, q.i, xv);
+            const cx<RX> al = {(RX)are, (RX)aim}, om = {(RX)ore, (RX)oim};
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+                cx<RX> pk = {(RX)pv[k].re, (RX)pv[k].im}, sk = {(RX)sv_[k].re, (RX)sv_[k].im};
+                xv[k] = cmad(al, pk, cmad(om, sk, xv[k]));
+            }
+            SpinorIO<PX>::store(x.rhs(q.r), g.stride, q.i, xv);
+        }
+        const cx<R> om = {(R)ore, (R)oim};
+        cx<R> rv[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) rv[k] = sv_[k] - om * tv[k];
+        SpinorIO<P>::roundtrip(rv);
+        st<P>(r, q.r, g.stride, q.i, rv);
+        cx<R> rh[12];
+        ld<P>(rhat, q.r, g.stride, q.i, rh);
+        cx<R> d = {R(0), R(0)};
+        R n = R(0);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            d = conjmad(rh[k], rv[k], d);
+            n = fma(rv[k].re, rv[k].re, fma(rv[k].im, rv[k].im, n));
+        }
+        red[0] = (double)d.re;
+        red[1] = (double)d.im;
+        red[2] = (double)n;
+    }
+    double tot[3];
+    if (grid_sum<3>(red, partials + (size_t)q.r * q.nsb * kRedNV, &S.ticket[2], q.sb, q.nsb, tot) &&
+        threadIdx.x == 0) {
+        const double r1re = tot[0], r1im = tot[1], rr = tot[2];
+        S.iters += 1;
+        S.rr = rr;
+        const double ore = S.omega_re, oim = S.omega_im;
+        if (!isfinite(rr) || !isfinite(r1re) || !isfinite(r1im)) {
+            S.breakdown = 1;
+            S.done = 1;
+        } else if (rr <= S.target2) {
+            S.done = 1;
+        } else {
+            const double rho2 = S.rho_re * S.rho_re + S.rho_im * S.rho_im;
+            const double om2 = ore * ore + oim * oim;
+            if (!(rho2 > 0.0) || !(om2 > 0.0) || !(r1re * r1re + r1im * r1im > 0.0)) {
+                S.breakdown = 1;
+                S.done = 1;
+            } else {
+                // beta = (rho1 / rho) * (alpha / omega)
+                const double qre = (r1re * S.rho_re + r1im * S.rho_im) / rho2;
+                const double qim = (r1im * S.rho_re - r1re * S.rho_im) / rho2;
+                const double are = S.alpha_re, aim = S.alpha_im;
+                const double wre = (are * ore + aim * oim) / om2;
+                const double wim = (aim * ore - are * oim) / om2;
+                S.beta_re = qre * wre - qim * wim;
+                S.beta_im = qre * wim + qim * wre;
+                S.rho_re = r1re;
+                S.rho_im = r1im;
+            }
+        }
+    }
+}
+
+int blas_xr_update(const Geom &g, const Vec &x, const Vec &p, const Vec &sv, const Vec &t, const Vec &r,
+                   const Vec &rhat, BiState *state, double *partials, cudaStream_t s)
+{
+    const int gr = grid_of(g, r.nrhs);
+    if (r.prec == WL_F64 && x.prec == WL_F64)
+        k_xr_update<WL_F64, WL_F64><<<gr, kBlock, 0, s>>>(g, x, p, sv, t, r, rhat, state, partials);
+    else if (r.prec == WL_F32 && x.prec == WL_F32)
+        k_xr_update<WL_F32, WL_F32><<<gr, kBlock, 0, s>>>(g, x, p, sv, t, r, rhat, state, partials);
+    else if (r.prec == WL_F16 && x.prec == WL_F32)
+        k_xr_update<WL_F16, WL_F32><<<gr, kBlock, 0, s>>>(g, x, p, sv, t, r, rhat, state, partials);
+    else {
+        set_error("blas_xr_update: unsupported precision pair");
+        return WL_ERR_ARG;
+    }
+    WL_CUDA_TRY(cudaGetLastError());
+    return WL_OK;
+}
+
+// ------------------------------------------------ p = r + beta (p - omega v)
+
+template <int P>
+__global__ void __launch_bounds__(kBlock) k_p_update(Geom g, Vec r, Vec p, Vec v, const BiState *state)
+{
+    const SiteIdx q = site_idx(r.nrhs);
+    if (__ldcg(&state[q.r].done) || q.i >= g.Vh) return;
+    using R = RT<P>;
+    const cx<R> be = {(R)__ldcg(&state[q.r].beta_re), (R)__ldcg(&state[q.r].beta_im)};
+    const cx<R> om = {(R)__ldcg(&state[q.r].omega_re), (R)__ldcg(&state[q.r].omega_im)};
+    cx<R> rv[12], pv[12], vv[12];
+    ld<P>(r, q.r, g.stride, q.i, rv);
+    ld<P>(p, q.r, g.stride, q.i, pv);
+    ld<P>(v, q.r, g.stride, q.i, vv);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) pv[k] = rv[k] + be * (pv[k] - om * vv[k]);
+    st<P>(p, q.r, g.stride, q.i, pv);
+}
+
+int blas_p_update(const Geom &g, const Vec &r, const Vec &p, const Vec &v, BiState *state, cudaStream_t s)
+{
+    switch (r.prec) {
+    case WL_F64: k_p_update<WL_F64><<<grid_of(g, r.nrhs), kBlock, 0, s>>>(g, r, p, v, state); break;
+    case WL_F32: k_p_update<WL_F32><<<grid_of(g, r.nrhs), kBlock, 0, s>>>(g, r, p, v, state); break;
+    case WL_F16: k_p_update<WL_F16><<<grid_of(g, r.nrhs), kBlock, 0, s>>>(g, r, p, v, state); break;
+    }
+    WL_CUDA_TRY(cudaGetLastError());
+    return WL_OK;
+}
+
+// ------------------------------------------------------------ (re)start
+// r = convert(r64); rhat = r; p = r; x = 0; rho = ||r||^2; target2 = delta2 * rho.
+// rhs with active[r] == 0 are marked done and left untouched.
+
+template <int P, int PX>
+__global__ void __launch_bounds__(kBlock) k_restart(Geom g, Vec r64, Vec r, Vec rhat, Vec p, Vec x, BiState *state,
+                                                    double *partials, const int *active, const double *delta2)
+{
+    const SiteIdx q = site_idx(r.nrhs);
+    BiState &S = state[q.r];
+    if (!active[q.r]) {
+        if (q.sb == 0 && threadIdx.x == 0) S.done = 1;
+        return;
+    }
+    double red[1] = {0.0};
+    if (q.i < g.Vh) {
+        using R = RT<P>;
+        cx<double> a[12];
+        SpinorIO<WL_F64>::load(r64.rhs(q.r), g.stride, q.i, a);
+        cx<R> v[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) v[k] = {(R)a[k].re, (R)a[k].im};
+        SpinorIO<P>::roundtrip(v);
+        st<P>(r, q.r, g.stride, q.i, v);
+        st<P>(rhat, q.r, g.stride, q.i, v);
+        st<P>(p, q.r, g.stride, q.i, v);
+        cx<RT<PX>> z[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) z[k] = {RT<PX>(0), RT<PX>(0)};
+        SpinorIO<PX>::store(x.rhs(q.r), g.stride, q.i, z);
+        R n = R(0);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) n = fma(v[k].re, v[k].re, fma(v[k].im, v[k].im, n));
+        red[0] = (double)n;
+    }
+    double tot[1];
+    if (grid_sum<1>(red, partials + (size_t)q.r * q.nsb * kRedNV, &S.ticket[3], q.sb, q.nsb, tot) &&
+        threadIdx.x == 0) {
+        S.rho_re = tot[0];
+        S.rho_im = 0.0;
+        S.rr = tot[0];
+        S.target2 = delta2[q.r] * tot[0];
+        S.alpha_re = S.omega_re = S.beta_re = 0.0;
+        S.alpha_im = S.omega_im = S.beta_im = 0.0;
+        S.iters = 0;
+        S.breakdown = 0;
+        S.done = (tot[0] > 0.0 && isfinite(tot[0])) ? 0 : 1;
+    }
+}
+
+int blas_restart(const Geom &g, const Vec &r64, const Vec &r, const Vec &rhat, const Vec &p, const Vec &x,
+                 BiState *state, double *partials, const int *active, const double *delta2, cudaStream_t s)
+{
+    const int gr = grid_of(g, r.nrhs);
+    if (r.prec == WL_F64 && x.prec == WL_F64)
+        k_restart<WL_F64, WL_F64><<<gr, kBlock, 0, s>>>(g, r64, r, rhat, p, x, state, partials, active, delta2);
+    else if (r.prec == WL_F32 && x.prec == WL_F32)
+        k_restart<WL_F32, WL_F32><<<gr, kBlock, 0, s>>>(g, r64, r, rhat, p, x, state, partials, active, delta2);
+    else if (r.prec == WL_F16 && x.prec == WL_F32)
+        k_restart<WL_F16, WL_F32><<<gr, kBlock, 0, s>>>(g, r64, r, rhat, p, x, state, partials, active, delta2);
+    else {
+        set_error("blas_restart: unsupported precision pair");
+        return WL_ERR_ARG;
+    }
+    WL_CUDA_TRY(cudaGetLastError());
+    return WL_OK;
+}
+
+// ------------------------------------------- x64 += e  (rhs with active != 0)
+
+template <int PX>
+__global__ void __launch_bounds__(kBlock) k_accum(Geom g, Vec e, Vec x64, const int *active)
+{
+    const SiteIdx q = site_idx(x64.nrhs);
+    if (!active[q.r] || q.i >= g.Vh) return;
+    cx<RT<PX>> a[12];
+    cx<double> b[12];
+    SpinorIO<PX>::load(e.rhs(q.r), g.stride, q.i, a);
+    SpinorIO<WL_F64>::load(x64.rhs(q.r), g.stride, q.i, b);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) b[k] = {b[k].re + (double)a[k].re, b[k].im + (double)a[k].im};
+    SpinorIO<WL_F64>::store(x64.rhs(q.r), g.stride, q.i, b);
+}
+
+int blas_accum(const Geom &g, const Vec &e, const Vec &x64, const int *active, cudaStream_t s)
+{
+    const int gr = grid_of(g, x64.nrhs);
+    if (e.prec == WL_F64) k_accum<WL_F64><<<gr, kBlock, 0, s>>>(g, e, x64, active);
+    else k_accum<WL_F32><<<gr, kBlock, 0, s>>>(g, e, x64, active);
+    WL_CUDA_TRY(cudaGetLastError());
+    return WL_OK;
+}
+
+// ------------------------------------------------------ squared norm (FP64)
+// out[r] = ||a_r||^2; uses tickets[r].
+
+template <int P>
+__global__ void __launch_bounds__(kBlock) k_norm2(Geom g, Vec a, double *out, double *partials, unsigned *tickets)
+{
+    const SiteIdx q = site_idx(a.nrhs);
+    double red[1] = {0.0};
+    if (q.i < g.Vh) {
+        cx<RT<P>> v[12];
+        ld<P>(a, q.r, g.stride, q.i, v);
+        double n = 0.0;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) n += (double)v[k].re * v[k].re + (double)v[k].im * v[k].im;
+        red[0] = n;
+    }
+    double tot[1];
+    if (grid_sum<1>(red, partials + (size_t)q.r * q.nsb * kRedNV, &tickets[q.r], q.sb, q.nsb, tot) &&
+        threadIdx.x == 0)
+        out[q.r] = tot[0];
+}
+
+int blas_norm2(const Geom &g, const Vec &a, double *out_dev, double *partials, unsigned *tickets, cudaStream_t s)
+{
+    const int gr = grid_of(g, a.nrhs);
+    switch (a.prec) {
+    case WL_F64: k_norm2<WL_F64><<<gr, kBlock, 0, s>>>(g, a, out_dev, partials, tickets); break;
+    case WL_F32: k_norm2<WL_F32><<<gr, kBlock, 0, s>>>(g, a, out_dev, partials, tickets); break;
+    case WL_F16: k_norm2<WL_F16><<<gr, kBlock, 0, s>>>(g, a, out_dev, partials, tickets); break;
+    }
+    WL_CUDA_TRY(cudaGetLastError());
+    return WL_OK;
+}
+
+// ------------------------------------- out = sum_j c_j in_j (FP64, k <= 16)
+// coefficients per rhs: c[r * k + j] (complex, re/im arrays on the device).
+
+struct LinIn {
+    const void *p[16];
+};
+
+__global__ void __launch_bounds__(kBlock) k_lincomb(Geom g, LinIn in, int k, size_t rhs_bytes, int nrhs,
+                                                    const double *cre, const double *cim, Vec out)
+{
+    const SiteIdx q = site_idx(nrhs);
+    if (q.i >= g.Vh) return;
+    cx<double> acc[12];
+#pragma unroll
+    for (int c = 0; c < 12; ++c) acc[c] = {0.0, 0.0};
+    for (int j = 0; j < k; ++j) {
+        const cx<double> w = {cre[q.r * k + j], cim[q.r * k + j]};
+        cx<double> v[12];
+        SpinorIO<WL_F64>::load(static_cast<const char *>(in.p[j]) + (size_t)q.r * rhs_bytes, g.stride, q.i, v);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) acc[c] = cmad(w, v[c], acc[c]);
+    }
+    SpinorIO<WL_F64>::store(out.rhs(q.r), g.stride, q.i, acc);
+}
+
+int blas_lincomb(const Geom &g, const double *cre_dev, const double *cim_dev, const Vec *const *in, int k,
+                 const Vec &out, cudaStream_t s)
+{
+    if (k < 1 || k > 16) { set_error("blas_lincomb: 1..16 inputs"); return WL_ERR_ARG; }
+    LinIn li;
+    for (int j = 0; j < k; ++j) li.p[j] = in[j]->ptr;
+    k_lincomb<<<grid_of(g, out.nrhs), kBlock, 0, s>>>(g, li, k, out.rhs_bytes, out.nrhs, cre_dev, cim_dev, out);
+    WL_CUDA_TRY(cudaGetLastError());
+    return WL_OK;
+}
+
+// ------------------------------------------------------------- conversion
+
+template <int PI, int PO>
+__global__ void __launch_bounds__(kBlock) k_convert(Geom g, Vec in, Vec out)
+{
+    const SiteIdx q = site_idx(out.nrhs);
+    if (q.i >= g.Vh) return;
+    cx<RT<PI>> a[12];
+    cx<RT<PO>> b[12];
+    SpinorIO<PI>::load(in.rhs(q.r), g.stride, q.i, a);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) b[k] = {(RT<PO>)a[k].re, (RT<PO>)a[k].im};
+    SpinorIO<PO>::store(out.rhs(q.r), g.stride, q.i, b);
+}
+
+int blas_convert(const Geom &g, const Vec &in, const Vec &out, cudaStream_t s)
+{
+    const int gr = grid_of(g, out.nrhs);
+#define WL_CONV(A, B) \
+    if (in.prec == A && out.prec == B) { k_convert<A, B><<<gr, kBlock, 0, s>>>(g, in, out); WL_CUDA_TRY(cudaGetLastError()); return WL_OK; }
+    WL_CONV(WL_F64, WL_F64) WL_CONV(WL_F64, WL_F32) WL_CONV(WL_F64, WL_F16)
+    WL_CONV(WL_F32, WL_F64) WL_CONV(WL_F32, WL_F32) WL_CONV(WL_F32, WL_F16)
+    WL_CONV(WL_F16, WL_F64) WL_CONV(WL_F16, WL_F32) WL_CONV(WL_F16, WL_F16)
+#undef WL_CONV
+    set_error("blas_convert: bad precision");
+    return WL_ERR_ARG;
+}
+
+}  // namespace wl

@@ -1,0 +1,399 @@
+// Internal types and device helpers shared by the CUDA translation units of
+// libwilson.  Not part of the C ABI.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "wilson.h"
+
+namespace wl {
+
+// ------------------------------------------------------------------ errors
+
+void set_error(const std::string &msg);
+
+#define WL_CUDA_TRY(expr)                                                                   \
+    do {                                                                                    \
+        cudaError_t _e = (expr);                                                            \
+        if (_e != cudaSuccess) {                                                            \
+            ::wl::set_error(std::string(#expr) + ": " + cudaGetErrorString(_e));            \
+            return _e == cudaErrorMemoryAllocation ? WL_ERR_OOM : WL_ERR_CUDA;              \
+        }                                                                                   \
+    } while (0)
+
+#define WL_TRY(expr)                  \
+    do {                              \
+        int _s = (expr);              \
+        if (_s != WL_OK) return _s;   \
+    } while (0)
+
+inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// ---------------------------------------------------------------- geometry
+
+// Lattice geometry in the form the kernels need.  Sites of one parity are
+// numbered i = floor(lex / 2) with lex = x + X*(y + Y*(z + Z*t)) (Section 4:
+// even sites first, then odd; within a parity, lexicographic order).
+struct Geom {
+    int X, Y, Z, T;
+    int Xh;          // X / 2
+    int Vh;          // sites per parity
+    int stride;      // padded per-parity array length (multiple of 64)
+    int antiperiodic;
+};
+
+// Coordinates of site i of parity p.
+struct Coord {
+    int x, y, z, t;
+};
+
+__device__ __forceinline__ Coord site_coord(const Geom &g, int i, int p)
+{
+    Coord c;
+    int xh = i % g.Xh;
+    int r = i / g.Xh;
+    c.y = r % g.Y;
+    r /= g.Y;
+    c.z = r % g.Z;
+    c.t = r / g.Z;
+    c.x = 2 * xh + ((p + c.y + c.z + c.t) & 1);
+    return c;
+}
+
+// Per-parity index of the site with coordinates c (either parity).
+__device__ __forceinline__ int site_index(const Geom &g, int x, int y, int z, int t)
+{
+    return (x >> 1) + g.Xh * (y + g.Y * (z + g.Z * t));
+}
+
+// ------------------------------------------------------------------ complex
+
+template <typename R>
+struct cx {
+    R re, im;
+};
+
+template <typename R>
+__device__ __forceinline__ cx<R> operator+(cx<R> a, cx<R> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename R>
+__device__ __forceinline__ cx<R> operator-(cx<R> a, cx<R> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename R>
+__device__ __forceinline__ cx<R> operator*(cx<R> a, cx<R> b)
+{
+    return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename R>
+__device__ __forceinline__ cx<R> operator*(R s, cx<R> a) { return {s * a.re, s * a.im}; }
+template <typename R>
+__device__ __forceinline__ cx<R> conjmul(cx<R> a, cx<R> b)  // conj(a) * b
+{
+    return {a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re};
+}
+template <typename R>
+__device__ __forceinline__ cx<R> cmad(cx<R> a, cx<R> b, cx<R> c)  // a*b + c
+{
+    return {fma(a.re, b.re, fma(-a.im, b.im, c.re)), fma(a.re, b.im, fma(a.im, b.re, c.im))};
+}
+template <typename R>
+__device__ __forceinline__ cx<R> conjmad(cx<R> a, cx<R> b, cx<R> c)  // conj(a)*b + c
+{
+    return {fma(a.re, b.re, fma(a.im, b.im, c.re)), fma(a.re, b.im, fma(-a.im, b.re, c.im))};
+}
+
+// ---------------------------------------------------------- precision I/O
+
+// Arithmetic type per storage precision: FP16 storage computes in FP32.
+template <int P> struct PrecTraits;
+template <> struct PrecTraits<WL_F64> { using R = double; };
+template <> struct PrecTraits<WL_F32> { using R = float; };
+template <> struct PrecTraits<WL_F16> { using R = float; };
+
+// Bytes per site of an internal spinor / per site of one direction's link.
+__host__ __device__ constexpr int spinor_site_bytes(int prec)
+{
+    return prec == WL_F64 ? 192 : prec == WL_F32 ? 96 : 52;
+}
+__host__ __device__ constexpr int link_site_bytes(int prec)
+{
+    return prec == WL_F64 ? 96 : prec == WL_F32 ? 48 : 24;
+}
+
+// Internal spinor layout, component k = 3*spin + colour (12 complex):
+//   F64: double2 [12][stride]
+//   F32: float4  [6][stride]   (chunk j = components 2j, 2j+1)
+//   F16: uint4   [3][stride]   (chunk j = components 4j..4j+3 as half2)
+//        followed by float norm[stride]; value = half * norm.
+template <int P> struct SpinorIO;
+
+template <> struct SpinorIO<WL_F64> {
+    using R = double;
+    static __device__ __forceinline__ void load(const void *base, int stride, int i, cx<R> (&v)[12])
+    {
+        const double2 *p = static_cast<const double2 *>(base);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            double2 t = __ldg(p + (size_t)k * stride + i);
+            v[k] = {t.x, t.y};
+        }
+    }
+    static __device__ __forceinline__ void roundtrip(cx<R> (&)[12]) {}
+    static __device__ __forceinline__ void store(void *base, int stride, int i, const cx<R> (&v)[12])
+    {
+        double2 *p = static_cast<double2 *>(base);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) p[(size_t)k * stride + i] = make_double2(v[k].re, v[k].im);
+    }
+};
+
+template <> struct SpinorIO<WL_F32> {
+    using R = float;
+    static __device__ __forceinline__ void load(const void *base, int stride, int i, cx<R> (&v)[12])
+    {
+        const float4 *p = static_cast<const float4 *>(base);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            float4 t = __ldg(p + (size_t)k * stride + i);
+            v[2 * k] = {t.x, t.y};
+            v[2 * k + 1] = {t.z, t.w};
+        }
+    }
+    static __device__ __forceinline__ void roundtrip(cx<R> (&)[12]) {}
+    static __device__ __forceinline__ void store(void *base, int stride, int i, const cx<R> (&v)[12])
+    {
+        float4 *p = static_cast<float4 *>(base);
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            p[(size_t)k * stride + i] = make_float4(v[2 * k].re, v[2 * k].im, v[2 * k + 1].re, v[2 * k + 1].im);
+    }
+};
+
+__device__ __forceinline__ uint32_t pack_half2(float a, float b)
+{
+    __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+__device__ __forceinline__ float2 unpack_half2(uint32_t u)
+{
+    __half2 h = *reinterpret_cast<__half2 *>(&u);
+    return __half22float2(h);
+}
+
+template <> struct SpinorIO<WL_F16> {
+    using R = float;
+    static __device__ __forceinline__ const float *norms(const void *base, int stride)
+    {
+        return reinterpret_cast<const float *>(static_cast<const uint4 *>(base) + 3 * (size_t)stride);
+    }
+    static __device__ __forceinline__ void load(const void *base, int stride, int i, cx<R> (&v)[12])
+    {
+        const uint4 *p = static_cast<const uint4 *>(base);
+        const float n = __ldg(norms(base, stride) + i);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            uint4 t = __ldg(p + (size_t)k * stride + i);
+            float2 a = unpack_half2(t.x), b = unpack_half2(t.y), c = unpack_half2(t.z), d = unpack_half2(t.w);
+            v[4 * k + 0] = {a.x * n, a.y * n};
+            v[4 * k + 1] = {b.x * n, b.y * n};
+            v[4 * k + 2] = {c.x * n, c.y * n};
+            v[4 * k + 3] = {d.x * n, d.y * n};
+        }
+    }
+    static __device__ __forceinline__ void store(void *base, int stride, int i, const cx<R> (&v)[12])
+    {
+        float m = 0.f;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) m = fmaxf(m, fmaxf(fabsf(v[k].re), fabsf(v[k].im)));
+        const float inv = m > 0.f ? 1.0f / m : 0.f;
+        uint4 *p = static_cast<uint4 *>(base);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            uint4 t;
+            t.x = pack_half2(v[4 * k + 0].re * inv, v[4 * k + 0].im * inv);
+            t.y = pack_half2(v[4 * k + 1].re * inv, v[4 * k + 1].im * inv);
+            t.z = pack_half2(v[4 * k + 2].re * inv, v[4 * k + 2].im * inv);
+            t.w = pack_half2(v[4 * k + 3].re * inv, v[4 * k + 3].im * inv);
+            p[(size_t)k * stride + i] = t;
+        }
+        const_cast<float *>(norms(base, stride))[i] = m;
+    }
+    // Replace v by the values a store followed by a load would return.
+    static __device__ __forceinline__ void roundtrip(cx<R> (&v)[12])
+    {
+        float m = 0.f;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) m = fmaxf(m, fmaxf(fabsf(v[k].re), fabsf(v[k].im)));
+        const float inv = m > 0.f ? 1.0f / m : 0.f;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            float2 h = unpack_half2(pack_half2(v[k].re * inv, v[k].im * inv));
+            v[k] = {h.x * m, h.y * m};
+        }
+    }
+};
+
+// Links: per parity, per direction, the first two rows (6 complex, k = 3*row + col):
+//   F64: double2 [4][6][stride];  F32: float4 [4][3][stride];  F16: uint2 [4][3][stride]
+// Row 2 is rebuilt as conj(row0 x row1).
+template <int P> struct LinkIO;
+
+template <typename R>
+__device__ __forceinline__ void reconstruct_row2(cx<R> (&u)[9])
+{
+    // u[6+c] = conj(r0 x r1)_c
+    cx<R> a = u[1] * u[5] - u[2] * u[4];
+    cx<R> b = u[2] * u[3] - u[0] * u[5];
+    cx<R> c = u[0] * u[4] - u[1] * u[3];
+    u[6] = {a.re, -a.im};
+    u[7] = {b.re, -b.im};
+    u[8] = {c.re, -c.im};
+}
+
+template <> struct LinkIO<WL_F64> {
+    using R = double;
+    static constexpr int chunks = 6;
+    static __device__ __forceinline__ void load(const void *dirbase, int stride, int i, cx<R> (&u)[9])
+    {
+        const double2 *p = static_cast<const double2 *>(dirbase);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            double2 t = __ldg(p + (size_t)k * stride + i);
+            u[k] = {t.x, t.y};
+        }
+        reconstruct_row2(u);
+    }
+};
+template <> struct LinkIO<WL_F32> {
+    using R = float;
+    static constexpr int chunks = 3;
+    static __device__ __forceinline__ void load(const void *dirbase, int stride, int i, cx<R> (&u)[9])
+    {
+        const float4 *p = static_cast<const float4 *>(dirbase);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float4 t = __ldg(p + (size_t)k * stride + i);
+            u[2 * k] = {t.x, t.y};
+            u[2 * k + 1] = {t.z, t.w};
+        }
+        reconstruct_row2(u);
+    }
+};
+template <> struct LinkIO<WL_F16> {
+    using R = float;
+    static constexpr int chunks = 3;
+    static __device__ __forceinline__ void load(const void *dirbase, int stride, int i, cx<R> (&u)[9])
+    {
+        const uint2 *p = static_cast<const uint2 *>(dirbase);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            uint2 t = __ldg(p + (size_t)k * stride + i);
+            float2 a = unpack_half2(t.x), b = unpack_half2(t.y);
+            u[2 * k] = {a.x, a.y};
+            u[2 * k + 1] = {b.x, b.y};
+        }
+        reconstruct_row2(u);
+    }
+};
+
+// Byte offset of direction mu inside one parity's link block.
+__host__ __device__ inline size_t link_dir_bytes(int prec, int stride)
+{
+    return (size_t)link_site_bytes(prec) * stride;
+}
+
+// ---------------------------------------------------------------- reductions
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide sum of NV doubles per thread; result valid in thread 0.
+// Fixed tree order (deterministic).  blockDim.x must be a multiple of 32, <= 1024.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV])
+{
+    __shared__ double sh[32][NV];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) sh[warp][k] = v[k];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double t = lane < nw ? sh[lane][k] : 0.0;
+            v[k] = warp_sum(t);
+        }
+    }
+    __syncthreads();
+}
+
+// Grid-wide deterministic reduction without a second launch ("last block"
+// pattern): every block deposits its NV partial sums in partials[blk][NV];
+// the block that arrives last (atomic ticket) adds the partials in block
+// order and returns true in all of its threads with the totals in tot
+// (valid in thread 0).  The ticket is reset to zero for the next use.
+// `nblk` blocks take part, numbered blk = 0..nblk-1.
+template <int NV>
+__device__ __forceinline__ bool grid_sum(double (&v)[NV], double *partials, unsigned *ticket, int blk,
+                                         int nblk, double (&tot)[NV])
+{
+    __shared__ bool is_last;
+    block_sum<NV>(v);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) partials[(size_t)blk * NV + k] = v[k];
+        __threadfence();
+        unsigned t = atomicAdd(ticket, 1u);
+        is_last = (t == (unsigned)nblk - 1);
+    }
+    __syncthreads();
+    if (!is_last) return false;
+    __threadfence();
+    double acc[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) acc[k] += __ldcg(partials + (size_t)b * NV + k);
+    block_sum<NV>(acc);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) tot[k] = acc[k];
+    if (threadIdx.x == 0) *ticket = 0u;
+    return true;
+}
+
+// --------------------------------------------------------- solver scalars
+
+// Device-resident BiCGstab scalars of one right-hand side (FP64).  Each
+// iteration's kernels read and update these, so no host round trip is
+// needed inside an iteration.
+struct BiState {
+    double rho_re, rho_im;      // <rhat, r>
+    double alpha_re, alpha_im;
+    double omega_re, omega_im;
+    double beta_re, beta_im;
+    double rr;                  // ||r||^2 of the latest residual
+    double target2;             // stop when rr <= target2
+    int done;                   // 1: converged or broken down -> kernels skip this rhs
+    int breakdown;              // 1: a denominator vanished
+    int iters;                  // completed iterations
+    int pad;
+    unsigned ticket[4];         // last-block tickets, one per reduction site
+};
+
+// Reduction scratch: partials[(rhs * nblocks + block) * kRedNV + k].
+constexpr int kRedNV = 4;
+constexpr int kBlock = 128;  // threads per block of every site kernel
+inline int site_blocks(const Geom &g) { return (g.Vh + kBlock - 1) / kBlock; }
+
+}  // namespace wl

@@ -1,0 +1,107 @@
+// Host-side internal interfaces between the translation units of libwilson.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+
+struct wl_lattice {
+    int dims[4];
+    int antiperiodic;
+    long volume;
+    wl::Geom geom;
+};
+
+namespace wl {
+
+// Device buffer owned by the library.
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+// Internal spinor vector (one parity or a batch of rhs of one parity).
+struct Vec {
+    void *ptr = nullptr;
+    int prec = 0;
+    int nrhs = 1;
+    size_t rhs_bytes = 0;  // bytes between consecutive rhs
+    __host__ __device__ void *rhs(int r) const { return static_cast<char *>(ptr) + (size_t)r * rhs_bytes; }
+};
+
+// Workspace arena of a gauge handle: named buffers, grown on demand, reused
+// across calls, freed with the handle.
+struct Workspace {
+    std::map<std::string, DevBuf> bufs;
+    int get(const std::string &name, size_t bytes, void **out);
+    void release();
+};
+
+
+// ---- solver.cu
+int full_relres(wl_gauge *g, const Vec &be, const Vec &bo, const Vec &xe, const Vec &xo, double kappa,
+                const std::vector<double> &bnorm, std::vector<double> &relres, cudaStream_t s);
+
+}  // namespace wl
+
+struct wl_gauge {
+    wl_lattice *lat;
+    unsigned prec_mask;
+    void *links[3][2];  // [prec index][parity] -> 4 directions of 12-real links
+    wl::Workspace ws;
+    std::mutex mu;      // one solve at a time per handle (shared workspace)
+};
+
+namespace wl {
+
+inline int prec_index(int prec) { return prec == WL_F64 ? 0 : prec == WL_F32 ? 1 : prec == WL_F16 ? 2 : -1; }
+inline bool valid_prec(int prec) { return prec_index(prec) >= 0; }
+
+size_t spinor_bytes(const Geom &g, int prec);
+int make_vec(wl_gauge *g, const std::string &name, int prec, int nrhs, Vec *v);
+
+// ---- layout.cu
+int import_spinors(const Geom &g, const void *const *canon, const Vec &out, int parity, cudaStream_t s);
+int export_spinors(const Geom &g, const Vec &in, void *const *canon, int parity, cudaStream_t s);
+
+// ---- dslash.cu
+// out[r] = a1 * x1[r] + a2 * x2[r] + coef * D_{p,1-p} in[r] for r < nrhs (x1, x2
+// optional).  rhs_block = rhs per thread (1, 2 or 4).  st (optional) skips
+// rhs whose solver state is done.
+int hop_ex(wl_gauge *g, const Vec &in, const Vec &out, const Vec *x1, double a1, const Vec *x2, double a2,
+           double coef, int out_parity, int dagger, int rhs_block, const BiState *st, cudaStream_t s);
+int hop(wl_gauge *g, const Vec &in, const Vec &out, const Vec *x, double coef, int out_parity, int dagger,
+        int rhs_block, cudaStream_t s);
+
+// Fused solver hops: second half of an operator application followed by the
+// BiCGstab reductions; blk_off / blk_total place this launch's blocks in a
+// reduction spread over several launches (full-lattice vectors).
+//   kind 0:  v = a1 * xin + coef * D tmp;  <rhat, v>        -> alpha = rho / <rhat, v>
+//   kind 1:  t = a1 * xin + coef * D tmp;  <t, xin>, <t, t> -> omega
+int hop_reduce(wl_gauge *g, int kind, const Vec &tmp, const Vec &xin, double a1, const Vec &out, const Vec &rhat,
+               double coef, int out_parity, int dagger, BiState *state, double *partials, int blk_off,
+               int blk_total, cudaStream_t s);
+
+// ---- blas.cu (all on one parity; nrhs from the vectors)
+int blas_s_update(const Geom &g, const Vec &r, const Vec &v, const Vec &s_out, BiState *st, cudaStream_t s);
+int blas_xr_update(const Geom &g, const Vec &x, const Vec &p, const Vec &sv, const Vec &t, const Vec &r,
+                   const Vec &rhat, BiState *st, double *partials, cudaStream_t s);
+int blas_p_update(const Geom &g, const Vec &r, const Vec &p, const Vec &v, BiState *st, cudaStream_t s);
+int blas_restart(const Geom &g, const Vec &r64, const Vec &r, const Vec &rhat, const Vec &p, const Vec &x,
+                 BiState *state, double *partials, const int *active, const double *delta2, cudaStream_t s);
+int blas_accum(const Geom &g, const Vec &e, const Vec &x64, const int *active, cudaStream_t s);
+int blas_norm2(const Geom &g, const Vec &a, double *out_dev, double *partials, unsigned *tickets, cudaStream_t s);
+int blas_lincomb(const Geom &g, const double *cre_dev, const double *cim_dev, const Vec *const *in, int k,
+                 const Vec &out, cudaStream_t s);
+int blas_convert(const Geom &g, const Vec &in, const Vec &out, cudaStream_t s);
+
+
+// ---- solver.cu
+int full_relres(wl_gauge *g, const Vec &be, const Vec &bo, const Vec &xe, const Vec &xo, double kappa,
+                const std::vector<double> &bnorm, std::vector<double> &relres, cudaStream_t s);
+
+}  // namespace wl

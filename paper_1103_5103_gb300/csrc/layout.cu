@@ -1,0 +1,302 @@
+// Geometry, handles, workspace and the canonical <-> internal layout kernels
+// (Section 4, Eqs. 7-8: structure-of-arrays fields, even sites first).
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "internal.h"
+
+namespace wl {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+size_t spinor_bytes(const Geom &g, int prec) { return (size_t)spinor_site_bytes(prec) * g.stride; }
+
+int Workspace::get(const std::string &name, size_t bytes, void **out)
+{
+    DevBuf &b = bufs[name];
+    if (b.bytes < bytes) {
+        if (b.ptr) cudaFree(b.ptr);
+        b.ptr = nullptr;
+        b.bytes = 0;
+        cudaError_t e = cudaMalloc(&b.ptr, bytes);
+        if (e != cudaSuccess) {
+            set_error("workspace '" + name + "' cudaMalloc(" + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+            b.ptr = nullptr;
+            return e == cudaErrorMemoryAllocation ? WL_ERR_OOM : WL_ERR_CUDA;
+        }
+        b.bytes = bytes;
+    }
+    *out = b.ptr;
+    return WL_OK;
+}
+
+void Workspace::release()
+{
+    for (auto &kv : bufs)
+        if (kv.second.ptr) cudaFree(kv.second.ptr);
+    bufs.clear();
+}
+
+int make_vec(wl_gauge *g, const std::string &name, int prec, int nrhs, Vec *v)
+{
+    v->prec = prec;
+    v->nrhs = nrhs;
+    v->rhs_bytes = (spinor_bytes(g->lat->geom, prec) + 255) & ~(size_t)255;
+    return g->ws.get(name, v->rhs_bytes * nrhs, &v->ptr);
+}
+
+// ------------------------------------------------------------ layout kernels
+
+template <int P>
+__global__ void k_import(Geom g, const double2 *__restrict__ canon, void *out, int parity)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.Vh) return;
+    const Coord c = site_coord(g, i, parity);
+    const size_t lex = c.x + (size_t)g.X * (c.y + (size_t)g.Y * (c.z + (size_t)g.Z * c.t));
+    using R = typename PrecTraits<P>::R;
+    cx<R> v[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        double2 t = canon[lex * 12 + k];
+        v[k] = {(R)t.x, (R)t.y};
+    }
+    SpinorIO<P>::store(out, g.stride, i, v);
+}
+
+template <int P>
+__global__ void k_export(Geom g, const void *in, double2 *__restrict__ canon, int parity)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.Vh) return;
+    const Coord c = site_coord(g, i, parity);
+    const size_t lex = c.x + (size_t)g.X * (c.y + (size_t)g.Y * (c.z + (size_t)g.Z * c.t));
+    using R = typename PrecTraits<P>::R;
+    cx<R> v[12];
+    SpinorIO<P>::load(in, g.stride, i, v);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) canon[lex * 12 + k] = make_double2((double)v[k].re, (double)v[k].im);
+}
+
+// Pack rows 0 and 1 of U_mu at the sites of one parity.
+template <int P>
+__global__ void k_pack_links(Geom g, const double2 *__restrict__ U, void *out, int parity)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int mu = blockIdx.y;
+    if (i >= g.Vh) return;
+    const Coord c = site_coord(g, i, parity);
+    const size_t V = (size_t)g.Vh * 2;
+    const size_t lex = c.x + (size_t)g.X * (c.y + (size_t)g.Y * (c.z + (size_t)g.Z * c.t));
+    const double2 *u = U + ((size_t)mu * V + lex) * 9;
+    char *dir = static_cast<char *>(out) + (size_t)mu * link_dir_bytes(P, g.stride);
+    if (P == WL_F64) {
+        double2 *p = reinterpret_cast<double2 *>(dir);
+        for (int k = 0; k < 6; ++k) p[(size_t)k * g.stride + i] = u[k];
+    } else if (P == WL_F32) {
+        float4 *p = reinterpret_cast<float4 *>(dir);
+        for (int k = 0; k < 3; ++k) {
+            double2 a = u[2 * k], b = u[2 * k + 1];
+            p[(size_t)k * g.stride + i] = make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
+        }
+    } else {
+        uint2 *p = reinterpret_cast<uint2 *>(dir);
+        for (int k = 0; k < 3; ++k) {
+            double2 a = u[2 * k], b = u[2 * k + 1];
+            uint2 t;
+            t.x = pack_half2((float)a.x, (float)a.y);
+            t.y = pack_half2((float)b.x, (float)b.y);
+            p[(size_t)k * g.stride + i] = t;
+        }
+    }
+}
+
+template <int P>
+static int launch_import(const Geom &g, const void *canon, void *out, int parity, cudaStream_t s)
+{
+    const int th = 128, bl = (g.Vh + th - 1) / th;
+    k_import<P><<<bl, th, 0, s>>>(g, static_cast<const double2 *>(canon), out, parity);
+    WL_CUDA_TRY(cudaGetLastError());
+    return WL_OK;
+}
+
+template <int P>
+static int launch_export(const Geom &g, const void *in, void *canon, int parity, cudaStream_t s)
+{
+    const int th = 128, bl = (g.Vh + th - 1) / th;
+    k_export<P><<<bl, th, 0, s>>>(g, in, static_cast<double2 *>(canon), parity);
+    WL_CUDA_TRY(cudaGetLastError());
+    return WL_OK;
+}
+
+int import_spinors(const Geom &g, const void *const *canon, const Vec &out, int parity, cudaStream_t s)
+{
+    for (int r = 0; r < out.nrhs; ++r) {
+        int st = out.prec == WL_F64   ? launch_import<WL_F64>(g, canon[r], out.rhs(r), parity, s)
+                 : out.prec == WL_F32 ? launch_import<WL_F32>(g, canon[r], out.rhs(r), parity, s)
+                                      : launch_import<WL_F16>(g, canon[r], out.rhs(r), parity, s);
+        WL_TRY(st);
+    }
+    return WL_OK;
+}
+
+int export_spinors(const Geom &g, const Vec &in, void *const *canon, int parity, cudaStream_t s)
+{
+    for (int r = 0; r < in.nrhs; ++r) {
+        int st = in.prec == WL_F64   ? launch_export<WL_F64>(g, in.rhs(r), canon[r], parity, s)
+                 : in.prec == WL_F32 ? launch_export<WL_F32>(g, in.rhs(r), canon[r], parity, s)
+                                     : launch_export<WL_F16>(g, in.rhs(r), canon[r], parity, s);
+        WL_TRY(st);
+    }
+    return WL_OK;
+}
+
+}  // namespace wl
+
+using namespace wl;
+
+// ---------------------------------------------------------------- C ABI
+
+extern "C" const char *wl_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" int wl_params_default(wl_solver_params *p)
+{
+    if (!p) { set_error("wl_params_default: NULL"); return WL_ERR_ARG; }
+    p->tol = 1e-10;
+    p->max_iter = 100000;
+    p->inner_prec = WL_F32;
+    p->inner_tol = 0.0;
+    p->max_restarts = 100;
+    p->guess = WL_GUESS_POLY;
+    p->mode = WL_MODE_GRAPH;
+    p->rhs_block = 0;
+    p->graph_iters = 8;
+    p->eo = 1;
+    return WL_OK;
+}
+
+extern "C" int wl_lattice_create(const int dims[4], int antiperiodic_t, wl_lattice **out)
+{
+    if (!dims || !out) { set_error("wl_lattice_create: NULL argument"); return WL_ERR_ARG; }
+    long V = 1;
+    for (int k = 0; k < 4; ++k) {
+        if (dims[k] < 2 || (dims[k] & 1)) {
+            set_error("wl_lattice_create: every extent must be even and >= 2 (got " + std::to_string(dims[k]) + ")");
+            return WL_ERR_ARG;
+        }
+        V *= dims[k];
+    }
+    if (V >= (1L << 31) / 12) { set_error("wl_lattice_create: volume too large"); return WL_ERR_ARG; }
+    wl_lattice *l = new wl_lattice;
+    std::memcpy(l->dims, dims, sizeof(int) * 4);
+    l->antiperiodic = antiperiodic_t ? 1 : 0;
+    l->volume = V;
+    Geom &g = l->geom;
+    g.X = dims[0]; g.Y = dims[1]; g.Z = dims[2]; g.T = dims[3];
+    g.Xh = dims[0] / 2;
+    g.Vh = (int)(V / 2);
+    g.stride = (g.Vh + 63) & ~63;
+    g.antiperiodic = l->antiperiodic;
+    *out = l;
+    return WL_OK;
+}
+
+extern "C" int wl_lattice_destroy(wl_lattice *lat)
+{
+    delete lat;
+    return WL_OK;
+}
+
+extern "C" int wl_spinor_bytes(const wl_lattice *lat, int prec, size_t *bytes)
+{
+    if (!lat || !bytes || !valid_prec(prec)) { set_error("wl_spinor_bytes: bad argument"); return WL_ERR_ARG; }
+    *bytes = spinor_bytes(lat->geom, prec);
+    return WL_OK;
+}
+
+extern "C" int wl_spinor_import(const wl_lattice *lat, const void *canon, void *internal, int prec, int parity,
+                                void *stream)
+{
+    if (!lat || !canon || !internal || !valid_prec(prec) || (parity != 0 && parity != 1)) {
+        set_error("wl_spinor_import: bad argument");
+        return WL_ERR_ARG;
+    }
+    Vec v;
+    v.ptr = internal;
+    v.prec = prec;
+    v.nrhs = 1;
+    const void *c[1] = {canon};
+    return import_spinors(lat->geom, c, v, parity, as_stream(stream));
+}
+
+extern "C" int wl_spinor_export(const wl_lattice *lat, const void *internal, void *canon, int prec, int parity,
+                                void *stream)
+{
+    if (!lat || !canon || !internal || !valid_prec(prec) || (parity != 0 && parity != 1)) {
+        set_error("wl_spinor_export: bad argument");
+        return WL_ERR_ARG;
+    }
+    Vec v;
+    v.ptr = const_cast<void *>(internal);
+    v.prec = prec;
+    v.nrhs = 1;
+    void *c[1] = {canon};
+    return export_spinors(lat->geom, v, c, parity, as_stream(stream));
+}
+
+extern "C" int wl_gauge_create(wl_lattice *lat, const void *U, unsigned prec_mask, void *stream, wl_gauge **out)
+{
+    if (!lat || !U || !out || !(prec_mask & (WL_F64 | WL_F32 | WL_F16)) || (prec_mask & ~7u)) {
+        set_error("wl_gauge_create: bad argument");
+        return WL_ERR_ARG;
+    }
+    cudaStream_t s = as_stream(stream);
+    wl_gauge *g = new wl_gauge;
+    g->lat = lat;
+    g->prec_mask = prec_mask;
+    std::memset(g->links, 0, sizeof(g->links));
+    const Geom &geo = lat->geom;
+    const int precs[3] = {WL_F64, WL_F32, WL_F16};
+    for (int pi = 0; pi < 3; ++pi) {
+        const int P = precs[pi];
+        if (!(prec_mask & P)) continue;
+        for (int par = 0; par < 2; ++par) {
+            const size_t bytes = 4 * link_dir_bytes(P, geo.stride);
+            cudaError_t e = cudaMalloc(&g->links[pi][par], bytes);
+            if (e != cudaSuccess) {
+                set_error(std::string("wl_gauge_create: cudaMalloc: ") + cudaGetErrorString(e));
+                wl_gauge_destroy(g);
+                return e == cudaErrorMemoryAllocation ? WL_ERR_OOM : WL_ERR_CUDA;
+            }
+            dim3 grid((geo.Vh + 127) / 128, 4);
+            const double2 *Uc = static_cast<const double2 *>(U);
+            if (P == WL_F64) k_pack_links<WL_F64><<<grid, 128, 0, s>>>(geo, Uc, g->links[pi][par], par);
+            if (P == WL_F32) k_pack_links<WL_F32><<<grid, 128, 0, s>>>(geo, Uc, g->links[pi][par], par);
+            if (P == WL_F16) k_pack_links<WL_F16><<<grid, 128, 0, s>>>(geo, Uc, g->links[pi][par], par);
+        }
+    }
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error(std::string("wl_gauge_create: ") + cudaGetErrorString(e));
+        wl_gauge_destroy(g);
+        return WL_ERR_CUDA;
+    }
+    *out = g;
+    return WL_OK;
+}
+
+extern "C" int wl_gauge_destroy(wl_gauge *g)
+{
+    if (!g) return WL_OK;
+    cudaDeviceSynchronize();
+    for (int pi = 0; pi < 3; ++pi)
+        for (int par = 0; par < 2; ++par)
+            if (g->links[pi][par]) cudaFree(g->links[pi][par]);
+    g->ws.release();
+    delete g;
+    return WL_OK;
+}

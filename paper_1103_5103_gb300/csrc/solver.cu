@@ -1,0 +1,497 @@
+// Solvers (Section 6): even-odd preconditioned BiCGstab with FP64 defect
+// correction around a reduced-precision inner loop, the multi-mass driver
+// with the Lagrange initial guess, and the plumbing they share.
+//
+// Inner BiCGstab iteration on M_prec = 1 - kappa^2 D_eo D_oe, per rhs
+// (van der Vorst; the paper cites it and does not print it):
+//   v = M_prec p                 hop D_oe p -> tmp;  v = p - k^2 D_eo tmp, <rhat,v> -> alpha
+//   s = r - alpha v
+//   t = M_prec s                 hop D_oe s -> tmp;  t = s - k^2 D_eo tmp, <t,s>, <t,t> -> omega
+//   x += alpha p + omega s; r = s - omega t;   <rhat,r>, ||r||^2 -> beta, convergence
+//   p = r + beta (p - omega v)
+// Seven kernels; every scalar stays in device memory (BiState), so an
+// iteration needs no host round trip and a block of iterations can be
+// replayed from a captured CUDA graph.  Kernels of a converged rhs return
+// at once, so surplus captured iterations cost only empty launches.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace wl {
+
+// Pinned host staging for small per-rhs arrays.
+struct Pinned {
+    void *p = nullptr;
+    size_t bytes = 0;
+    int reserve(size_t b)
+    {
+        if (b <= bytes) return WL_OK;
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        WL_CUDA_TRY(cudaMallocHost(&p, b));
+        bytes = b;
+        return WL_OK;
+    }
+    ~Pinned()
+    {
+        if (p) cudaFreeHost(p);
+    }
+};
+
+// Scratch of one batched solve: per-rhs state, reduction partials, flags.
+struct Scratch {
+    BiState *state = nullptr;    // [nrhs]
+    double *partials = nullptr;  // [nrhs][2 * site_blocks][kRedNV]
+    double *norms = nullptr;     // [nrhs * 4]
+    unsigned *tickets = nullptr; // [nrhs * 4]
+    int *active = nullptr;       // [nrhs]
+    double *delta2 = nullptr;    // [nrhs]
+    double *coef = nullptr;      // [2][nrhs * 16] lincomb coefficients
+};
+
+static int get_scratch(wl_gauge *g, int nrhs, Scratch *sc, cudaStream_t s)
+{
+    const Geom &geo = g->lat->geom;
+    void *p;
+    WL_TRY(g->ws.get("state", sizeof(BiState) * nrhs, &p));
+    sc->state = static_cast<BiState *>(p);
+    WL_TRY(g->ws.get("partials", sizeof(double) * nrhs * 2 * site_blocks(geo) * kRedNV, &p));
+    sc->partials = static_cast<double *>(p);
+    WL_TRY(g->ws.get("norms", sizeof(double) * nrhs * 4, &p));
+    sc->norms = static_cast<double *>(p);
+    bool fresh = g->ws.bufs["tickets"].bytes < sizeof(unsigned) * nrhs * 4;
+    WL_TRY(g->ws.get("tickets", sizeof(unsigned) * nrhs * 4, &p));
+    sc->tickets = static_cast<unsigned *>(p);
+    if (fresh) WL_CUDA_TRY(cudaMemsetAsync(p, 0, sizeof(unsigned) * nrhs * 4, s));
+    WL_TRY(g->ws.get("active", sizeof(int) * nrhs, &p));
+    sc->active = static_cast<int *>(p);
+    WL_TRY(g->ws.get("delta2", sizeof(double) * nrhs, &p));
+    sc->delta2 = static_cast<double *>(p);
+    WL_TRY(g->ws.get("coef", sizeof(double) * 2 * nrhs * 16, &p));
+    sc->coef = static_cast<double *>(p);
+    // tickets inside BiState start at zero
+    WL_CUDA_TRY(cudaMemsetAsync(sc->state, 0, sizeof(BiState) * nrhs, s));
+    return WL_OK;
+}
+
+// --------------------------------------------------------------- inner loop
+
+struct Inner {
+    wl_gauge *g;
+    int prec, xprec, nrhs;
+    double kappa;
+    Vec r, rhat, p, v, s, t, tmp, e;
+    Scratch sc;
+};
+
+static int make_inner(wl_gauge *g, int prec, int nrhs, double kappa, Inner *in, cudaStream_t s)
+{
+    in->g = g;
+    in->prec = prec;
+    in->xprec = prec == WL_F64 ? WL_F64 : WL_F32;
+    in->nrhs = nrhs;
+    in->kappa = kappa;
+    WL_TRY(make_vec(g, "in_r", prec, nrhs, &in->r));
+    WL_TRY(make_vec(g, "in_rhat", prec, nrhs, &in->rhat));
+    WL_TRY(make_vec(g, "in_p", prec, nrhs, &in->p));
+    WL_TRY(make_vec(g, "in_v", prec, nrhs, &in->v));
+    WL_TRY(make_vec(g, "in_s", prec, nrhs, &in->s));
+    WL_TRY(make_vec(g, "in_t", prec, nrhs, &in->t));
+    WL_TRY(make_vec(g, "in_tmp", prec, nrhs, &in->tmp));
+    WL_TRY(make_vec(g, "in_e", in->xprec, nrhs, &in->e));
+    return get_scratch(g, nrhs, &in->sc, s);
+}
+
+// Enqueue one BiCGstab iteration for every rhs.
+static int inner_iteration(Inner &in, int rhs_block, cudaStream_t s)
+{
+    const Geom &geo = in.g->lat->geom;
+    const double k2 = in.kappa * in.kappa;
+    const int nsb = site_blocks(geo);
+    WL_TRY(hop_ex(in.g, in.p, in.tmp, nullptr, 0.0, nullptr, 0.0, 1.0, WL_ODD, 0, rhs_block, in.sc.state, s));
+    WL_TRY(hop_reduce(in.g, 0, in.tmp, in.p, 1.0, in.v, in.rhat, -k2, WL_EVEN, 0, in.sc.state, in.sc.partials, 0,
+                      nsb, s));
+    WL_TRY(blas_s_update(geo, in.r, in.v, in.s, in.sc.state, s));
+    WL_TRY(hop_ex(in.g, in.s, in.tmp, nullptr, 0.0, nullptr, 0.0, 1.0, WL_ODD, 0, rhs_block, in.sc.state, s));
+    WL_TRY(hop_reduce(in.g, 1, in.tmp, in.s, 1.0, in.t, in.rhat, -k2, WL_EVEN, 0, in.sc.state, in.sc.partials, 0,
+                      nsb, s));
+    WL_TRY(blas_xr_update(geo, in.e, in.p, in.s, in.t, in.r, in.rhat, in.sc.state, in.sc.partials, s));
+    WL_TRY(blas_p_update(geo, in.r, in.p, in.v, in.sc.state, s));
+    return WL_OK;
+}
+
+// Run inner iterations until every rhs is done or max_iter is reached.
+// Returns the state array copied to host in host_state.
+static int run_inner(Inner &in, const wl_solver_params &prm, int max_iter, std::vector<BiState> &host_state,
+                     cudaStream_t s)
+{
+    const int nrhs = in.nrhs;
+    const int rb = prm.rhs_block > 0 ? prm.rhs_block : 1;
+    Pinned pin;
+    WL_TRY(pin.reserve(sizeof(BiState) * nrhs));
+    BiState *hs = static_cast<BiState *>(pin.p);
+    host_state.resize(nrhs);
+    const int K = std::max(1, prm.graph_iters);
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap = nullptr;
+    int status = WL_OK;
+    if (prm.mode == WL_MODE_GRAPH) {
+        WL_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            for (int k = 0; k < K && status == WL_OK; ++k) status = inner_iteration(in, rb, cap);
+            e = cudaStreamEndCapture(cap, &graph);
+        }
+        if (e == cudaSuccess && status == WL_OK) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess || status != WL_OK) {
+            if (exec) cudaGraphExecDestroy(exec);
+            cudaStreamDestroy(cap);
+            if (status == WL_OK) {
+                set_error(std::string("graph capture: ") + cudaGetErrorString(e));
+                status = WL_ERR_CUDA;
+            }
+            return status;
+        }
+    }
+    int done_iters = 0;
+    for (;;) {
+        if (exec) {
+            cudaError_t e = cudaGraphLaunch(exec, s);
+            if (e != cudaSuccess) {
+                set_error(std::string("cudaGraphLaunch: ") + cudaGetErrorString(e));
+                status = WL_ERR_CUDA;
+                break;
+            }
+            done_iters += K;
+        } else {
+            status = inner_iteration(in, rb, s);
+            if (status != WL_OK) break;
+            done_iters += 1;
+        }
+        cudaError_t e = cudaMemcpyAsync(hs, in.sc.state, sizeof(BiState) * nrhs, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            set_error(std::string("inner loop: ") + cudaGetErrorString(e));
+            status = WL_ERR_CUDA;
+            break;
+        }
+        bool all = true;
+        for (int r = 0; r < nrhs; ++r) all &= hs[r].done != 0;
+        if (all || done_iters >= max_iter) break;
+    }
+    std::memcpy(host_state.data(), hs, sizeof(BiState) * nrhs);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (cap) cudaStreamDestroy(cap);
+    return status;
+}
+
+// ----------------------------------------------------- outer (FP64) loop
+
+struct Timer {
+    std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+    double sec() const
+    {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+};
+
+static double default_inner_tol(int prec)
+{
+    return prec == WL_F32 ? 1e-5 : prec == WL_F16 ? 3e-3 : 1e-12;
+}
+
+// Solve M_prec x = bprec for nrhs right-hand sides by defect correction:
+//   r = bprec - M_prec x (FP64); stop when ||r|| <= tol * bnorm;
+//   inner BiCGstab in prec on M_prec e = r to relative residual delta;
+//   x += e (FP64).
+// x64 holds the initial guesses and receives the solutions.
+static int eo_defect_correction(wl_gauge *g, const Vec &bprec, const Vec &x64, double kappa,
+                                const wl_solver_params &prm, const std::vector<double> &bnorm,
+                                std::vector<wl_solver_stats> &stats, cudaStream_t s)
+{
+    const Geom &geo = g->lat->geom;
+    const int nrhs = bprec.nrhs;
+    const int prec = prm.inner_prec;
+    Inner in;
+    WL_TRY(make_inner(g, prec, nrhs, kappa, &in, s));
+    Vec r64, tmp64;
+    WL_TRY(make_vec(g, "dc_r64", WL_F64, nrhs, &r64));
+    WL_TRY(make_vec(g, "dc_tmp64", WL_F64, nrhs, &tmp64));
+    Pinned pin;
+    WL_TRY(pin.reserve(nrhs * (sizeof(double) * 2 + sizeof(int))));
+    double *h_rn2 = static_cast<double *>(pin.p);
+    double *h_delta2 = h_rn2 + nrhs;
+    int *h_active = reinterpret_cast<int *>(h_delta2 + nrhs);
+    const double delta0 = prm.inner_tol > 0 ? prm.inner_tol : default_inner_tol(prec);
+    std::vector<int> outer_done(nrhs, 0), iters(nrhs, 0), restarts(nrhs, 0), fails(nrhs, 0);
+    std::vector<double> last_rn(nrhs, INFINITY);
+    std::vector<BiState> hst;
+    const double k2 = kappa * kappa;
+    int total_restarts = 0;
+    for (;;) {
+        // r64 = bprec - x + kappa^2 D_eo D_oe x
+        WL_TRY(hop(g, x64, tmp64, nullptr, 1.0, WL_ODD, 0, 1, s));
+        WL_TRY(hop_ex(g, tmp64, r64, &bprec, 1.0, &x64, -1.0, k2, WL_EVEN, 0, 1, nullptr, s));
+        WL_TRY(blas_norm2(geo, r64, in.sc.norms, in.sc.partials, in.sc.tickets, s));
+        WL_CUDA_TRY(cudaMemcpyAsync(h_rn2, in.sc.norms, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
+        WL_CUDA_TRY(cudaStreamSynchronize(s));
+        int n_active = 0;
+        for (int r = 0; r < nrhs; ++r) {
+            const double rn = std::sqrt(h_rn2[r]);
+            h_active[r] = 0;
+            if (outer_done[r]) continue;
+            if (!std::isfinite(rn)) { outer_done[r] = 1; stats[r].status = WL_ERR_BREAKDOWN; continue; }
+            if (rn <= prm.tol * bnorm[r]) { outer_done[r] = 1; stats[r].status = WL_OK; continue; }
+            if (iters[r] >= prm.max_iter || restarts[r] >= prm.max_restarts || fails[r] >= 5) {
+                outer_done[r] = 1;
+                stats[r].status = fails[r] >= 5 ? WL_ERR_BREAKDOWN : WL_ERR_NOCONV;
+                continue;
+            }
+            // no need to iterate the inner solve below what the outer target needs
+            const double need = 0.5 * prm.tol * bnorm[r] / rn;
+            const double d = std::max(delta0, need);
+            h_delta2[r] = d * d;
+            h_active[r] = 1;
+            fails[r] = rn >= 0.5 * last_rn[r] ? fails[r] + 1 : 0;  // stagnation guard
+            last_rn[r] = rn;
+            ++n_active;
+        }
+        if (n_active == 0) break;
+        WL_CUDA_TRY(cudaMemcpyAsync(in.sc.active, h_active, sizeof(int) * nrhs, cudaMemcpyHostToDevice, s));
+        WL_CUDA_TRY(cudaMemcpyAsync(in.sc.delta2, h_delta2, sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
+        WL_TRY(blas_restart(geo, r64, in.r, in.rhat, in.p, in.e, in.sc.state, in.sc.partials, in.sc.active,
+                            in.sc.delta2, s));
+        int cap = 0;
+        for (int r = 0; r < nrhs; ++r)
+            if (h_active[r]) cap = std::max(cap, prm.max_iter - iters[r]);
+        WL_TRY(run_inner(in, prm, cap, hst, s));
+        WL_TRY(blas_accum(geo, in.e, x64, in.sc.active, s));
+        for (int r = 0; r < nrhs; ++r)
+            if (h_active[r]) {
+                iters[r] += hst[r].iters;
+                restarts[r] += 1;
+            }
+        ++total_restarts;
+    }
+    for (int r = 0; r < nrhs; ++r) {
+        stats[r].iterations = iters[r];
+        stats[r].matvecs = 2 * iters[r] + restarts[r] + 1;
+        stats[r].restarts = restarts[r];
+    }
+    (void)total_restarts;
+    return WL_OK;
+}
+
+// Per-rhs FP64 squared norms of one parity vector (host result).
+static int norms2_host(wl_gauge *g, const Vec &v, Scratch &sc, std::vector<double> &out, cudaStream_t s)
+{
+    const int n = v.nrhs;
+    WL_TRY(blas_norm2(g->lat->geom, v, sc.norms, sc.partials, sc.tickets, s));
+    out.resize(n);
+    WL_CUDA_TRY(cudaMemcpyAsync(out.data(), sc.norms, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    WL_CUDA_TRY(cudaStreamSynchronize(s));
+    return WL_OK;
+}
+
+// FP64 relative residuals ||b - M_k x|| / ||b|| over the full lattice for
+// nrhs vectors given by their halves.
+int full_relres(wl_gauge *g, const Vec &be, const Vec &bo, const Vec &xe, const Vec &xo, double kappa,
+                const std::vector<double> &bnorm, std::vector<double> &relres, cudaStream_t s)
+{
+    const int nrhs = be.nrhs;
+    Vec re, ro;
+    WL_TRY(make_vec(g, "rr_re", WL_F64, nrhs, &re));
+    WL_TRY(make_vec(g, "rr_ro", WL_F64, nrhs, &ro));
+    // r_e = b_e - x_e + kappa D_eo x_o ; r_o = b_o - x_o + kappa D_oe x_e
+    WL_TRY(hop_ex(g, xo, re, &be, 1.0, &xe, -1.0, kappa, WL_EVEN, 0, 1, nullptr, s));
+    WL_TRY(hop_ex(g, xe, ro, &bo, 1.0, &xo, -1.0, kappa, WL_ODD, 0, 1, nullptr, s));
+    Scratch sc;
+    WL_TRY(get_scratch(g, nrhs, &sc, s));
+    std::vector<double> n2e, n2o;
+    WL_TRY(norms2_host(g, re, sc, n2e, s));
+    WL_TRY(norms2_host(g, ro, sc, n2o, s));
+    relres.resize(nrhs);
+    for (int r = 0; r < nrhs; ++r) relres[r] = bnorm[r] > 0 ? std::sqrt(n2e[r] + n2o[r]) / bnorm[r] : 0.0;
+    return WL_OK;
+}
+
+// One mass for nrhs sources already imported as be, bo (FP64):
+// bprec = b_e + kappa D_eo b_o; solve; x_o = b_o + kappa D_oe x_e;
+// FP64 true residual over the full lattice; export x.
+static int solve_one_mass(wl_gauge *g, const Vec &be, const Vec &bo, const Vec &xe, double m0,
+                          const wl_solver_params &prm, const std::vector<double> &bnorm2, void *const *x_out,
+                          int x_out_stride, std::vector<wl_solver_stats> &stats, cudaStream_t s)
+{
+    const Geom &geo = g->lat->geom;
+    const int nrhs = be.nrhs;
+    const double kappa = 1.0 / (2.0 * m0 + 8.0);
+    Vec bprec, xo;
+    WL_TRY(make_vec(g, "mm_bprec", WL_F64, nrhs, &bprec));
+    WL_TRY(make_vec(g, "mm_xo", WL_F64, nrhs, &xo));
+    WL_TRY(hop(g, bo, bprec, &be, kappa, WL_EVEN, 0, 1, s));
+    std::vector<double> bnorm(nrhs);
+    for (int r = 0; r < nrhs; ++r) bnorm[r] = std::sqrt(bnorm2[r]);
+    WL_TRY(eo_defect_correction(g, bprec, xe, kappa, prm, bnorm, stats, s));
+    WL_TRY(hop(g, xe, xo, &bo, kappa, WL_ODD, 0, 1, s));
+    std::vector<double> rel;
+    WL_TRY(full_relres(g, be, bo, xe, xo, kappa, bnorm, rel, s));
+    std::vector<void *> outs(nrhs);
+    for (int r = 0; r < nrhs; ++r) {
+        stats[r].mass = m0;
+        stats[r].true_relres = rel[r];
+        outs[r] = x_out[(size_t)r * x_out_stride];
+    }
+    WL_TRY(export_spinors(geo, xe, outs.data(), WL_EVEN, s));
+    WL_TRY(export_spinors(geo, xo, outs.data(), WL_ODD, s));
+    return WL_OK;
+}
+
+static int check_params(const wl_gauge *g, const wl_solver_params *p)
+{
+    if (!p || !(p->tol > 0) || p->max_iter < 1 || !valid_prec(p->inner_prec) || p->max_restarts < 1 ||
+        (p->mode != WL_MODE_HOST && p->mode != WL_MODE_GRAPH) || p->graph_iters < 0 || p->rhs_block < 0 ||
+        p->rhs_block > 4) {
+        set_error("solver parameters out of range");
+        return WL_ERR_ARG;
+    }
+    if (!(g->prec_mask & WL_F64) || !(g->prec_mask & p->inner_prec)) {
+        set_error("gauge handle needs FP64 links and links of the inner precision");
+        return WL_ERR_ARG;
+    }
+    return WL_OK;
+}
+
+}  // namespace wl
+
+using namespace wl;
+
+// ---------------------------------------------------------------- C ABI
+
+extern "C" int bicgstab_solve(wl_gauge *g, const void *b, void *x, double m0, const wl_solver_params *p,
+                              wl_solver_stats *stats, void *stream)
+{
+    if (!g || !b || !x || !stats) { set_error("bicgstab_solve: NULL argument"); return WL_ERR_ARG; }
+    WL_TRY(check_params(g, p));
+    if (!p->eo) { set_error("bicgstab_solve: only the even-odd preconditioned solve is provided"); return WL_ERR_ARG; }
+    if (!(2.0 * m0 + 8.0 > 0.0)) { set_error("bicgstab_solve: need 2 m0 + 8 > 0"); return WL_ERR_ARG; }
+    std::lock_guard<std::mutex> lock(g->mu);
+    cudaStream_t s = as_stream(stream);
+    const Geom &geo = g->lat->geom;
+    Timer tm;
+    Vec be, bo, xe;
+    WL_TRY(make_vec(g, "b_e", WL_F64, 1, &be));
+    WL_TRY(make_vec(g, "b_o", WL_F64, 1, &bo));
+    WL_TRY(make_vec(g, "x_e", WL_F64, 1, &xe));
+    const void *bc[1] = {b};
+    const void *xc[1] = {x};
+    WL_TRY(import_spinors(geo, bc, be, WL_EVEN, s));
+    WL_TRY(import_spinors(geo, bc, bo, WL_ODD, s));
+    WL_TRY(import_spinors(geo, xc, xe, WL_EVEN, s));
+    Scratch sc;
+    WL_TRY(get_scratch(g, 1, &sc, s));
+    std::vector<double> ne, no;
+    WL_TRY(norms2_host(g, be, sc, ne, s));
+    WL_TRY(norms2_host(g, bo, sc, no, s));
+    std::vector<double> bn2 = {ne[0] + no[0]};
+    std::vector<wl_solver_stats> st(1);
+    std::memset(st.data(), 0, sizeof(wl_solver_stats));
+    void *xo[1] = {x};
+    WL_TRY(solve_one_mass(g, be, bo, xe, m0, *p, bn2, xo, 1, st, s));
+    WL_CUDA_TRY(cudaStreamSynchronize(s));
+    st[0].seconds = tm.sec();
+    *stats = st[0];
+    return st[0].status;
+}
+
+extern "C" int multimass_solve(wl_gauge *g, const void *const *b, void *const *x, int n_rhs, const double *m0,
+                               int n_mass, const wl_solver_params *p, wl_solver_stats *stats, void *stream)
+{
+    if (!g || !b || !x || !m0 || !stats || n_rhs < 1 || n_mass < 1 || n_mass > 17) {
+        set_error("multimass_solve: bad argument (1 <= n_mass <= 17)");
+        return WL_ERR_ARG;
+    }
+    WL_TRY(check_params(g, p));
+    for (int i = 0; i < n_mass; ++i) {
+        if (!(2.0 * m0[i] + 8.0 > 0.0)) { set_error("multimass_solve: need 2 m0 + 8 > 0"); return WL_ERR_ARG; }
+        for (int j = 0; j < i; ++j)
+            if (m0[i] == m0[j]) { set_error("multimass_solve: masses must be distinct"); return WL_ERR_ARG; }
+    }
+    for (int r = 0; r < n_rhs; ++r)
+        if (!b[r]) { set_error("multimass_solve: NULL source"); return WL_ERR_ARG; }
+    for (int k = 0; k < n_rhs * n_mass; ++k)
+        if (!x[k]) { set_error("multimass_solve: NULL solution pointer"); return WL_ERR_ARG; }
+    std::lock_guard<std::mutex> lock(g->mu);
+    cudaStream_t s = as_stream(stream);
+    const Geom &geo = g->lat->geom;
+    Vec be, bo;
+    WL_TRY(make_vec(g, "b_e", WL_F64, n_rhs, &be));
+    WL_TRY(make_vec(g, "b_o", WL_F64, n_rhs, &bo));
+    WL_TRY(import_spinors(geo, b, be, WL_EVEN, s));
+    WL_TRY(import_spinors(geo, b, bo, WL_ODD, s));
+    Scratch sc;
+    WL_TRY(get_scratch(g, n_rhs, &sc, s));
+    std::vector<double> ne, no, bn2(n_rhs);
+    WL_TRY(norms2_host(g, be, sc, ne, s));
+    WL_TRY(norms2_host(g, bo, sc, no, s));
+    for (int r = 0; r < n_rhs; ++r) bn2[r] = ne[r] + no[r];
+
+    // heaviest first (Section 7)
+    std::vector<int> order(n_mass);
+    std::iota(order.begin(), order.end(), 0);
+    std::sort(order.begin(), order.end(), [&](int a, int c) { return m0[a] > m0[c]; });
+    std::vector<Vec> sol(n_mass);  // even-site FP64 solutions in solve order
+    std::vector<wl_solver_stats> st(n_rhs);
+    Pinned pin;
+    WL_TRY(pin.reserve(sizeof(double) * 2 * n_rhs * 16));
+    double *hc = static_cast<double *>(pin.p);
+    int worst = WL_OK;
+    for (int k = 0; k < n_mass; ++k) {
+        Timer tm;
+        const int im = order[k];
+        const double m = m0[im];
+        WL_TRY(make_vec(g, "mm_sol" + std::to_string(k), WL_F64, n_rhs, &sol[k]));
+        if (k == 0 || p->guess == WL_GUESS_ZERO) {
+            WL_CUDA_TRY(cudaMemsetAsync(sol[k].ptr, 0, sol[k].rhs_bytes * n_rhs, s));
+        } else {
+            // Lagrange extrapolation of psi = x / (m + 4) through all previous
+            // masses (Eq. Poly): x_guess = (m + 4) sum_j w_j x_j / (m_j + 4),
+            // w_j = prod_{i != j} (m - m_i) / (m_j - m_i).
+            for (int j = 0; j < k; ++j) {
+                const double mj = m0[order[j]];
+                double w = 1.0;
+                for (int i = 0; i < k; ++i)
+                    if (i != j) {
+                        const double mi = m0[order[i]];
+                        w *= (m - mi) / (mj - mi);
+                    }
+                const double c = (m + 4.0) * w / (mj + 4.0);
+                for (int r = 0; r < n_rhs; ++r) {
+                    hc[r * k + j] = c;
+                    hc[n_rhs * 16 + r * k + j] = 0.0;
+                }
+            }
+            WL_CUDA_TRY(cudaMemcpyAsync(sc.coef, hc, sizeof(double) * 2 * n_rhs * 16, cudaMemcpyHostToDevice, s));
+            std::vector<const Vec *> ins(k);
+            for (int j = 0; j < k; ++j) ins[j] = &sol[j];
+            WL_TRY(blas_lincomb(geo, sc.coef, sc.coef + n_rhs * 16, ins.data(), k, sol[k], s));
+        }
+        for (int r = 0; r < n_rhs; ++r) std::memset(&st[r], 0, sizeof(wl_solver_stats));
+        WL_TRY(solve_one_mass(g, be, bo, sol[k], m, *p, bn2, x + im, n_mass, st, s));
+        WL_CUDA_TRY(cudaStreamSynchronize(s));
+        const double sec = tm.sec();
+        for (int r = 0; r < n_rhs; ++r) {
+            st[r].seconds = sec;
+            stats[(size_t)r * n_mass + im] = st[r];
+            if (st[r].status != WL_OK) worst = st[r].status;
+        }
+    }
+    return worst;
+}

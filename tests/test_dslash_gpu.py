@@ -1,0 +1,145 @@
+"""GPU parity of the hop / M / M_prec kernels against the FP64 oracle, through
+the C ABI (wilson_dslash, wilson_dslash_dag, wilson_hop, spinor import/export).
+Tolerances (relative l2): FP64 1e-12, FP32 1e-6, FP16 storage 5e-3."""
+import numpy as np
+import pytest
+import torch
+
+from helpers import TOL, rel
+from oracle import oracle as O
+from paper_1103_5103_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+LATTICES = [(2, 2, 2, 2), (4, 4, 4, 4), (4, 4, 4, 8), (6, 4, 4, 8), (8, 8, 8, 8), (4, 6, 2, 10)]
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_1103_5103_gb300 import api as A
+    return A
+
+
+def _field(dims, kind, seed=1):
+    return synth.unit_gauge_field(dims) if kind == "free" else synth.gauge_field(dims, 0.5, seed=seed)
+
+
+def _setup(api, dims, kind, antiperiodic=True, precs=("f64", "f32", "f16")):
+    U = _field(dims, kind)
+    lat = api.Lattice(dims, antiperiodic)
+    g = api.Gauge(lat, torch.from_numpy(U).cuda(), precs=precs)
+    return U, lat, g
+
+
+def _cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("dims", LATTICES)
+@pytest.mark.parametrize("kind", ["free", "random"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16"])
+def test_dslash_ops_vs_oracle(api, dims, kind, prec):
+    U, lat, g = _setup(api, dims, kind)
+    psi = synth.gaussian_source(dims, seed=5)
+    kappa = 0.123
+    dpsi = _cuda(psi)
+    out = torch.empty_like(dpsi)
+    for op, okind, par in [(api.OP_HOP, O.OP_HOP, 0.0), (api.OP_M, O.OP_MK, kappa), (api.OP_MPREC, O.OP_MPREC, kappa)]:
+        for dag in (False, True):
+            want = O.apply(okind, U, dims, psi, par, dagger=dag)
+            if op == api.OP_MPREC:
+                src = psi.copy()
+                src[O.parity_mask(dims)] = 0
+                want = O.apply(okind, U, dims, src, par, dagger=dag)
+            f = api.wilson_dslash_dag if dag else api.wilson_dslash
+            f(g, dpsi, out, kappa, prec, op)
+            torch.cuda.synchronize()
+            err = rel(out.cpu().numpy(), want)
+            assert err < TOL[prec], (op, dag, err)
+
+
+@pytest.mark.parametrize("antiperiodic", [True, False])
+def test_boundary_conditions(api, antiperiodic):
+    dims = (4, 4, 4, 6)
+    U, lat, g = _setup(api, dims, "random", antiperiodic)
+    psi = synth.z2_source(dims, seed=3)
+    out = torch.empty((lat.volume, 4, 3), dtype=torch.complex128, device="cuda")
+    api.wilson_dslash(g, _cuda(psi), out, 0.11, "f64", api.OP_M)
+    want = O.apply(O.OP_MK, U, dims, psi, 0.11, antiperiodic=antiperiodic)
+    assert rel(out.cpu().numpy(), want) < 1e-12
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16"])
+def test_internal_layout_roundtrip(api, prec):
+    dims = (6, 4, 4, 8)
+    lat = api.Lattice(dims)
+    psi = synth.gaussian_source(dims, seed=7)
+    d = _cuda(psi)
+    back = torch.zeros_like(d)
+    for par in (0, 1):
+        buf = lat.new_internal(prec)
+        lat.spinor_import(d, buf, prec, par)
+        lat.spinor_export(buf, back, prec, par)
+    torch.cuda.synchronize()
+    err = rel(back.cpu().numpy(), psi)
+    if prec == "f64":
+        assert err == 0.0
+    else:
+        assert err < {"f32": 1e-7, "f16": 1e-3}[prec], err
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16"])
+@pytest.mark.parametrize("parity", [0, 1])
+def test_wilson_hop_internal_xpay(api, prec, parity):
+    """out_p = x_p + coef * D_{p,1-p} in on internal buffers."""
+    dims = (8, 4, 4, 8)
+    U, lat, g = _setup(api, dims, "random")
+    psi = synth.gaussian_source(dims, seed=8)
+    xv = synth.z2_source(dims, seed=9)
+    coef = -0.37
+    odd = O.parity_mask(dims)
+    src = psi.copy()
+    src[odd == bool(1 - parity)] = 0            # keep the input parity 1-p only
+    want = xv + coef * O.hop(U, dims, src)
+    mask_out = odd if parity == 1 else ~odd
+    bi, bx, bo = lat.new_internal(prec), lat.new_internal(prec), lat.new_internal(prec)
+    lat.spinor_import(_cuda(psi), bi, prec, 1 - parity)
+    lat.spinor_import(_cuda(xv), bx, prec, parity)
+    api.wilson_hop(g, bi, bo, bx, coef, prec, parity)
+    out = torch.zeros((lat.volume, 4, 3), dtype=torch.complex128, device="cuda")
+    lat.spinor_export(bo, out, prec, parity)
+    torch.cuda.synchronize()
+    err = rel(out.cpu().numpy()[mask_out], want[mask_out])
+    assert err < TOL[prec], err
+
+
+def test_dslash_rejects_bad_arguments(api):
+    dims = (4, 4, 4, 4)
+    U, lat, g = _setup(api, dims, "free", precs=("f32",))
+    d = torch.zeros((lat.volume, 4, 3), dtype=torch.complex128, device="cuda")
+    o = torch.zeros_like(d)
+    with pytest.raises(api.WilsonError) as e:
+        api.wilson_dslash(g, d, o, 0.1, "f64", api.OP_M)    # no FP64 links in this handle
+    assert e.value.status == api.WL_ERR_ARG
+    with pytest.raises(api.WilsonError):
+        api.wilson_dslash(g, d, d, 0.1, "f32", api.OP_M)    # aliasing
+    with pytest.raises(api.WilsonError):
+        api.wilson_dslash(g, d, o, 0.1, "f32", 7)           # bad operator id
+
+
+def test_large_lattice_sampled_sites(api):
+    """16^3 x 32 FP32 M: compare sampled output sites with the oracle
+    computed site by site on a local patch."""
+    dims = (16, 16, 16, 32)
+    U = synth.gauge_field(dims, 0.5, seed=2)
+    lat = api.Lattice(dims)
+    g = api.Gauge(lat, _cuda(U), precs=("f32",))
+    psi = synth.gaussian_source(dims, seed=4)
+    out = torch.empty((lat.volume, 4, 3), dtype=torch.complex128, device="cuda")
+    api.wilson_dslash(g, _cuda(psi), out, 0.124, "f32", api.OP_M)
+    full = O.apply(O.OP_MK, U, dims, psi, 0.124)
+    o = out.cpu().numpy()
+    rng = np.random.default_rng(0)
+    sites = rng.integers(0, lat.volume, size=2000)
+    err = rel(o[sites], full[sites])
+    assert err < 1e-6

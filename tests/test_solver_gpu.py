@@ -1,0 +1,126 @@
+"""GPU solver parity: every mass reaches FP64 true relative residual <= 1e-10
+and the solution agrees with the FP64 oracle to 1e-8 (relative l2)."""
+import numpy as np
+import pytest
+import torch
+
+from helpers import rel
+from oracle import oracle as O
+from paper_1103_5103_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_1103_5103_gb300 import api as A
+    return A
+
+
+def _cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _gauge(api, dims, eps, seed, precs=("f64", "f32", "f16")):
+    U = synth.gauge_field(dims, eps, seed=seed)
+    lat = api.Lattice(dims)
+    return U, lat, api.Gauge(lat, _cuda(U), precs=precs)
+
+
+@pytest.mark.parametrize("inner", ["f64", "f32", "f16"])
+@pytest.mark.parametrize("mode", ["graph", "host"])
+def test_bicgstab_solve_vs_oracle(api, inner, mode):
+    dims = (4, 4, 4, 8)
+    U, lat, g = _gauge(api, dims, 0.3, 11)
+    b = synth.z2_source(dims, seed=12)
+    m0 = 0.1
+    x = torch.zeros((lat.volume, 4, 3), dtype=torch.complex128, device="cuda")
+    prm = api.params(inner_prec=inner, mode=api.MODE_GRAPH if mode == "graph" else api.MODE_HOST)
+    st = api.bicgstab_solve(g, _cuda(b), x, m0, prm)
+    assert st["status"] == 0 and st["true_relres"] <= 1e-10, st
+    ref, _ = O.eo_solve(U, dims, b, m0, tol=1e-13)
+    assert rel(x.cpu().numpy(), ref) < 1e-8
+    assert O.true_relres(U, dims, b, x.cpu().numpy(), m0) <= 1.1e-10
+
+
+@pytest.mark.parametrize("inner", ["f32", "f16"])
+def test_multimass_c1_config(api, inner):
+    """8^4, eps 0.3, point source, masses {0.5, 0.3, 0.2, 0.1}."""
+    dims = (8, 8, 8, 8)
+    U, lat, g = _gauge(api, dims, 0.3, 1)
+    b = synth.point_source(dims)
+    masses = [0.5, 0.3, 0.2, 0.1]
+    xs, stats = api.multimass_solve(g, [_cuda(b)], masses, api.params(inner_prec=inner))
+    ref, _ = O.multimass_solve(U, dims, b, masses, tol=1e-12)
+    for i, m in enumerate(masses):
+        st = stats[0][i]
+        assert st["status"] == 0 and st["true_relres"] <= 1e-10, st
+        assert abs(st["mass"] - m) == 0
+        assert rel(xs[0][i].cpu().numpy(), ref[i]) < 1e-8
+
+
+def test_multimass_batched_rhs_and_guesses(api):
+    """Several sources in one call, unordered masses, zero vs polynomial guess."""
+    dims = (4, 4, 4, 8)
+    U, lat, g = _gauge(api, dims, 0.5, 21)
+    bs = [synth.point_source(dims, 0, 0), synth.point_source(dims, 2, 1), synth.z2_source(dims, 22)]
+    masses = [0.2, 0.4, 0.05, 0.3]
+    for guess in (api.GUESS_ZERO, api.GUESS_POLY):
+        xs, stats = api.multimass_solve(g, [_cuda(b) for b in bs], masses, api.params(guess=guess))
+        for r, b in enumerate(bs):
+            for i, m in enumerate(masses):
+                assert stats[r][i]["status"] == 0 and stats[r][i]["true_relres"] <= 1e-10
+                ref, _ = O.eo_solve(U, dims, b, m, tol=1e-13)
+                assert rel(xs[r][i].cpu().numpy(), ref) < 1e-8
+
+
+def test_multimass_guess_reduces_iterations(api):
+    dims = (8, 8, 8, 8)
+    U, lat, g = _gauge(api, dims, 0.3, 31)
+    b = _cuda(synth.z2_source(dims, 32))
+    masses = [0.40, 0.35, 0.30, 0.25, 0.20]
+    _, s0 = api.multimass_solve(g, [b], masses, api.params(guess=api.GUESS_ZERO, inner_prec="f64"))
+    _, s1 = api.multimass_solve(g, [b], masses, api.params(guess=api.GUESS_POLY, inner_prec="f64"))
+    it0 = sum(s["iterations"] for s in s0[0])
+    it1 = sum(s["iterations"] for s in s1[0])
+    assert it1 < it0, (it0, it1)
+
+
+def test_bicgstab_m_vs_oracle(api):
+    dims = (4, 4, 4, 8)
+    U, lat, g = _gauge(api, dims, 0.5, 41, precs=("f64",))
+    b = synth.z2_source(dims, 42)
+    masses = [0.4, 0.25, 0.1, 0.05]
+    xs = [torch.empty((lat.volume, 4, 3), dtype=torch.complex128, device="cuda") for _ in masses]
+    stats = api.bicgstab_m_solve(g, _cuda(b), xs, masses, api.params(inner_prec="f64"))
+    ref, ost = O.bicgstab_m(U, dims, b, masses, tol=1e-12)
+    for i, m in enumerate(masses):
+        assert stats[i]["true_relres"] <= 1e-10, stats[i]
+        assert rel(xs[i].cpu().numpy(), ref[i]) < 1e-8
+    # the unshifted (lightest) mass needs the most iterations; heavier ones freeze earlier
+    its = [stats[i]["iterations"] for i in range(len(masses))]
+    assert its[3] == max(its) and its[0] <= its[3]
+    # iteration counts agree with the oracle's recursion (same arithmetic up to rounding)
+    assert abs(its[3] - ost["iterations"][3]) <= 2
+
+
+def test_solver_rejects_bad_arguments(api):
+    dims = (4, 4, 4, 4)
+    U, lat, g = _gauge(api, dims, 0.3, 1, precs=("f64", "f32"))
+    b = _cuda(synth.point_source(dims))
+    with pytest.raises(api.WilsonError):
+        api.multimass_solve(g, [b], [0.1, 0.1], api.params())           # duplicate masses
+    with pytest.raises(api.WilsonError):
+        api.multimass_solve(g, [b], [0.1], api.params(inner_prec="f16"))  # no FP16 links
+    with pytest.raises(api.WilsonError):
+        api.multimass_solve(g, [b], [-4.5], api.params())                 # 2 m0 + 8 <= 0
+
+
+def test_noconv_status_keeps_last_iterate(api):
+    dims = (4, 4, 4, 8)
+    U, lat, g = _gauge(api, dims, 0.3, 51)
+    b = _cuda(synth.z2_source(dims, 52))
+    x = torch.zeros_like(b)
+    st = api.bicgstab_solve(g, b, x, 0.05, api.params(max_iter=3, inner_prec="f64", graph_iters=1), check=False)
+    assert st["call_status"] == api.WL_ERR_NOCONV
+    assert 0 < st["true_relres"] < 1.0
