@@ -1,0 +1,364 @@
+#!/usr/bin/env python3
+"""Benchmark: multi-mass Wilson solve time to a 1e-10 true residual, and the
+hop (dslash) kernel's HBM bandwidth against the measured GB300 copy peak.
+
+One step = the paper's single-mass multi-mass scheme (even-odd
+preconditioning, FP64 defect correction around a reduced-precision
+BiCGstab, Lagrange initial guesses, masses heaviest first) for every source
+of the workload, all sources batched in one multimass_solve call.
+
+Default workload (--config c3): 24^3 x 64 lattice, synthetic SU(3) links
+exp(i 0.5 H), antiperiodic in time, 12 spin-colour point sources at site 0,
+8 masses m0 = 0.40 .. 0.05.  --config c2 selects 16^3 x 32, eps 0.5, one Z2
+source, the same 8 masses (its working set fits in the 129 MB L2).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+For N > 1 launch with torch.distributed.run; every rank solves its own
+replica of the workload (the solve does not shard: replicas only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "multi-mass solve time to 1e-10 true residual; dslash GB/s vs GB300 HBM peak"
+UNIT = "s"
+MASSES = [0.40, 0.35, 0.30, 0.25, 0.20, 0.15, 0.10, 0.05]
+CONFIGS = {
+    "c3": dict(name="24^3x64, 12 spin-colour point sources x 8 masses (m0 0.40..0.05), eps 0.5",
+               dims=(24, 24, 24, 64), eps=0.5, seed=3, sources="points12"),
+    "c2": dict(name="16^3x32, 1 Z2 source x 8 masses (m0 0.40..0.05), eps 0.5",
+               dims=(16, 16, 16, 32), eps=0.5, seed=2, sources="z2"),
+}
+# algorithmic bytes of one hop: per output site 8 links, per output site and
+# rhs one input spinor (each read once) and one output spinor
+LINK_B = {"f64": 96, "f32": 48, "f16": 24}
+SPINOR_B = {"f64": 192, "f32": 96, "f16": 52}
+# The reference arm cannot afford a full oracle solve; it times a sample of
+# oracle BiCGstab iterations and scales by this many inner iterations per
+# step (the paper scheme's FP32-inner count on the c3 workload, from the
+# optimised arm's own JSON line `iterations_per_step`).
+REF_ITERS_PER_STEP = {"c3": None, "c2": None}
+
+
+def sources(cfg):
+    from paper_1103_5103_gb300 import synth
+    d = cfg["dims"]
+    if cfg["sources"] == "points12":
+        return [synth.point_source(d, s, c) for s in range(4) for c in range(3)]
+    return [synth.z2_source(d, seed=3)]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1])]
+        mx = [num(r[2]) for r in rows if num(r[2])]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for n, v in zip(names, r[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def dist_setup():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, ws):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_sample(cfg, U, bs, target_s=15.0):
+    """Time FP64 oracle applications of M_prec (lightest mass, first source)
+    for about target_s seconds.  One BiCGstab iteration applies the operator
+    twice; its six vector updates are not timed (under 2% of an oracle
+    iteration).  Returns (seconds per iteration, applications, seconds)."""
+    from oracle import oracle as O
+    dims = cfg["dims"]
+    m = MASSES[-1]
+    bp = O.eo_source(U, dims, bs[0], m)
+    n, t = 0, 0.0
+    while t < target_s or n < 2:
+        t0 = time.perf_counter()
+        bp = O.apply(O.OP_MPREC, U, dims, bp, O.kappa(m))
+        t += time.perf_counter() - t0
+        n += 1
+    return 2.0 * t / n, n, t
+
+
+def run_reference(args, cfg):
+    ws, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
+    if rank != 0:
+        return
+    from paper_1103_5103_gb300 import synth
+    U = synth.gauge_field(cfg["dims"], cfg["eps"], seed=cfg["seed"])
+    bs = sources(cfg)
+    iters_per_step = REF_ITERS_PER_STEP.get(args.config)
+    if not iters_per_step:
+        print(json.dumps({"impl": "reference", "unavailable":
+                          "no iteration count recorded for this workload; the oracle cannot run a full step"}))
+        return
+    times = []
+    for k in range(args.warmup + args.steps):
+        s_it, n, dt = oracle_sample(cfg, U, bs, target_s=max(5.0, 90.0 / (args.warmup + args.steps)))
+        if k >= args.warmup:
+            times.append(s_it * iters_per_step)
+    v = float(np.mean(times))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": cfg["name"]},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": v, "unit": UNIT,
+                             "sample": f"FP64 oracle M_prec applications timed on one host core (2 per "
+                                       f"BiCGstab iteration), scaled by {iters_per_step} inner iterations per step"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_ours(args, cfg):
+    import torch
+    from paper_1103_5103_gb300 import api, synth
+
+    ws, rank, local = dist_setup()
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    dims = cfg["dims"]
+    t0 = time.time()
+    U = synth.gauge_field(dims, cfg["eps"], seed=cfg["seed"])
+    bs_h = sources(cfg)
+    gen_s = time.time() - t0
+    lat = api.Lattice(dims)
+    g = api.Gauge(lat, torch.from_numpy(U).to(dev))
+    V = lat.volume
+    nr, nm = len(bs_h), len(MASSES)
+    bs = [torch.from_numpy(b).to(dev) for b in bs_h]
+    xs = [[torch.empty((V, 4, 3), dtype=torch.complex128, device=dev) for _ in MASSES] for _ in bs]
+    prm = api.params(inner_prec=args.inner, rhs_block=args.rhs_block)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        _, st = api.multimass_solve(g, bs, MASSES, prm, xs=xs)
+        return st
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # timed region: flush L2 before each step (inputs are also larger than L2)
+    barrier(ws)
+    torch.cuda.synchronize()
+    api.profile_enable(g, True)
+    launches0 = api.launch_count()
+    clocks = ClockSampler(dev.index or 0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    step_ms = []
+    all_stats = None
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        all_stats = step()
+        b.record(stream)
+        b.synchronize()
+        step_ms.append(a.elapsed_time(b))
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = api.launch_count() - launches0
+    prof = api.profile_read(g)[args.inner]
+    api.profile_enable(g, False)
+    barrier(ws)
+    t_step = max_over_ranks(float(np.mean(step_ms)) / 1e3, ws)
+
+    # end to end through the public API with pinned host buffers
+    bs_pin = [torch.from_numpy(b).pin_memory() for b in bs_h]
+    xs_pin = [[torch.empty((V, 4, 3), dtype=torch.complex128).pin_memory() for _ in MASSES] for _ in bs_h]
+    h2d = sum(b.numel() * 16 for b in bs_pin)
+    d2h = sum(x.numel() * 16 for row in xs_pin for x in row)
+    e2e_ms = []
+    for _ in range(max(1, args.steps)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for bd, bp in zip(bs, bs_pin):
+            bd.copy_(bp, non_blocking=True)
+        _, st = api.multimass_solve(g, bs, MASSES, prm, xs=xs)
+        for row_d, row_p in zip(xs, xs_pin):
+            for xd, xp in zip(row_d, row_p):
+                xp.copy_(xd, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    t_e2e = max_over_ranks(float(np.mean(e2e_ms)) / 1e3, ws)
+
+    peak, peak_kind = measured_peaks()
+    Vh = V // 2
+    # hop roofline from the live event timings of the solve's own hop launches
+    if prof["launches"]:
+        per_launch_sites = prof["sites"] / prof["launches"]
+        per_launch_site_rhs = prof["site_rhs"] / prof["launches"]
+        bytes_launch = per_launch_sites * 8 * LINK_B[args.inner] + per_launch_site_rhs * 2 * SPINOR_B[args.inner]
+        avg_s = prof["ms"] / prof["launches"] / 1e3
+        achieved = bytes_launch / avg_s / 1e9
+        hop_gflops = 1320 * per_launch_site_rhs / avg_s / 1e9
+    else:
+        bytes_launch = avg_s = achieved = hop_gflops = None
+    iters = sum(st["iterations"] for row in all_stats for st in row)
+    worst = max(st["true_relres"] for row in all_stats for st in row)
+    per_mass = {f"{m:.2f}": {"iterations": int(sum(all_stats[r][i]["iterations"] for r in range(nr))),
+                             "restarts": int(sum(all_stats[r][i]["restarts"] for r in range(nr))),
+                             "seconds": float(all_stats[0][i]["seconds"]),
+                             "max_true_relres": float(max(all_stats[r][i]["true_relres"] for r in range(nr)))}
+                for i, m in enumerate(MASSES)}
+
+    line = {
+        "metric": METRIC, "value": t_step, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": args.inner, "data": "synthetic",
+        "config": {"workload": cfg["name"], "sources": nr, "masses": MASSES, "inner_prec": args.inner,
+                   "tol": 1e-10, "l2": "flushed (256 MB write) before every step; working set > L2",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "e2e": {"value": t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "kernel": f"k_hop<{args.inner}> (D_oe p, first hop of each BiCGstab iteration)",
+                     "peak_kind": peak_kind, "bytes_per_launch": bytes_launch,
+                     "avg_launch_us": avg_s * 1e6 if avg_s else None, "timed_launches": prof["launches"],
+                     "gflops_1320": hop_gflops},
+        "clocks": clk,
+        "iterations_per_step": int(iters), "max_true_relres": worst, "per_mass": per_mass,
+        "gauge_generation_s": gen_s,
+    }
+    if rank == 0 and ws == 1 and not args.no_baseline:
+        # FP64 BiCGstab-M on the same GPU, same sources and masses (context for
+        # the paper's comparison; not part of the timed step)
+        t_m, it_m, worst_m = 0.0, 0, 0.0
+        nsrc = min(nr, args.baseline_sources)
+        for r in range(nsrc):
+            xm = [torch.empty((V, 4, 3), dtype=torch.complex128, device=dev) for _ in MASSES]
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            stm = api.bicgstab_m_solve(g, bs[r], xm, MASSES, api.params(), check=False)
+            torch.cuda.synchronize()
+            t_m += time.perf_counter() - t0
+            it_m += max(s["iterations"] for s in stm)
+            worst_m = max(worst_m, max(s["true_relres"] for s in stm))
+            del xm
+        line["bicgstab_m_fp64"] = {"seconds_per_step": t_m * nr / nsrc, "sources_run": nsrc,
+                                   "iterations_per_source": it_m / nsrc, "max_true_relres": worst_m,
+                                   "speedup_of_single_mass_scheme": (t_m * nr / nsrc) / t_step}
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        s_it, n_it, dt = oracle_sample(cfg, U, bs_h, target_s=args.cpu_seconds)
+        line["cpu_baseline"] = {"value": s_it * iters, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{n_it} FP64 oracle applications of M_prec (lightest mass, source 0) "
+                                          f"took {dt:.1f} s on one host core = {s_it:.2f} s per BiCGstab "
+                                          f"iteration (2 applications); scaled by the step's {iters} inner "
+                                          f"iterations"}
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", choices=sorted(CONFIGS), default="c3")
+    ap.add_argument("--inner", choices=["f32", "f16", "f64"], default="f32")
+    ap.add_argument("--rhs-block", type=int, default=0)
+    ap.add_argument("--baseline-sources", type=int, default=12)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-baseline", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    cfg = CONFIGS[args.config]
+    if args.impl == "reference":
+        run_reference(args, cfg)
+    else:
+        run_ours(args, cfg)
+
+
+if __name__ == "__main__":
+    main()

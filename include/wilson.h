@@ -154,6 +154,16 @@ int wl_gauge_destroy(wl_gauge *g);
 int wilson_hop(wl_gauge *g, const void *in, void *out, const void *x, double coef, int prec,
                int out_parity, int dagger, void *stream);
 
+/* Batched hop over n_rhs internal spinors of one parity laid out rhs_stride
+ * bytes apart (rhs_stride >= wl_spinor_bytes, a multiple of 256):
+ *   out_r = x_r + coef * D_{p,1-p} in_r   (x may be NULL: out_r = coef D in_r).
+ * Thread blocks are ordered with the rhs index fastest, so the blocks that
+ * read a given link run together and the link comes from HBM once per
+ * launch; rhs_block (1, 2 or 4; 0 = 1) rhs are handled by one thread, which
+ * then loads each link into registers once for all of them. */
+int wilson_hop_multi(wl_gauge *g, const void *in, void *out, const void *x, double coef, int prec,
+                     int out_parity, int dagger, int n_rhs, size_t rhs_stride, int rhs_block, void *stream);
+
 /* Canonical full-lattice operator application (complex128 in and out):
  *   WL_OP_HOP   out = D in
  *   WL_OP_M     out = in - kappa D in                        (Eq. 3, kappa form)
@@ -204,6 +214,32 @@ int bicgstab_m_solve(wl_gauge *g, const void *b, void *const *x, const double *m
  * Synchronises the stream. */
 int multimass_solve(wl_gauge *g, const void *const *b, void *const *x, int n_rhs, const double *m0,
                     int n_mass, const wl_solver_params *p, wl_solver_stats *stats, void *stream);
+
+/* ------------------------------------------------------------ profiling */
+
+/* Live timing of the dominant kernel, the hop D_oe p that opens every inner
+ * BiCGstab iteration.  While profiling is on, each iteration records a pair
+ * of CUDA events around that launch on the solve's stream (inside the
+ * captured graph in WL_MODE_GRAPH); the solver adds up their elapsed times
+ * at the host synchronisation that already follows every block of
+ * iterations.  Only iterations in which every right-hand side was still
+ * active are counted, so each counted launch processed exactly
+ * n_rhs * V/2 output sites. */
+typedef struct {
+    long long launches;    /* counted hop launches                               */
+    double    ms;          /* summed CUDA-event durations of those launches      */
+    double    site_rhs;    /* sum over counted launches of (V/2) * n_rhs          */
+    double    sites;       /* sum over counted launches of V/2 (link-reuse model) */
+} wl_kernel_profile;
+
+/* Reset the counters of g and start (on = 1) or stop (on = 0) profiling. */
+int wl_profile_enable(wl_gauge *g, int on);
+/* Counters per inner precision: out[0] FP64, out[1] FP32, out[2] FP16. */
+int wl_profile_read(wl_gauge *g, wl_kernel_profile out[3]);
+
+/* Number of kernels this library has launched in the process so far (direct
+ * launches plus, for every replay of a captured graph, its kernel nodes). */
+int wl_launch_count(long long *out);
 
 #ifdef __cplusplus
 }

@@ -60,6 +60,13 @@ class SolverStats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class KernelProfile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_longlong), ("ms", _dbl), ("site_rhs", _dbl), ("sites", _dbl)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 def _sig(name, args, res=_int):
     f = getattr(_lib, name)
     f.argtypes = args
@@ -77,9 +84,13 @@ _sig("wl_spinor_export", [_vp, _vp, _vp, _int, _int, _vp])
 _sig("wl_gauge_create", [_vp, _vp, ctypes.c_uint, _vp, ctypes.POINTER(_vp)])
 _sig("wl_gauge_destroy", [_vp])
 _sig("wilson_hop", [_vp, _vp, _vp, _vp, _dbl, _int, _int, _int, _vp])
+_sig("wilson_hop_multi", [_vp, _vp, _vp, _vp, _dbl, _int, _int, _int, _int, ctypes.c_size_t, _int, _vp])
 _sig("wilson_dslash", [_vp, _vp, _vp, _dbl, _int, _int, _vp])
 _sig("wilson_dslash_dag", [_vp, _vp, _vp, _dbl, _int, _int, _vp])
 _sig("bicgstab_solve", [_vp, _vp, _vp, _dbl, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats), _vp])
+_sig("wl_launch_count", [ctypes.POINTER(ctypes.c_longlong)])
+_sig("wl_profile_enable", [_vp, _int])
+_sig("wl_profile_read", [_vp, ctypes.POINTER(KernelProfile)])
 _sig("bicgstab_m_solve", [_vp, _vp, ctypes.POINTER(_vp), ctypes.POINTER(_dbl), _int, ctypes.POINTER(SolverParams),
                           ctypes.POINTER(SolverStats), _vp])
 _sig("multimass_solve", [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _int, ctypes.POINTER(_dbl), _int,
@@ -209,6 +220,14 @@ def wilson_hop(g: Gauge, inp: torch.Tensor, out: torch.Tensor, x, coef: float, p
                            int(out_parity), int(dagger), _stream(stream)))
 
 
+def hop_batch(g: Gauge, inp: torch.Tensor, out: torch.Tensor, nrhs: int, rhs_stride: int, coef: float, prec,
+              out_parity: int, rhs_block: int = 1, x=None, dagger: bool = False, stream=None):
+    """wilson_hop_multi: out_r = x_r + coef D in_r for nrhs internal spinors rhs_stride bytes apart."""
+    _check(_lib.wilson_hop_multi(g.handle, _ptr(inp), _ptr(out), None if x is None else _ptr(x), float(coef),
+                                 _prec(prec), int(out_parity), int(dagger), int(nrhs), int(rhs_stride),
+                                 int(rhs_block), _stream(stream)))
+
+
 def wilson_dslash(g: Gauge, inp: torch.Tensor, out: torch.Tensor, kappa: float, prec, op=OP_M, stream=None):
     V = g.lat.volume
     _check(_lib.wilson_dslash(g.handle, _canon(inp, V, "in"), _canon(out, V, "out"), float(kappa), _prec(prec),
@@ -269,3 +288,22 @@ def bicgstab_m_solve(g: Gauge, b: torch.Tensor, xs, masses, prm: SolverParams | 
     if check:
         _check(s)
     return [st[i].as_dict() for i in range(nm)]
+
+
+def profile_enable(g: Gauge, on: bool = True):
+    """Reset the live hop-timing counters of g and switch them on or off."""
+    _check(_lib.wl_profile_enable(g.handle, int(on)))
+
+
+def profile_read(g: Gauge) -> dict:
+    """{'f64': {...}, 'f32': {...}, 'f16': {...}} hop launch counters."""
+    arr = (KernelProfile * 3)()
+    _check(_lib.wl_profile_read(g.handle, arr))
+    return {"f64": arr[0].as_dict(), "f32": arr[1].as_dict(), "f16": arr[2].as_dict()}
+
+
+def launch_count() -> int:
+    """Kernels launched by the library in this process (wl_launch_count)."""
+    n = ctypes.c_longlong()
+    _check(_lib.wl_launch_count(ctypes.byref(n)))
+    return n.value

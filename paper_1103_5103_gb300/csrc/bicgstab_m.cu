@@ -397,6 +397,7 @@ extern "C" int bicgstab_m_solve(wl_gauge *g, const void *b, void *const *x, cons
     if (ns) WL_CUDA_TRY(cudaMemcpyAsync(sh, hsh.data(), sizeof(ShiftState) * ns, cudaMemcpyHostToDevice, s));
     // iterate the unshifted system to half the tolerance (iterated/true gap)
     k_m_init<<<1, 1, 0, s>>>(st, d_norm, 0.25 * hm.target2);
+    note_launch(s);
     WL_CUDA_TRY(cudaStreamSynchronize(s));
 
     const double a1 = ms + 4.0;
@@ -408,13 +409,20 @@ extern "C" int bicgstab_m_solve(wl_gauge *g, const void *b, void *const *x, cons
         WL_TRY(hop_reduce(g, 0, po, pe, a1, ve, rhe, -0.5, WL_EVEN, 0, st, partials, 0, 2 * nsb, q));
         WL_TRY(hop_reduce(g, 0, pe, po, a1, vo, rho, -0.5, WL_ODD, 0, st, partials, nsb, 2 * nsb, q));
         k_m_s<<<2 * nsb, kBlock, 0, q>>>(geo, nsb, r, v, sv, st);
+        note_launch(q);
         // t = A s, <t,s>, <t,t> -> omega
         WL_TRY(hop_reduce(g, 1, so, se, a1, te, rhe, -0.5, WL_EVEN, 0, st, partials, 0, 2 * nsb, q));
         WL_TRY(hop_reduce(g, 1, se, so, a1, to, rho, -0.5, WL_ODD, 0, st, partials, nsb, 2 * nsb, q));
-        if (ns) k_shift_a<<<1, 32, 0, q>>>(sh, ns, st, mst);
+        if (ns) {
+            k_shift_a<<<1, 32, 0, q>>>(sh, ns, st, mst);
+            note_launch(q);
+        }
         k_m_update<<<2 * nsb, kBlock, 0, q>>>(geo, nsb, xv, pv, sv, t, r, rhat, shv, sh, ns, st, partials);
         k_shift_b<<<1, 32, 0, q>>>(sh, ns, st, mst);
         k_m_p<<<2 * nsb, kBlock, 0, q>>>(geo, nsb, r, pv, v, shv, sh, ns, st);
+        note_launch(q);
+        note_launch(q);
+        note_launch(q);
         WL_CUDA_TRY(cudaGetLastError());
         return WL_OK;
     };
@@ -423,6 +431,7 @@ extern "C" int bicgstab_m_solve(wl_gauge *g, const void *b, void *const *x, cons
     const int K = p->mode == WL_MODE_GRAPH ? std::max(1, p->graph_iters) : 1;
     cudaGraphExec_t exec = nullptr;
     cudaStream_t cap = nullptr;
+    size_t graph_nodes = 0;
     if (p->mode == WL_MODE_GRAPH) {
         WL_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
         cudaGraph_t graph = nullptr;
@@ -433,7 +442,10 @@ extern "C" int bicgstab_m_solve(wl_gauge *g, const void *b, void *const *x, cons
             e = cudaStreamEndCapture(cap, &graph);
         }
         if (e == cudaSuccess && status == WL_OK) e = cudaGraphInstantiate(&exec, graph, 0);
-        if (graph) cudaGraphDestroy(graph);
+        if (graph) {
+            cudaGraphGetNodes(graph, nullptr, &graph_nodes);
+            cudaGraphDestroy(graph);
+        }
         if (e != cudaSuccess || status != WL_OK) {
             cudaStreamDestroy(cap);
             if (status != WL_OK) return status;
@@ -447,6 +459,7 @@ extern "C" int bicgstab_m_solve(wl_gauge *g, const void *b, void *const *x, cons
         if (exec) {
             cudaError_t e = cudaGraphLaunch(exec, s);
             if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); status = WL_ERR_CUDA; break; }
+            add_launches((long long)graph_nodes);
         } else {
             status = iteration(s);
             if (status != WL_OK) break;

@@ -65,6 +65,7 @@ int blas_s_update(const Geom &g, const Vec &r, const Vec &v, const Vec &s_out, B
     case WL_F16: k_s_update<WL_F16><<<grid_of(g, r.nrhs), kBlock, 0, s>>>(g, r, v, s_out, state); break;
     }
     WL_CUDA_TRY(cudaGetLastError());
+    note_launch(s);
     return WL_OK;
 }
 
@@ -167,6 +168,7 @@ int blas_xr_update(const Geom &g, const Vec &x, const Vec &p, const Vec &sv, con
         return WL_ERR_ARG;
     }
     WL_CUDA_TRY(cudaGetLastError());
+    note_launch(s);
     return WL_OK;
 }
 
@@ -197,6 +199,7 @@ int blas_p_update(const Geom &g, const Vec &r, const Vec &p, const Vec &v, BiSta
     case WL_F16: k_p_update<WL_F16><<<grid_of(g, r.nrhs), kBlock, 0, s>>>(g, r, p, v, state); break;
     }
     WL_CUDA_TRY(cudaGetLastError());
+    note_launch(s);
     return WL_OK;
 }
 
@@ -265,6 +268,7 @@ int blas_restart(const Geom &g, const Vec &r64, const Vec &r, const Vec &rhat, c
         return WL_ERR_ARG;
     }
     WL_CUDA_TRY(cudaGetLastError());
+    note_launch(s);
     return WL_OK;
 }
 
@@ -290,6 +294,7 @@ int blas_accum(const Geom &g, const Vec &e, const Vec &x64, const int *active, c
     if (e.prec == WL_F64) k_accum<WL_F64><<<gr, kBlock, 0, s>>>(g, e, x64, active);
     else k_accum<WL_F32><<<gr, kBlock, 0, s>>>(g, e, x64, active);
     WL_CUDA_TRY(cudaGetLastError());
+    note_launch(s);
     return WL_OK;
 }
 
@@ -324,6 +329,7 @@ int blas_norm2(const Geom &g, const Vec &a, double *out_dev, double *partials, u
     case WL_F16: k_norm2<WL_F16><<<gr, kBlock, 0, s>>>(g, a, out_dev, partials, tickets); break;
     }
     WL_CUDA_TRY(cudaGetLastError());
+    note_launch(s);
     return WL_OK;
 }
 
@@ -360,6 +366,7 @@ int blas_lincomb(const Geom &g, const double *cre_dev, const double *cim_dev, co
     for (int j = 0; j < k; ++j) li.p[j] = in[j]->ptr;
     k_lincomb<<<grid_of(g, out.nrhs), kBlock, 0, s>>>(g, li, k, out.rhs_bytes, out.nrhs, cre_dev, cim_dev, out);
     WL_CUDA_TRY(cudaGetLastError());
+    note_launch(s);
     return WL_OK;
 }
 
@@ -382,7 +389,7 @@ int blas_convert(const Geom &g, const Vec &in, const Vec &out, cudaStream_t s)
 {
     const int gr = grid_of(g, out.nrhs);
 #define WL_CONV(A, B) \
-    if (in.prec == A && out.prec == B) { k_convert<A, B><<<gr, kBlock, 0, s>>>(g, in, out); WL_CUDA_TRY(cudaGetLastError()); return WL_OK; }
+    if (in.prec == A && out.prec == B) { k_convert<A, B><<<gr, kBlock, 0, s>>>(g, in, out); WL_CUDA_TRY(cudaGetLastError()); note_launch(s); return WL_OK; }
     WL_CONV(WL_F64, WL_F64) WL_CONV(WL_F64, WL_F32) WL_CONV(WL_F64, WL_F16)
     WL_CONV(WL_F32, WL_F64) WL_CONV(WL_F32, WL_F32) WL_CONV(WL_F32, WL_F16)
     WL_CONV(WL_F16, WL_F64) WL_CONV(WL_F16, WL_F32) WL_CONV(WL_F16, WL_F16)

@@ -33,6 +33,12 @@ void set_error(const std::string &msg);
 
 inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// Kernel launch accounting (wl_launch_count): note_launch(s) after a launch
+// on stream s counts it unless s is being captured into a graph; graph
+// replays add their kernel-node count through add_launches.
+void note_launch(cudaStream_t s);
+void add_launches(long long n);
+
 // ---------------------------------------------------------------- geometry
 
 // Lattice geometry in the form the kernels need.  Sites of one parity are

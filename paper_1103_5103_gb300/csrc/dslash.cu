@@ -342,8 +342,10 @@ static void launch_hop_t(const HopArgs &a, const EpiStore &e, cudaStream_t s)
 template <int P, bool DAG>
 static void launch_hop_nb(int nb, HopArgs a, const EpiStore &e, cudaStream_t s)
 {
-    if (nb >= 4) { a.ngroups = (a.nrhs + 3) / 4; launch_hop_t<P, DAG, 4>(a, e, s); }
-    else if (nb == 2) { a.ngroups = (a.nrhs + 1) / 2; launch_hop_t<P, DAG, 2>(a, e, s); }
+    if constexpr (P != WL_F64) {  // FP64 with 4 rhs per thread spills registers
+        if (nb >= 4) { a.ngroups = (a.nrhs + 3) / 4; launch_hop_t<P, DAG, 4>(a, e, s); return; }
+    }
+    if (nb >= 2) { a.ngroups = (a.nrhs + 1) / 2; launch_hop_t<P, DAG, 2>(a, e, s); }
     else { a.ngroups = a.nrhs; launch_hop_t<P, DAG, 1>(a, e, s); }
 }
 
@@ -382,6 +384,7 @@ int hop_ex(wl_gauge *g, const Vec &in, const Vec &out, const Vec *x1, double a1,
     default: set_error("hop: bad precision"); return WL_ERR_ARG;
     }
     WL_CUDA_TRY(cudaGetLastError());
+    note_launch(s);
     return WL_OK;
 }
 
@@ -433,6 +436,7 @@ static int hop_reduce_k(wl_gauge *g, const Vec &tmp, const Vec &xin, double a1, 
     default: set_error("hop_reduce: bad precision"); return WL_ERR_ARG;
     }
     WL_CUDA_TRY(cudaGetLastError());
+    note_launch(s);
     return WL_OK;
 }
 
@@ -466,6 +470,27 @@ extern "C" int wilson_hop(wl_gauge *g, const void *in, void *out, const void *x,
     vo.ptr = out;
     vx.ptr = const_cast<void *>(x);
     return hop(g, vi, vo, x ? &vx : nullptr, coef, out_parity, dagger ? 1 : 0, 1, as_stream(stream));
+}
+
+extern "C" int wilson_hop_multi(wl_gauge *g, const void *in, void *out, const void *x, double coef, int prec,
+                                int out_parity, int dagger, int n_rhs, size_t rhs_stride, int rhs_block,
+                                void *stream)
+{
+    if (!g || !in || !out || !valid_prec(prec) || (out_parity != 0 && out_parity != 1) || in == out || n_rhs < 1 ||
+        rhs_block < 0 || rhs_block > 4 || rhs_block == 3 || (rhs_stride & 255) ||
+        rhs_stride < spinor_bytes(g->lat->geom, prec)) {
+        set_error("wilson_hop_multi: bad argument");
+        return WL_ERR_ARG;
+    }
+    Vec vi, vo, vx;
+    vi.ptr = const_cast<void *>(in);
+    vo.ptr = out;
+    vx.ptr = const_cast<void *>(x);
+    vi.prec = vo.prec = vx.prec = prec;
+    vi.nrhs = vo.nrhs = vx.nrhs = n_rhs;
+    vi.rhs_bytes = vo.rhs_bytes = vx.rhs_bytes = rhs_stride;
+    const int nb = (prec == WL_F64 && rhs_block > 2) ? 2 : rhs_block;
+    return hop(g, vi, vo, x ? &vx : nullptr, coef, out_parity, dagger ? 1 : 0, nb, as_stream(stream));
 }
 
 static int dslash_common(wl_gauge *g, const void *in, void *out, double kappa, int prec, int op, int dagger,

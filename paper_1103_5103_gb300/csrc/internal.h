@@ -54,6 +54,8 @@ struct wl_gauge {
     void *links[3][2];  // [prec index][parity] -> 4 directions of 12-real links
     wl::Workspace ws;
     std::mutex mu;      // one solve at a time per handle (shared workspace)
+    int profiling = 0;
+    wl_kernel_profile prof[3] = {};
 };
 
 namespace wl {

@@ -1,5 +1,6 @@
 // Geometry, handles, workspace and the canonical <-> internal layout kernels
 // (Section 4, Eqs. 7-8: structure-of-arrays fields, even sites first).
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -9,8 +10,18 @@
 namespace wl {
 
 static thread_local std::string g_last_error;
+static std::atomic<long long> g_launches{0};
 
 void set_error(const std::string &msg) { g_last_error = msg; }
+
+void note_launch(cudaStream_t s)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive) return;
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+void add_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 size_t spinor_bytes(const Geom &g, int prec) { return (size_t)spinor_site_bytes(prec) * g.stride; }
 
@@ -120,6 +131,7 @@ static int launch_import(const Geom &g, const void *canon, void *out, int parity
     const int th = 128, bl = (g.Vh + th - 1) / th;
     k_import<P><<<bl, th, 0, s>>>(g, static_cast<const double2 *>(canon), out, parity);
     WL_CUDA_TRY(cudaGetLastError());
+    note_launch(s);
     return WL_OK;
 }
 
@@ -129,6 +141,7 @@ static int launch_export(const Geom &g, const void *in, void *canon, int parity,
     const int th = 128, bl = (g.Vh + th - 1) / th;
     k_export<P><<<bl, th, 0, s>>>(g, in, static_cast<double2 *>(canon), parity);
     WL_CUDA_TRY(cudaGetLastError());
+    note_launch(s);
     return WL_OK;
 }
 
@@ -161,6 +174,13 @@ using namespace wl;
 // ---------------------------------------------------------------- C ABI
 
 extern "C" const char *wl_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" int wl_launch_count(long long *out)
+{
+    if (!out) { set_error("wl_launch_count: NULL"); return WL_ERR_ARG; }
+    *out = g_launches.load();
+    return WL_OK;
+}
 
 extern "C" int wl_params_default(wl_solver_params *p)
 {
@@ -276,6 +296,7 @@ extern "C" int wl_gauge_create(wl_lattice *lat, const void *U, unsigned prec_mas
             if (P == WL_F64) k_pack_links<WL_F64><<<grid, 128, 0, s>>>(geo, Uc, g->links[pi][par], par);
             if (P == WL_F32) k_pack_links<WL_F32><<<grid, 128, 0, s>>>(geo, Uc, g->links[pi][par], par);
             if (P == WL_F16) k_pack_links<WL_F16><<<grid, 128, 0, s>>>(geo, Uc, g->links[pi][par], par);
+            note_launch(s);
         }
     }
     cudaError_t e = cudaStreamSynchronize(s);

@@ -108,13 +108,16 @@ static int make_inner(wl_gauge *g, int prec, int nrhs, double kappa, Inner *in, 
     return get_scratch(g, nrhs, &in->sc, s);
 }
 
-// Enqueue one BiCGstab iteration for every rhs.
-static int inner_iteration(Inner &in, int rhs_block, cudaStream_t s)
+// Enqueue one BiCGstab iteration for every rhs.  ev (optional) is a pair of
+// events recorded around the first hop for live kernel timing.
+static int inner_iteration(Inner &in, int rhs_block, cudaStream_t s, cudaEvent_t *ev = nullptr)
 {
     const Geom &geo = in.g->lat->geom;
     const double k2 = in.kappa * in.kappa;
     const int nsb = site_blocks(geo);
+    if (ev) WL_CUDA_TRY(cudaEventRecord(ev[0], s));
     WL_TRY(hop_ex(in.g, in.p, in.tmp, nullptr, 0.0, nullptr, 0.0, 1.0, WL_ODD, 0, rhs_block, in.sc.state, s));
+    if (ev) WL_CUDA_TRY(cudaEventRecord(ev[1], s));
     WL_TRY(hop_reduce(in.g, 0, in.tmp, in.p, 1.0, in.v, in.rhat, -k2, WL_EVEN, 0, in.sc.state, in.sc.partials, 0,
                       nsb, s));
     WL_TRY(blas_s_update(geo, in.r, in.v, in.s, in.sc.state, s));
@@ -137,20 +140,42 @@ static int run_inner(Inner &in, const wl_solver_params &prm, int max_iter, std::
     WL_TRY(pin.reserve(sizeof(BiState) * nrhs));
     BiState *hs = static_cast<BiState *>(pin.p);
     host_state.resize(nrhs);
-    const int K = std::max(1, prm.graph_iters);
+    const int K = prm.mode == WL_MODE_GRAPH ? std::max(1, prm.graph_iters) : 1;
     cudaGraphExec_t exec = nullptr;
     cudaStream_t cap = nullptr;
     int status = WL_OK;
+    // live timing of the first hop of each iteration (wl_profile_enable)
+    const bool prof = in.g->profiling != 0;
+    std::vector<cudaEvent_t> ev(prof ? 2 * K : 0);
+    for (auto &e : ev) WL_CUDA_TRY(cudaEventCreate(&e));
+    struct EvFree {
+        std::vector<cudaEvent_t> &v;
+        ~EvFree() { for (auto e : v) cudaEventDestroy(e); }
+    } ev_free{ev};
+    std::vector<int> it_before(nrhs, 0);
+    long long graph_kernels = 0;
     if (prm.mode == WL_MODE_GRAPH) {
         WL_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            for (int k = 0; k < K && status == WL_OK; ++k) status = inner_iteration(in, rb, cap);
+            for (int k = 0; k < K && status == WL_OK; ++k)
+                status = inner_iteration(in, rb, cap, prof ? &ev[2 * k] : nullptr);
             e = cudaStreamEndCapture(cap, &graph);
         }
         if (e == cudaSuccess && status == WL_OK) e = cudaGraphInstantiate(&exec, graph, 0);
-        if (graph) cudaGraphDestroy(graph);
+        if (graph) {
+            // kernel nodes only (event-record nodes are not launches)
+            size_t n = 0;
+            cudaGraphGetNodes(graph, nullptr, &n);
+            std::vector<cudaGraphNode_t> nodes(n);
+            if (n) cudaGraphGetNodes(graph, nodes.data(), &n);
+            for (auto nd : nodes) {
+                cudaGraphNodeType t;
+                if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++graph_kernels;
+            }
+            cudaGraphDestroy(graph);
+        }
         if (e != cudaSuccess || status != WL_OK) {
             if (exec) cudaGraphExecDestroy(exec);
             cudaStreamDestroy(cap);
@@ -170,9 +195,10 @@ static int run_inner(Inner &in, const wl_solver_params &prm, int max_iter, std::
                 status = WL_ERR_CUDA;
                 break;
             }
+            add_launches(graph_kernels);
             done_iters += K;
         } else {
-            status = inner_iteration(in, rb, s);
+            status = inner_iteration(in, rb, s, prof ? &ev[0] : nullptr);
             if (status != WL_OK) break;
             done_iters += 1;
         }
@@ -182,6 +208,28 @@ static int run_inner(Inner &in, const wl_solver_params &prm, int max_iter, std::
             set_error(std::string("inner loop: ") + cudaGetErrorString(e));
             status = WL_ERR_CUDA;
             break;
+        }
+        if (prof) {
+            // iterations of this block in which every rhs ran: the smallest
+            // per-rhs advance among rhs that were active
+            int full = K;
+            int n_act = 0;
+            for (int r = 0; r < nrhs; ++r) {
+                const int d = hs[r].iters - it_before[r];
+                if (d > 0 || !hs[r].done) { full = std::min(full, d); ++n_act; }
+                it_before[r] = hs[r].iters;
+            }
+            wl_kernel_profile &P = in.g->prof[prec_index(in.prec)];
+            const double vh = (double)in.g->lat->geom.Vh;
+            for (int k = 0; k < full && n_act == nrhs; ++k) {
+                float ms = 0.f;
+                if (cudaEventElapsedTime(&ms, ev[2 * k], ev[2 * k + 1]) == cudaSuccess) {
+                    P.launches += 1;
+                    P.ms += ms;
+                    P.site_rhs += vh * nrhs;
+                    P.sites += vh;
+                }
+            }
         }
         bool all = true;
         for (int r = 0; r < nrhs; ++r) all &= hs[r].done != 0;
@@ -374,6 +422,23 @@ static int check_params(const wl_gauge *g, const wl_solver_params *p)
 using namespace wl;
 
 // ---------------------------------------------------------------- C ABI
+
+extern "C" int wl_profile_enable(wl_gauge *g, int on)
+{
+    if (!g) { set_error("wl_profile_enable: NULL"); return WL_ERR_ARG; }
+    std::lock_guard<std::mutex> lock(g->mu);
+    g->profiling = on ? 1 : 0;
+    std::memset(g->prof, 0, sizeof(g->prof));
+    return WL_OK;
+}
+
+extern "C" int wl_profile_read(wl_gauge *g, wl_kernel_profile out[3])
+{
+    if (!g || !out) { set_error("wl_profile_read: NULL"); return WL_ERR_ARG; }
+    std::lock_guard<std::mutex> lock(g->mu);
+    std::memcpy(out, g->prof, sizeof(g->prof));
+    return WL_OK;
+}
 
 extern "C" int bicgstab_solve(wl_gauge *g, const void *b, void *x, double m0, const wl_solver_params *p,
                               wl_solver_stats *stats, void *stream)

@@ -93,15 +93,17 @@ def test_bicgstab_m_vs_oracle(api):
     masses = [0.4, 0.25, 0.1, 0.05]
     xs = [torch.empty((lat.volume, 4, 3), dtype=torch.complex128, device="cuda") for _ in masses]
     stats = api.bicgstab_m_solve(g, _cuda(b), xs, masses, api.params(inner_prec="f64"))
-    ref, ost = O.bicgstab_m(U, dims, b, masses, tol=1e-12)
+    ref, _ = O.bicgstab_m(U, dims, b, masses, tol=1e-12)
     for i, m in enumerate(masses):
         assert stats[i]["true_relres"] <= 1e-10, stats[i]
         assert rel(xs[i].cpu().numpy(), ref[i]) < 1e-8
     # the unshifted (lightest) mass needs the most iterations; heavier ones freeze earlier
     its = [stats[i]["iterations"] for i in range(len(masses))]
     assert its[3] == max(its) and its[0] <= its[3]
-    # iteration counts agree with the oracle's recursion (same arithmetic up to rounding)
-    assert abs(its[3] - ost["iterations"][3]) <= 2
+    # the library iterates the unshifted system to tol/2 (iterated/true residual
+    # gap); the oracle's recursion run to the same target needs the same count
+    _, ost = O.bicgstab_m(U, dims, b, masses, tol=0.5e-10)
+    assert abs(its[3] - ost["iterations"][3]) <= 1, (its, ost["iterations"])
 
 
 def test_solver_rejects_bad_arguments(api):
