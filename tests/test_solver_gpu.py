@@ -126,3 +126,27 @@ def test_noconv_status_keeps_last_iterate(api):
     st = api.bicgstab_solve(g, b, x, 0.05, api.params(max_iter=3, inner_prec="f64", graph_iters=1), check=False)
     assert st["call_status"] == api.WL_ERR_NOCONV
     assert 0 < st["true_relres"] < 1.0
+
+
+@pytest.mark.parametrize("mode", ["graph", "host"])
+def test_profiling_counts_hop_launches(api, mode):
+    """Live hop timing: events around the first hop of each iteration, in
+    captured graphs too; no error leaks into later calls."""
+    dims = (8, 8, 8, 8)
+    U, lat, g = _gauge(api, dims, 0.3, 61, precs=("f64", "f32"))
+    b = _cuda(synth.z2_source(dims, 62))
+    api.profile_enable(g, True)
+    n0 = api.launch_count()
+    prm = api.params(mode=api.MODE_GRAPH if mode == "graph" else api.MODE_HOST)
+    xs, stats = api.multimass_solve(g, [b, b], [0.3, 0.1], prm)
+    prof = api.profile_read(g)["f32"]
+    api.profile_enable(g, False)
+    iters = stats[0][0]["iterations"] + stats[0][1]["iterations"]
+    assert 0 < prof["launches"] <= iters
+    assert prof["launches"] >= iters // 2
+    assert 0 < prof["ms"] / prof["launches"] < 10.0
+    assert prof["site_rhs"] == 2 * prof["sites"] == 2 * prof["launches"] * lat.volume // 2
+    assert api.launch_count() - n0 >= 7 * prof["launches"]
+    # a following solve is unaffected
+    _, st2 = api.multimass_solve(g, [b], [0.2], api.params())
+    assert st2[0][0]["status"] == 0
