@@ -116,10 +116,17 @@ static int inner_iteration(Inner &in, int rhs_block, cudaStream_t s, cudaEvent_t
     const double k2 = in.kappa * in.kappa;
     const int nsb = site_blocks(geo);
     // Under stream capture a plain cudaEventRecord only orders work inside
-    // the capture; cudaEventRecordExternal makes it a real record node.
-    if (ev) WL_CUDA_TRY(cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal));
+    // the capture; cudaEventRecordExternal (legal only while capturing)
+    // makes it a real record node.
+    unsigned evflags = cudaEventRecordDefault;
+    if (ev) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        WL_CUDA_TRY(cudaStreamIsCapturing(s, &cs));
+        if (cs == cudaStreamCaptureStatusActive) evflags = cudaEventRecordExternal;
+        WL_CUDA_TRY(cudaEventRecordWithFlags(ev[0], s, evflags));
+    }
     WL_TRY(hop_ex(in.g, in.p, in.tmp, nullptr, 0.0, nullptr, 0.0, 1.0, WL_ODD, 0, rhs_block, in.sc.state, s));
-    if (ev) WL_CUDA_TRY(cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal));
+    if (ev) WL_CUDA_TRY(cudaEventRecordWithFlags(ev[1], s, evflags));
     WL_TRY(hop_reduce(in.g, 0, in.tmp, in.p, 1.0, in.v, in.rhat, -k2, WL_EVEN, 0, in.sc.state, in.sc.partials, 0,
                       nsb, s));
     WL_TRY(blas_s_update(geo, in.r, in.v, in.s, in.sc.state, s));
