@@ -43,8 +43,8 @@ CONFIGS = {
 }
 # algorithmic bytes of one hop: per output site 8 links, per output site and
 # rhs one input spinor (each read once) and one output spinor
-LINK_B = {"f64": 96, "f32": 48, "f16": 24}
-SPINOR_B = {"f64": 192, "f32": 96, "f16": 52}
+LINK_B = {"f64": 96, "df": 96, "f32": 48, "f16": 24}
+SPINOR_B = {"f64": 192, "df": 192, "f32": 96, "f16": 52}
 # The reference arm cannot afford a full oracle solve; it times a sample of
 # oracle BiCGstab iterations and scales by this many inner iterations per
 # step (the paper scheme's FP32-inner count on the c3 workload, from the
@@ -213,7 +213,7 @@ def run_ours(args, cfg):
     nr, nm = len(bs_h), len(MASSES)
     bs = [torch.from_numpy(b).to(dev) for b in bs_h]
     xs = [[torch.empty((V, 4, 3), dtype=torch.complex128, device=dev) for _ in MASSES] for _ in bs]
-    prm = api.params(inner_prec=args.inner, rhs_block=args.rhs_block)
+    prm = api.params(inner_prec=args.inner, rhs_block=args.rhs_block, outer_prec=args.outer)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -294,6 +294,7 @@ def run_ours(args, cfg):
         "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": args.inner, "data": "synthetic",
         "config": {"workload": cfg["name"], "sources": nr, "masses": MASSES, "inner_prec": args.inner,
+                   "outer_prec": args.outer,
                    "tol": 1e-10, "l2": "flushed (256 MB write) before every step; working set > L2",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "e2e": {"value": t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
@@ -345,6 +346,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", choices=sorted(CONFIGS), default="c3")
     ap.add_argument("--inner", choices=["f32", "f16", "f64"], default="f32")
+    ap.add_argument("--outer", choices=["df", "f64"], default="df")
     ap.add_argument("--rhs-block", type=int, default=0)
     ap.add_argument("--baseline-sources", type=int, default=12)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

@@ -33,8 +33,8 @@
  *                  (the paper's gamma_1..gamma_4 directions)
  *    Sources and solutions are full-lattice vectors; the even/odd split is
  *    internal.  Site parity = (x+y+z+t) mod 2; site 0 is even.
- *  - Precisions: WL_F64, WL_F32 and WL_F16 (FP16 storage with one FP32 norm
- *    per site, arithmetic in FP32).  Links are stored as their first two rows
+ *  - Precisions: WL_F64, WL_F32, WL_F16 (FP16 storage with one FP32 norm
+ *    per site, arithmetic in FP32) and WL_DF (double-float, see below).  Links are stored as their first two rows
  *    (12 reals) and the third row is rebuilt as conj(row0 x row1), which is
  *    exact for SU(3) links.
  */
@@ -61,6 +61,9 @@ extern "C" {
 #define WL_F64 1
 #define WL_F32 2
 #define WL_F16 4
+#define WL_DF  8  /* double-float: a value is hi + lo of two FP32 numbers (about 48
+                     significant bits); arithmetic by error-free transformations on
+                     the FP32 pipes.  Used for the outer (reliable-update) loop. */
 
 /* ----------------------------------------------------------------- parity */
 #define WL_EVEN 0
@@ -92,6 +95,9 @@ typedef struct {
     int    rhs_block;    /* right-hand sides per thread in batched hops; 0 = autotune  */
     int    graph_iters;  /* iterations per captured graph (WL_MODE_GRAPH)               */
     int    eo;           /* 1: even-odd preconditioned solve (bicgstab_solve)           */
+    int    outer_prec;   /* WL_F64 or WL_DF: precision of the residual recomputation
+                            b - M x, of the solution accumulator and of the even-odd
+                            reconstruction                                           */
 } wl_solver_params;
 
 typedef struct {
@@ -106,7 +112,8 @@ typedef struct {
 
 /* Fill *p with defaults: tol 1e-10, max_iter 100000, inner WL_F32,
  * inner_tol 0 (1e-5 for FP32, 3e-3 for FP16, tol for FP64), max_restarts 100,
- * WL_GUESS_POLY, WL_MODE_GRAPH, rhs_block 0, graph_iters 8, eo 1. */
+ * WL_GUESS_POLY, WL_MODE_GRAPH, rhs_block 0, graph_iters 8, eo 1,
+ * outer_prec WL_DF. */
 int wl_params_default(wl_solver_params *p);
 
 /* Thread-local message describing the last failing call on this thread. */

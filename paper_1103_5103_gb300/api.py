@@ -20,12 +20,12 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libwilson.so")
 
 WL_OK, WL_ERR_ARG, WL_ERR_CUDA, WL_ERR_OOM, WL_ERR_NOCONV, WL_ERR_BREAKDOWN, WL_ERR_TIMEOUT, WL_ERR_CHECKED = range(8)
-F64, F32, F16 = 1, 2, 4
+F64, F32, F16, DF = 1, 2, 4, 8
 EVEN, ODD = 0, 1
 OP_HOP, OP_M, OP_MPREC = 0, 1, 2
 GUESS_ZERO, GUESS_POLY = 0, 1
 MODE_HOST, MODE_GRAPH = 0, 1
-_PREC_NAMES = {"f64": F64, "f32": F32, "f16": F16}
+_PREC_NAMES = {"f64": F64, "f32": F32, "f16": F16, "df": DF}
 
 
 def _prec(p) -> int:
@@ -49,7 +49,7 @@ _vp, _int, _dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
 class SolverParams(ctypes.Structure):
     _fields_ = [("tol", _dbl), ("max_iter", _int), ("inner_prec", _int), ("inner_tol", _dbl),
                 ("max_restarts", _int), ("guess", _int), ("mode", _int), ("rhs_block", _int),
-                ("graph_iters", _int), ("eo", _int)]
+                ("graph_iters", _int), ("eo", _int), ("outer_prec", _int)]
 
 
 class SolverStats(ctypes.Structure):
@@ -136,7 +136,7 @@ def params(**kw) -> SolverParams:
     p = SolverParams()
     _check(_lib.wl_params_default(ctypes.byref(p)))
     for k, v in kw.items():
-        if k == "inner_prec":
+        if k in ("inner_prec", "outer_prec"):
             v = _prec(v)
         if not hasattr(p, k):
             raise KeyError(k)
@@ -190,7 +190,7 @@ class Lattice:
 class Gauge:
     """wl_gauge handle built from canonical complex128 CUDA links (4, V, 3, 3)."""
 
-    def __init__(self, lat: Lattice, U: torch.Tensor, precs=("f64", "f32", "f16"), stream=None):
+    def __init__(self, lat: Lattice, U: torch.Tensor, precs=("f64", "f32", "f16", "df"), stream=None):
         if U.dtype != torch.complex128 or U.numel() != 36 * lat.volume:
             raise ValueError("links: expected complex128 (4, V, 3, 3)")
         mask = 0

@@ -521,6 +521,7 @@ extern "C" int bicgstab_m_solve(wl_gauge *g, const void *b, void *const *x, cons
     for (int i : polish) {
         wl_solver_params pp = *p;
         pp.inner_prec = WL_F64;
+        pp.outer_prec = WL_F64;
         pp.eo = 1;
         wl_solver_stats pol;
         const int ps_ = bicgstab_solve(g, b, x[i], m0[i], &pp, &pol, stream);

@@ -204,10 +204,10 @@ int blas_p_update(const Geom &g, const Vec &r, const Vec &p, const Vec &v, BiSta
 }
 
 // ------------------------------------------------------------ (re)start
-// r = convert(r64); rhat = r; p = r; x = 0; rho = ||r||^2; target2 = delta2 * rho.
+// r = convert(r_outer); rhat = r; p = r; x = 0; rho = ||r||^2; target2 = delta2 * rho.
 // rhs with active[r] == 0 are marked done and left untouched.
 
-template <int P, int PX>
+template <int PO, int P, int PX>
 __global__ void __launch_bounds__(kBlock) k_restart(Geom g, Vec r64, Vec r, Vec rhat, Vec p, Vec x, BiState *state,
                                                     double *partials, const int *active, const double *delta2)
 {
@@ -220,11 +220,11 @@ __global__ void __launch_bounds__(kBlock) k_restart(Geom g, Vec r64, Vec r, Vec 
     double red[1] = {0.0};
     if (q.i < g.Vh) {
         using R = RT<P>;
-        cx<double> a[12];
-        SpinorIO<WL_F64>::load(r64.rhs(q.r), g.stride, q.i, a);
+        cx<RT<PO>> a[12];
+        SpinorIO<PO>::load(r64.rhs(q.r), g.stride, q.i, a);
         cx<R> v[12];
 #pragma unroll
-        for (int k = 0; k < 12; ++k) v[k] = {(R)a[k].re, (R)a[k].im};
+        for (int k = 0; k < 12; ++k) v[k] = cconv<R>(a[k]);
         SpinorIO<P>::roundtrip(v);
         st<P>(r, q.r, g.stride, q.i, v);
         st<P>(rhat, q.r, g.stride, q.i, v);
@@ -253,16 +253,17 @@ __global__ void __launch_bounds__(kBlock) k_restart(Geom g, Vec r64, Vec r, Vec 
     }
 }
 
-int blas_restart(const Geom &g, const Vec &r64, const Vec &r, const Vec &rhat, const Vec &p, const Vec &x,
-                 BiState *state, double *partials, const int *active, const double *delta2, cudaStream_t s)
+template <int PO>
+static int restart_po(const Geom &g, const Vec &r64, const Vec &r, const Vec &rhat, const Vec &p, const Vec &x,
+                      BiState *state, double *partials, const int *active, const double *delta2, cudaStream_t s)
 {
     const int gr = grid_of(g, r.nrhs);
     if (r.prec == WL_F64 && x.prec == WL_F64)
-        k_restart<WL_F64, WL_F64><<<gr, kBlock, 0, s>>>(g, r64, r, rhat, p, x, state, partials, active, delta2);
+        k_restart<PO, WL_F64, WL_F64><<<gr, kBlock, 0, s>>>(g, r64, r, rhat, p, x, state, partials, active, delta2);
     else if (r.prec == WL_F32 && x.prec == WL_F32)
-        k_restart<WL_F32, WL_F32><<<gr, kBlock, 0, s>>>(g, r64, r, rhat, p, x, state, partials, active, delta2);
+        k_restart<PO, WL_F32, WL_F32><<<gr, kBlock, 0, s>>>(g, r64, r, rhat, p, x, state, partials, active, delta2);
     else if (r.prec == WL_F16 && x.prec == WL_F32)
-        k_restart<WL_F16, WL_F32><<<gr, kBlock, 0, s>>>(g, r64, r, rhat, p, x, state, partials, active, delta2);
+        k_restart<PO, WL_F16, WL_F32><<<gr, kBlock, 0, s>>>(g, r64, r, rhat, p, x, state, partials, active, delta2);
     else {
         set_error("blas_restart: unsupported precision pair");
         return WL_ERR_ARG;
@@ -272,27 +273,67 @@ int blas_restart(const Geom &g, const Vec &r64, const Vec &r, const Vec &rhat, c
     return WL_OK;
 }
 
-// ------------------------------------------- x64 += e  (rhs with active != 0)
+int blas_restart(const Geom &g, const Vec &r64, const Vec &r, const Vec &rhat, const Vec &p, const Vec &x,
+                 BiState *state, double *partials, const int *active, const double *delta2, cudaStream_t s)
+{
+    if (r64.prec == WL_DF) return restart_po<WL_DF>(g, r64, r, rhat, p, x, state, partials, active, delta2, s);
+    return restart_po<WL_F64>(g, r64, r, rhat, p, x, state, partials, active, delta2, s);
+}
 
-template <int PX>
+// ----------------------------------------- x_outer += e  (rhs with active != 0)
+
+template <int PO, int PX>
 __global__ void __launch_bounds__(kBlock) k_accum(Geom g, Vec e, Vec x64, const int *active)
 {
     const SiteIdx q = site_idx(x64.nrhs);
     if (!active[q.r] || q.i >= g.Vh) return;
     cx<RT<PX>> a[12];
-    cx<double> b[12];
+    cx<RT<PO>> b[12];
     SpinorIO<PX>::load(e.rhs(q.r), g.stride, q.i, a);
-    SpinorIO<WL_F64>::load(x64.rhs(q.r), g.stride, q.i, b);
+    SpinorIO<PO>::load(x64.rhs(q.r), g.stride, q.i, b);
 #pragma unroll
-    for (int k = 0; k < 12; ++k) b[k] = {b[k].re + (double)a[k].re, b[k].im + (double)a[k].im};
-    SpinorIO<WL_F64>::store(x64.rhs(q.r), g.stride, q.i, b);
+    for (int k = 0; k < 12; ++k) b[k] = b[k] + cconv<RT<PO>>(a[k]);
+    SpinorIO<PO>::store(x64.rhs(q.r), g.stride, q.i, b);
 }
 
 int blas_accum(const Geom &g, const Vec &e, const Vec &x64, const int *active, cudaStream_t s)
 {
     const int gr = grid_of(g, x64.nrhs);
-    if (e.prec == WL_F64) k_accum<WL_F64><<<gr, kBlock, 0, s>>>(g, e, x64, active);
-    else k_accum<WL_F32><<<gr, kBlock, 0, s>>>(g, e, x64, active);
+    if (x64.prec == WL_DF) {
+        if (e.prec == WL_F64) k_accum<WL_DF, WL_F64><<<gr, kBlock, 0, s>>>(g, e, x64, active);
+        else k_accum<WL_DF, WL_F32><<<gr, kBlock, 0, s>>>(g, e, x64, active);
+    } else {
+        if (e.prec == WL_F64) k_accum<WL_F64, WL_F64><<<gr, kBlock, 0, s>>>(g, e, x64, active);
+        else k_accum<WL_F64, WL_F32><<<gr, kBlock, 0, s>>>(g, e, x64, active);
+    }
+    WL_CUDA_TRY(cudaGetLastError());
+    note_launch(s);
+    return WL_OK;
+}
+
+// --------------------------------------------- out = x + a * y (outer prec)
+
+template <int PO>
+__global__ void __launch_bounds__(kBlock) k_xpay(Geom g, Vec x, double a, Vec y, Vec out)
+{
+    const SiteIdx q = site_idx(out.nrhs);
+    if (q.i >= g.Vh) return;
+    using R = RT<PO>;
+    cx<R> xv[12], yv[12];
+    SpinorIO<PO>::load(x.rhs(q.r), g.stride, q.i, xv);
+    SpinorIO<PO>::load(y.rhs(q.r), g.stride, q.i, yv);
+    const R c = Conv<R>::from(a);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) xv[k] = xv[k] + c * yv[k];
+    SpinorIO<PO>::store(out.rhs(q.r), g.stride, q.i, xv);
+}
+
+int blas_xpay(const Geom &g, const Vec &x, double a, const Vec &y, const Vec &out, cudaStream_t s)
+{
+    const int gr = grid_of(g, out.nrhs);
+    if (out.prec == WL_DF) k_xpay<WL_DF><<<gr, kBlock, 0, s>>>(g, x, a, y, out);
+    else if (out.prec == WL_F64) k_xpay<WL_F64><<<gr, kBlock, 0, s>>>(g, x, a, y, out);
+    else { set_error("blas_xpay: outer precision only"); return WL_ERR_ARG; }
     WL_CUDA_TRY(cudaGetLastError());
     note_launch(s);
     return WL_OK;
@@ -311,7 +352,10 @@ __global__ void __launch_bounds__(kBlock) k_norm2(Geom g, Vec a, double *out, do
         ld<P>(a, q.r, g.stride, q.i, v);
         double n = 0.0;
 #pragma unroll
-        for (int k = 0; k < 12; ++k) n += (double)v[k].re * v[k].re + (double)v[k].im * v[k].im;
+        for (int k = 0; k < 12; ++k) {
+            const double re = to_double(v[k].re), im = to_double(v[k].im);
+            n += re * re + im * im;
+        }
         red[0] = n;
     }
     double tot[1];
@@ -327,6 +371,7 @@ int blas_norm2(const Geom &g, const Vec &a, double *out_dev, double *partials, u
     case WL_F64: k_norm2<WL_F64><<<gr, kBlock, 0, s>>>(g, a, out_dev, partials, tickets); break;
     case WL_F32: k_norm2<WL_F32><<<gr, kBlock, 0, s>>>(g, a, out_dev, partials, tickets); break;
     case WL_F16: k_norm2<WL_F16><<<gr, kBlock, 0, s>>>(g, a, out_dev, partials, tickets); break;
+    case WL_DF: k_norm2<WL_DF><<<gr, kBlock, 0, s>>>(g, a, out_dev, partials, tickets); break;
     }
     WL_CUDA_TRY(cudaGetLastError());
     note_launch(s);
@@ -340,22 +385,24 @@ struct LinIn {
     const void *p[16];
 };
 
+template <int PO>
 __global__ void __launch_bounds__(kBlock) k_lincomb(Geom g, LinIn in, int k, size_t rhs_bytes, int nrhs,
                                                     const double *cre, const double *cim, Vec out)
 {
+    using R = RT<PO>;
     const SiteIdx q = site_idx(nrhs);
     if (q.i >= g.Vh) return;
-    cx<double> acc[12];
+    cx<R> acc[12];
 #pragma unroll
-    for (int c = 0; c < 12; ++c) acc[c] = {0.0, 0.0};
+    for (int c = 0; c < 12; ++c) acc[c] = {R(0), R(0)};
     for (int j = 0; j < k; ++j) {
-        const cx<double> w = {cre[q.r * k + j], cim[q.r * k + j]};
-        cx<double> v[12];
-        SpinorIO<WL_F64>::load(static_cast<const char *>(in.p[j]) + (size_t)q.r * rhs_bytes, g.stride, q.i, v);
+        const cx<R> w = {Conv<R>::from(cre[q.r * k + j]), Conv<R>::from(cim[q.r * k + j])};
+        cx<R> v[12];
+        SpinorIO<PO>::load(static_cast<const char *>(in.p[j]) + (size_t)q.r * rhs_bytes, g.stride, q.i, v);
 #pragma unroll
         for (int c = 0; c < 12; ++c) acc[c] = cmad(w, v[c], acc[c]);
     }
-    SpinorIO<WL_F64>::store(out.rhs(q.r), g.stride, q.i, acc);
+    SpinorIO<PO>::store(out.rhs(q.r), g.stride, q.i, acc);
 }
 
 int blas_lincomb(const Geom &g, const double *cre_dev, const double *cim_dev, const Vec *const *in, int k,
@@ -364,7 +411,11 @@ int blas_lincomb(const Geom &g, const double *cre_dev, const double *cim_dev, co
     if (k < 1 || k > 16) { set_error("blas_lincomb: 1..16 inputs"); return WL_ERR_ARG; }
     LinIn li;
     for (int j = 0; j < k; ++j) li.p[j] = in[j]->ptr;
-    k_lincomb<<<grid_of(g, out.nrhs), kBlock, 0, s>>>(g, li, k, out.rhs_bytes, out.nrhs, cre_dev, cim_dev, out);
+    if (out.prec == WL_DF)
+        k_lincomb<WL_DF><<<grid_of(g, out.nrhs), kBlock, 0, s>>>(g, li, k, out.rhs_bytes, out.nrhs, cre_dev, cim_dev, out);
+    else if (out.prec == WL_F64)
+        k_lincomb<WL_F64><<<grid_of(g, out.nrhs), kBlock, 0, s>>>(g, li, k, out.rhs_bytes, out.nrhs, cre_dev, cim_dev, out);
+    else { set_error("blas_lincomb: outer precision only"); return WL_ERR_ARG; }
     WL_CUDA_TRY(cudaGetLastError());
     note_launch(s);
     return WL_OK;
@@ -381,7 +432,7 @@ __global__ void __launch_bounds__(kBlock) k_convert(Geom g, Vec in, Vec out)
     cx<RT<PO>> b[12];
     SpinorIO<PI>::load(in.rhs(q.r), g.stride, q.i, a);
 #pragma unroll
-    for (int k = 0; k < 12; ++k) b[k] = {(RT<PO>)a[k].re, (RT<PO>)a[k].im};
+    for (int k = 0; k < 12; ++k) b[k] = cconv<RT<PO>>(a[k]);
     SpinorIO<PO>::store(out.rhs(q.r), g.stride, q.i, b);
 }
 
@@ -393,6 +444,7 @@ int blas_convert(const Geom &g, const Vec &in, const Vec &out, cudaStream_t s)
     WL_CONV(WL_F64, WL_F64) WL_CONV(WL_F64, WL_F32) WL_CONV(WL_F64, WL_F16)
     WL_CONV(WL_F32, WL_F64) WL_CONV(WL_F32, WL_F32) WL_CONV(WL_F32, WL_F16)
     WL_CONV(WL_F16, WL_F64) WL_CONV(WL_F16, WL_F32) WL_CONV(WL_F16, WL_F16)
+    WL_CONV(WL_DF, WL_F64) WL_CONV(WL_F64, WL_DF) WL_CONV(WL_DF, WL_F32) WL_CONV(WL_DF, WL_DF)
 #undef WL_CONV
     set_error("blas_convert: bad precision");
     return WL_ERR_ARG;

@@ -110,6 +110,77 @@ __device__ __forceinline__ cx<R> conjmad(cx<R> a, cx<R> b, cx<R> c)  // conj(a)*
     return {fma(a.re, b.re, fma(a.im, b.im, c.re)), fma(a.re, b.im, fma(-a.im, b.re, c.im))};
 }
 
+// ------------------------------------------------------------ double-float
+//
+// A double-float value is the unevaluated sum hi + lo of two FP32 numbers
+// with |lo| <= ulp(hi)/2, about 48 significant bits.  GB300 executes FP64 at
+// 1/57 of its FP32 rate, so the FP64-class parts of the solver (residual
+// recomputation, solution accumulator, even-odd reconstruction) run in this
+// format on the FP32 pipes.  The operations are the classical error-free
+// transformations: Knuth's two-sum, the FMA two-product, and Dekker's
+// renormalisation (fast two-sum); products and sums keep the low-order
+// cross terms, so the relative error of each operation is a few 2^-48.
+
+struct df {
+    float hi, lo;
+    __host__ __device__ df() {}
+    __host__ __device__ constexpr df(float h, float l) : hi(h), lo(l) {}
+    __host__ __device__ explicit constexpr df(int v) : hi((float)v), lo(0.f) {}
+    __host__ __device__ explicit constexpr df(float v) : hi(v), lo(0.f) {}
+    // split a double: hi = round(d), lo = round(d - hi)
+    __host__ __device__ explicit df(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
+};
+
+using ::fma;  // keep the float/double overloads visible next to the df one
+
+__device__ __forceinline__ df df_fast_two_sum(float a, float b)  // |a| >= |b|
+{
+    const float s = a + b;
+    return df(s, b - (s - a));
+}
+
+__device__ __forceinline__ df operator+(df a, df b)
+{
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    float e = (a.hi - (s - bb)) + (b.hi - bb);  // two-sum error of the high parts
+    e += a.lo + b.lo;
+    return df_fast_two_sum(s, e);
+}
+__device__ __forceinline__ df operator-(df a) { return df(-a.hi, -a.lo); }
+__device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
+__device__ __forceinline__ df operator*(df a, df b)
+{
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);  // exact error of the high product
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ df fma(df a, df b, df c) { return a * b + c; }
+__device__ __forceinline__ double to_double(df a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ double to_double(float a) { return (double)a; }
+__device__ __forceinline__ double to_double(double a) { return a; }
+__device__ __forceinline__ float to_float(df a) { return a.hi + a.lo; }
+
+// Conversions between arithmetic types (double <-> df go through the split).
+template <typename T> struct Conv;
+template <> struct Conv<double> {
+    static __device__ __forceinline__ double from(double v) { return v; }
+    static __device__ __forceinline__ double from(float v) { return (double)v; }
+    static __device__ __forceinline__ double from(df v) { return to_double(v); }
+};
+template <> struct Conv<float> {
+    static __device__ __forceinline__ float from(double v) { return (float)v; }
+    static __device__ __forceinline__ float from(float v) { return v; }
+    static __device__ __forceinline__ float from(df v) { return to_float(v); }
+};
+template <> struct Conv<df> {
+    static __device__ __forceinline__ df from(double v) { return df(v); }
+    static __device__ __forceinline__ df from(float v) { return df(v); }
+    static __device__ __forceinline__ df from(df v) { return v; }
+};
+
 // ---------------------------------------------------------- precision I/O
 
 // Arithmetic type per storage precision: FP16 storage computes in FP32.
@@ -117,15 +188,22 @@ template <int P> struct PrecTraits;
 template <> struct PrecTraits<WL_F64> { using R = double; };
 template <> struct PrecTraits<WL_F32> { using R = float; };
 template <> struct PrecTraits<WL_F16> { using R = float; };
+template <> struct PrecTraits<WL_DF> { using R = df; };
 
 // Bytes per site of an internal spinor / per site of one direction's link.
 __host__ __device__ constexpr int spinor_site_bytes(int prec)
 {
-    return prec == WL_F64 ? 192 : prec == WL_F32 ? 96 : 52;
+    return prec == WL_F64 ? 192 : prec == WL_F32 ? 96 : prec == WL_DF ? 192 : 52;
 }
 __host__ __device__ constexpr int link_site_bytes(int prec)
 {
-    return prec == WL_F64 ? 96 : prec == WL_F32 ? 48 : 24;
+    return prec == WL_F64 ? 96 : prec == WL_F32 ? 48 : prec == WL_DF ? 96 : 24;
+}
+
+template <typename To, typename From>
+__device__ __forceinline__ cx<To> cconv(cx<From> z)
+{
+    return {Conv<To>::from(z.re), Conv<To>::from(z.im)};
 }
 
 // Internal spinor layout, component k = 3*spin + colour (12 complex):
@@ -133,6 +211,7 @@ __host__ __device__ constexpr int link_site_bytes(int prec)
 //   F32: float4  [6][stride]   (chunk j = components 2j, 2j+1)
 //   F16: uint4   [3][stride]   (chunk j = components 4j..4j+3 as half2)
 //        followed by float norm[stride]; value = half * norm.
+//   DF:  float4  [12][stride]  (chunk k = component k as re.hi, re.lo, im.hi, im.lo)
 template <int P> struct SpinorIO;
 
 template <> struct SpinorIO<WL_F64> {
@@ -241,8 +320,29 @@ template <> struct SpinorIO<WL_F16> {
     }
 };
 
+template <> struct SpinorIO<WL_DF> {
+    using R = df;
+    static __device__ __forceinline__ void load(const void *base, int stride, int i, cx<R> (&v)[12])
+    {
+        const float4 *p = static_cast<const float4 *>(base);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            float4 t = __ldg(p + (size_t)k * stride + i);
+            v[k] = {df(t.x, t.y), df(t.z, t.w)};
+        }
+    }
+    static __device__ __forceinline__ void roundtrip(cx<R> (&)[12]) {}
+    static __device__ __forceinline__ void store(void *base, int stride, int i, const cx<R> (&v)[12])
+    {
+        float4 *p = static_cast<float4 *>(base);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) p[(size_t)k * stride + i] = make_float4(v[k].re.hi, v[k].re.lo, v[k].im.hi, v[k].im.lo);
+    }
+};
+
 // Links: per parity, per direction, the first two rows (6 complex, k = 3*row + col):
 //   F64: double2 [4][6][stride];  F32: float4 [4][3][stride];  F16: uint2 [4][3][stride]
+//   DF:  float4 [4][6][stride] (re.hi, re.lo, im.hi, im.lo)
 // Row 2 is rebuilt as conj(row0 x row1).
 template <int P> struct LinkIO;
 
@@ -299,6 +399,21 @@ template <> struct LinkIO<WL_F16> {
             float2 a = unpack_half2(t.x), b = unpack_half2(t.y);
             u[2 * k] = {a.x, a.y};
             u[2 * k + 1] = {b.x, b.y};
+        }
+        reconstruct_row2(u);
+    }
+};
+
+template <> struct LinkIO<WL_DF> {
+    using R = df;
+    static constexpr int chunks = 6;
+    static __device__ __forceinline__ void load(const void *dirbase, int stride, int i, cx<R> (&u)[9])
+    {
+        const float4 *p = static_cast<const float4 *>(dirbase);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            float4 t = __ldg(p + (size_t)k * stride + i);
+            u[k] = {df(t.x, t.y), df(t.z, t.w)};
         }
         reconstruct_row2(u);
     }

@@ -32,11 +32,11 @@ template <> struct Proj<1> { static constexpr int a1 = 0, c1 = 2, a2 = 1, c2 = 0
 template <> struct Proj<2> { static constexpr int a1 = 1, c1 = 3, a2 = 0, c2 = 1; };  // (0,-i,0,1) (i,0,1,0)
 template <> struct Proj<3> { static constexpr int a1 = 1, c1 = 0, a2 = 0, c2 = 0; };  // (0,1,0,1) (1,0,1,0)
 
-// acc += sign * L psi (1 -/+ gamma_MU) with L = u (ADJ = false) or u^dag.
-// PLUS = 0 selects (1 - gamma_MU), PLUS = 1 selects (1 + gamma_MU).
+// acc += (neg ? -1 : 1) * L psi (1 -/+ gamma_MU) with L = u (ADJ = false) or
+// u^dag.  PLUS = 0 selects (1 - gamma_MU), PLUS = 1 selects (1 + gamma_MU).
 // Spinor component k = 3*spin + colour.
 template <int MU, int PLUS, bool ADJ, typename R>
-__device__ __forceinline__ void transport(cx<R> (&acc)[12], const cx<R> (&psi)[12], const cx<R> (&u)[9], R sign)
+__device__ __forceinline__ void transport(cx<R> (&acc)[12], const cx<R> (&psi)[12], const cx<R> (&u)[9], bool neg)
 {
     constexpr int A1 = Proj<MU>::a1, A2 = Proj<MU>::a2;
     constexpr int C1 = (Proj<MU>::c1 + 2 * PLUS) & 3, C2 = (Proj<MU>::c2 + 2 * PLUS) & 3;
@@ -52,7 +52,7 @@ __device__ __forceinline__ void transport(cx<R> (&acc)[12], const cx<R> (&psi)[1
     cx<R> w1[3], w2[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        cx<R> s1 = {0, 0}, s2 = {0, 0};
+        cx<R> s1 = {R(0), R(0)}, s2 = {R(0), R(0)};
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
             if constexpr (!ADJ) {
@@ -63,8 +63,8 @@ __device__ __forceinline__ void transport(cx<R> (&acc)[12], const cx<R> (&psi)[1
                 s2 = conjmad(u[3 * b + a], h2[b], s2);
             }
         }
-        w1[a] = sign * s1;
-        w2[a] = sign * s2;
+        w1[a] = neg ? cx<R>{-s1.re, -s1.im} : s1;
+        w2[a] = neg ? cx<R>{-s2.re, -s2.im} : s2;
     }
     // expand: res_s += w_k v_k^dag[s]
 #pragma unroll
@@ -101,7 +101,7 @@ __device__ __forceinline__ void hop_dir(const HopArgs &a, int i, const Coord &c,
     using R = typename PrecTraits<P>::R;
     const Geom &g = a.g;
     int fwd, bwd;
-    R sf = R(1), sb = R(1);
+    bool sf = false, sb = false;  // antiperiodic sign flips
     if constexpr (MU == 0) {
         const int xf = c.x + 1 == g.X ? 0 : c.x + 1;
         const int xb = c.x == 0 ? g.X - 1 : c.x - 1;
@@ -120,8 +120,8 @@ __device__ __forceinline__ void hop_dir(const HopArgs &a, int i, const Coord &c,
         fwd = lastt ? i - (g.T - 1) * s : i + s;
         bwd = firstt ? i + (g.T - 1) * s : i - s;
         if (g.antiperiodic) {
-            if (lastt) sf = R(-1);
-            if (firstt) sb = R(-1);
+            sf = lastt;
+            sb = firstt;
         }
     }
     const size_t dir_off = (size_t)MU * link_dir_bytes(P, g.stride);
@@ -171,18 +171,19 @@ struct EpiStore {
             const size_t off = (size_t)rr * rhs_bytes;
             cx<R> o[12];
 #pragma unroll
-            for (int k = 0; k < 12; ++k) o[k] = R(coef) * acc[r][k];
+            const R c = Conv<R>::from(coef);
+            for (int k = 0; k < 12; ++k) o[k] = c * acc[r][k];
             if (x1) {
                 cx<R> v[12];
                 SpinorIO<P>::load(static_cast<const char *>(x1) + off, a.g.stride, i, v);
 #pragma unroll
-                for (int k = 0; k < 12; ++k) o[k] = o[k] + R(a1) * v[k];
+                for (int k = 0; k < 12; ++k) o[k] = o[k] + Conv<R>::from(a1) * v[k];
             }
             if (x2) {
                 cx<R> v[12];
                 SpinorIO<P>::load(static_cast<const char *>(x2) + off, a.g.stride, i, v);
 #pragma unroll
-                for (int k = 0; k < 12; ++k) o[k] = o[k] + R(a2) * v[k];
+                for (int k = 0; k < 12; ++k) o[k] = o[k] + Conv<R>::from(a2) * v[k];
             }
             SpinorIO<P>::store(static_cast<char *>(out) + off, a.g.stride, i, o);
         }
@@ -342,11 +343,14 @@ static void launch_hop_t(const HopArgs &a, const EpiStore &e, cudaStream_t s)
 template <int P, bool DAG>
 static void launch_hop_nb(int nb, HopArgs a, const EpiStore &e, cudaStream_t s)
 {
-    if constexpr (P != WL_F64) {  // FP64 with 4 rhs per thread spills registers
+    if constexpr (P == WL_F32 || P == WL_F16) {  // wider types spill with 4 rhs per thread
         if (nb >= 4) { a.ngroups = (a.nrhs + 3) / 4; launch_hop_t<P, DAG, 4>(a, e, s); return; }
     }
-    if (nb >= 2) { a.ngroups = (a.nrhs + 1) / 2; launch_hop_t<P, DAG, 2>(a, e, s); }
-    else { a.ngroups = a.nrhs; launch_hop_t<P, DAG, 1>(a, e, s); }
+    if constexpr (P != WL_DF) {
+        if (nb >= 2) { a.ngroups = (a.nrhs + 1) / 2; launch_hop_t<P, DAG, 2>(a, e, s); return; }
+    }
+    a.ngroups = a.nrhs;
+    launch_hop_t<P, DAG, 1>(a, e, s);
 }
 
 int hop_ex(wl_gauge *g, const Vec &in, const Vec &out, const Vec *x1, double a1, const Vec *x2, double a2,
@@ -381,6 +385,7 @@ int hop_ex(wl_gauge *g, const Vec &in, const Vec &out, const Vec *x1, double a1,
     case WL_F64: dagger ? launch_hop_nb<WL_F64, true>(nb, a, e, s) : launch_hop_nb<WL_F64, false>(nb, a, e, s); break;
     case WL_F32: dagger ? launch_hop_nb<WL_F32, true>(nb, a, e, s) : launch_hop_nb<WL_F32, false>(nb, a, e, s); break;
     case WL_F16: dagger ? launch_hop_nb<WL_F16, true>(nb, a, e, s) : launch_hop_nb<WL_F16, false>(nb, a, e, s); break;
+    case WL_DF: dagger ? launch_hop_nb<WL_DF, true>(nb, a, e, s) : launch_hop_nb<WL_DF, false>(nb, a, e, s); break;
     default: set_error("hop: bad precision"); return WL_ERR_ARG;
     }
     WL_CUDA_TRY(cudaGetLastError());
@@ -489,7 +494,7 @@ extern "C" int wilson_hop_multi(wl_gauge *g, const void *in, void *out, const vo
     vi.prec = vo.prec = vx.prec = prec;
     vi.nrhs = vo.nrhs = vx.nrhs = n_rhs;
     vi.rhs_bytes = vo.rhs_bytes = vx.rhs_bytes = rhs_stride;
-    const int nb = (prec == WL_F64 && rhs_block > 2) ? 2 : rhs_block;
+    const int nb = rhs_block;
     return hop(g, vi, vo, x ? &vx : nullptr, coef, out_parity, dagger ? 1 : 0, nb, as_stream(stream));
 }
 

@@ -51,7 +51,7 @@ int full_relres(wl_gauge *g, const Vec &be, const Vec &bo, const Vec &xe, const 
 struct wl_gauge {
     wl_lattice *lat;
     unsigned prec_mask;
-    void *links[3][2];  // [prec index][parity] -> 4 directions of 12-real links
+    void *links[4][2];  // [prec index][parity] -> 4 directions of 12-real links
     wl::Workspace ws;
     std::mutex mu;      // one solve at a time per handle (shared workspace)
     int profiling = 0;
@@ -60,7 +60,10 @@ struct wl_gauge {
 
 namespace wl {
 
-inline int prec_index(int prec) { return prec == WL_F64 ? 0 : prec == WL_F32 ? 1 : prec == WL_F16 ? 2 : -1; }
+inline int prec_index(int prec)
+{
+    return prec == WL_F64 ? 0 : prec == WL_F32 ? 1 : prec == WL_F16 ? 2 : prec == WL_DF ? 3 : -1;
+}
 inline bool valid_prec(int prec) { return prec_index(prec) >= 0; }
 
 size_t spinor_bytes(const Geom &g, int prec);
@@ -100,6 +103,7 @@ int blas_norm2(const Geom &g, const Vec &a, double *out_dev, double *partials, u
 int blas_lincomb(const Geom &g, const double *cre_dev, const double *cim_dev, const Vec *const *in, int k,
                  const Vec &out, cudaStream_t s);
 int blas_convert(const Geom &g, const Vec &in, const Vec &out, cudaStream_t s);
+int blas_xpay(const Geom &g, const Vec &x, double a, const Vec &y, const Vec &out, cudaStream_t s);  // out = x + a y
 
 
 // ---- solver.cu

@@ -73,7 +73,7 @@ __global__ void k_import(Geom g, const double2 *__restrict__ canon, void *out, i
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
         double2 t = canon[lex * 12 + k];
-        v[k] = {(R)t.x, (R)t.y};
+        v[k] = {Conv<R>::from(t.x), Conv<R>::from(t.y)};
     }
     SpinorIO<P>::store(out, g.stride, i, v);
 }
@@ -89,7 +89,7 @@ __global__ void k_export(Geom g, const void *in, double2 *__restrict__ canon, in
     cx<R> v[12];
     SpinorIO<P>::load(in, g.stride, i, v);
 #pragma unroll
-    for (int k = 0; k < 12; ++k) canon[lex * 12 + k] = make_double2((double)v[k].re, (double)v[k].im);
+    for (int k = 0; k < 12; ++k) canon[lex * 12 + k] = make_double2(to_double(v[k].re), to_double(v[k].im));
 }
 
 // Pack rows 0 and 1 of U_mu at the sites of one parity.
@@ -112,6 +112,12 @@ __global__ void k_pack_links(Geom g, const double2 *__restrict__ U, void *out, i
         for (int k = 0; k < 3; ++k) {
             double2 a = u[2 * k], b = u[2 * k + 1];
             p[(size_t)k * g.stride + i] = make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
+        }
+    } else if (P == WL_DF) {
+        float4 *p = reinterpret_cast<float4 *>(dir);
+        for (int k = 0; k < 6; ++k) {
+            const df re(u[k].x), im(u[k].y);
+            p[(size_t)k * g.stride + i] = make_float4(re.hi, re.lo, im.hi, im.lo);
         }
     } else {
         uint2 *p = reinterpret_cast<uint2 *>(dir);
@@ -150,6 +156,7 @@ int import_spinors(const Geom &g, const void *const *canon, const Vec &out, int 
     for (int r = 0; r < out.nrhs; ++r) {
         int st = out.prec == WL_F64   ? launch_import<WL_F64>(g, canon[r], out.rhs(r), parity, s)
                  : out.prec == WL_F32 ? launch_import<WL_F32>(g, canon[r], out.rhs(r), parity, s)
+                 : out.prec == WL_DF  ? launch_import<WL_DF>(g, canon[r], out.rhs(r), parity, s)
                                       : launch_import<WL_F16>(g, canon[r], out.rhs(r), parity, s);
         WL_TRY(st);
     }
@@ -161,6 +168,7 @@ int export_spinors(const Geom &g, const Vec &in, void *const *canon, int parity,
     for (int r = 0; r < in.nrhs; ++r) {
         int st = in.prec == WL_F64   ? launch_export<WL_F64>(g, in.rhs(r), canon[r], parity, s)
                  : in.prec == WL_F32 ? launch_export<WL_F32>(g, in.rhs(r), canon[r], parity, s)
+                 : in.prec == WL_DF  ? launch_export<WL_DF>(g, in.rhs(r), canon[r], parity, s)
                                      : launch_export<WL_F16>(g, in.rhs(r), canon[r], parity, s);
         WL_TRY(st);
     }
@@ -195,6 +203,7 @@ extern "C" int wl_params_default(wl_solver_params *p)
     p->rhs_block = 0;
     p->graph_iters = 8;
     p->eo = 1;
+    p->outer_prec = WL_DF;
     return WL_OK;
 }
 
@@ -269,7 +278,7 @@ extern "C" int wl_spinor_export(const wl_lattice *lat, const void *internal, voi
 
 extern "C" int wl_gauge_create(wl_lattice *lat, const void *U, unsigned prec_mask, void *stream, wl_gauge **out)
 {
-    if (!lat || !U || !out || !(prec_mask & (WL_F64 | WL_F32 | WL_F16)) || (prec_mask & ~7u)) {
+    if (!lat || !U || !out || !(prec_mask & (WL_F64 | WL_F32 | WL_F16 | WL_DF)) || (prec_mask & ~15u)) {
         set_error("wl_gauge_create: bad argument");
         return WL_ERR_ARG;
     }
@@ -279,9 +288,10 @@ extern "C" int wl_gauge_create(wl_lattice *lat, const void *U, unsigned prec_mas
     g->prec_mask = prec_mask;
     std::memset(g->links, 0, sizeof(g->links));
     const Geom &geo = lat->geom;
-    const int precs[3] = {WL_F64, WL_F32, WL_F16};
-    for (int pi = 0; pi < 3; ++pi) {
-        const int P = precs[pi];
+    const int precs[4] = {WL_F64, WL_F32, WL_F16, WL_DF};
+    for (int k = 0; k < 4; ++k) {
+        const int P = precs[k];
+        const int pi = prec_index(P);
         if (!(prec_mask & P)) continue;
         for (int par = 0; par < 2; ++par) {
             const size_t bytes = 4 * link_dir_bytes(P, geo.stride);
@@ -296,6 +306,7 @@ extern "C" int wl_gauge_create(wl_lattice *lat, const void *U, unsigned prec_mas
             if (P == WL_F64) k_pack_links<WL_F64><<<grid, 128, 0, s>>>(geo, Uc, g->links[pi][par], par);
             if (P == WL_F32) k_pack_links<WL_F32><<<grid, 128, 0, s>>>(geo, Uc, g->links[pi][par], par);
             if (P == WL_F16) k_pack_links<WL_F16><<<grid, 128, 0, s>>>(geo, Uc, g->links[pi][par], par);
+            if (P == WL_DF) k_pack_links<WL_DF><<<grid, 128, 0, s>>>(geo, Uc, g->links[pi][par], par);
             note_launch(s);
         }
     }
@@ -314,7 +325,7 @@ extern "C" int wl_gauge_destroy(wl_gauge *g)
 {
     if (!g) return WL_OK;
     cudaDeviceSynchronize();
-    for (int pi = 0; pi < 3; ++pi)
+    for (int pi = 0; pi < 4; ++pi)
         for (int par = 0; par < 2; ++par)
             if (g->links[pi][par]) cudaFree(g->links[pi][par]);
     g->ws.release();

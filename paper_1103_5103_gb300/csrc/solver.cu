@@ -281,9 +281,9 @@ static int eo_defect_correction(wl_gauge *g, const Vec &bprec, const Vec &x64, d
     const int prec = prm.inner_prec;
     Inner in;
     WL_TRY(make_inner(g, prec, nrhs, kappa, &in, s));
-    Vec r64, tmp64;
-    WL_TRY(make_vec(g, "dc_r64", WL_F64, nrhs, &r64));
-    WL_TRY(make_vec(g, "dc_tmp64", WL_F64, nrhs, &tmp64));
+    Vec r64, tmp64;  // outer precision (FP64 or double-float)
+    WL_TRY(make_vec(g, "dc_r64", x64.prec, nrhs, &r64));
+    WL_TRY(make_vec(g, "dc_tmp64", x64.prec, nrhs, &tmp64));
     Pinned pin;
     WL_TRY(pin.reserve(nrhs * (sizeof(double) * 2 + sizeof(int))));
     double *h_rn2 = static_cast<double *>(pin.p);
@@ -382,20 +382,18 @@ int full_relres(wl_gauge *g, const Vec &be, const Vec &bo, const Vec &xe, const 
     return WL_OK;
 }
 
-// One mass for nrhs sources already imported as be, bo (FP64):
-// bprec = b_e + kappa D_eo b_o; solve; x_o = b_o + kappa D_oe x_e;
-// FP64 true residual over the full lattice; export x.
-static int solve_one_mass(wl_gauge *g, const Vec &be, const Vec &bo, const Vec &xe, double m0,
+// One mass for nrhs sources already imported as be, bo (outer precision),
+// with bprec = b_e + kappa D_eo b_o prepared by the caller: solve, rebuild
+// x_o = b_o + kappa D_oe x_e, compute the full-lattice residual, export x.
+static int solve_one_mass(wl_gauge *g, const Vec &be, const Vec &bo, const Vec &bprec, const Vec &xe, double m0,
                           const wl_solver_params &prm, const std::vector<double> &bnorm2, void *const *x_out,
                           int x_out_stride, std::vector<wl_solver_stats> &stats, cudaStream_t s)
 {
     const Geom &geo = g->lat->geom;
     const int nrhs = be.nrhs;
     const double kappa = 1.0 / (2.0 * m0 + 8.0);
-    Vec bprec, xo;
-    WL_TRY(make_vec(g, "mm_bprec", WL_F64, nrhs, &bprec));
-    WL_TRY(make_vec(g, "mm_xo", WL_F64, nrhs, &xo));
-    WL_TRY(hop(g, bo, bprec, &be, kappa, WL_EVEN, 0, 1, s));
+    Vec xo;
+    WL_TRY(make_vec(g, "mm_xo", xe.prec, nrhs, &xo));
     std::vector<double> bnorm(nrhs);
     for (int r = 0; r < nrhs; ++r) bnorm[r] = std::sqrt(bnorm2[r]);
     WL_TRY(eo_defect_correction(g, bprec, xe, kappa, prm, bnorm, stats, s));
@@ -415,14 +413,14 @@ static int solve_one_mass(wl_gauge *g, const Vec &be, const Vec &bo, const Vec &
 
 static int check_params(const wl_gauge *g, const wl_solver_params *p)
 {
-    if (!p || !(p->tol > 0) || p->max_iter < 1 || !valid_prec(p->inner_prec) || p->max_restarts < 1 ||
-        (p->mode != WL_MODE_HOST && p->mode != WL_MODE_GRAPH) || p->graph_iters < 0 || p->rhs_block < 0 ||
-        p->rhs_block > 4) {
+    if (!p || !(p->tol > 0) || p->max_iter < 1 || !valid_prec(p->inner_prec) || p->inner_prec == WL_DF ||
+        p->max_restarts < 1 || (p->mode != WL_MODE_HOST && p->mode != WL_MODE_GRAPH) || p->graph_iters < 0 ||
+        p->rhs_block < 0 || p->rhs_block > 4 || (p->outer_prec != WL_F64 && p->outer_prec != WL_DF)) {
         set_error("solver parameters out of range");
         return WL_ERR_ARG;
     }
-    if (!(g->prec_mask & WL_F64) || !(g->prec_mask & p->inner_prec)) {
-        set_error("gauge handle needs FP64 links and links of the inner precision");
+    if (!(g->prec_mask & p->outer_prec) || !(g->prec_mask & p->inner_prec)) {
+        set_error("gauge handle needs links of the outer and of the inner precision");
         return WL_ERR_ARG;
     }
     return WL_OK;
@@ -462,10 +460,12 @@ extern "C" int bicgstab_solve(wl_gauge *g, const void *b, void *x, double m0, co
     cudaStream_t s = as_stream(stream);
     const Geom &geo = g->lat->geom;
     Timer tm;
-    Vec be, bo, xe;
-    WL_TRY(make_vec(g, "b_e", WL_F64, 1, &be));
-    WL_TRY(make_vec(g, "b_o", WL_F64, 1, &bo));
-    WL_TRY(make_vec(g, "x_e", WL_F64, 1, &xe));
+    const int PO = p->outer_prec;
+    Vec be, bo, xe, bprec;
+    WL_TRY(make_vec(g, "b_e", PO, 1, &be));
+    WL_TRY(make_vec(g, "b_o", PO, 1, &bo));
+    WL_TRY(make_vec(g, "x_e", PO, 1, &xe));
+    WL_TRY(make_vec(g, "mm_bprec", PO, 1, &bprec));
     const void *bc[1] = {b};
     const void *xc[1] = {x};
     WL_TRY(import_spinors(geo, bc, be, WL_EVEN, s));
@@ -480,7 +480,8 @@ extern "C" int bicgstab_solve(wl_gauge *g, const void *b, void *x, double m0, co
     std::vector<wl_solver_stats> st(1);
     std::memset(st.data(), 0, sizeof(wl_solver_stats));
     void *xo[1] = {x};
-    WL_TRY(solve_one_mass(g, be, bo, xe, m0, *p, bn2, xo, 1, st, s));
+    WL_TRY(hop(g, bo, bprec, &be, 1.0 / (2.0 * m0 + 8.0), WL_EVEN, 0, 1, s));  // b_e + kappa D_eo b_o
+    WL_TRY(solve_one_mass(g, be, bo, bprec, xe, m0, *p, bn2, xo, 1, st, s));
     WL_CUDA_TRY(cudaStreamSynchronize(s));
     st[0].seconds = tm.sec();
     *stats = st[0];
@@ -507,11 +508,16 @@ extern "C" int multimass_solve(wl_gauge *g, const void *const *b, void *const *x
     std::lock_guard<std::mutex> lock(g->mu);
     cudaStream_t s = as_stream(stream);
     const Geom &geo = g->lat->geom;
-    Vec be, bo;
-    WL_TRY(make_vec(g, "b_e", WL_F64, n_rhs, &be));
-    WL_TRY(make_vec(g, "b_o", WL_F64, n_rhs, &bo));
+    const int PO = p->outer_prec;
+    Vec be, bo, dbo, bprec;
+    WL_TRY(make_vec(g, "b_e", PO, n_rhs, &be));
+    WL_TRY(make_vec(g, "b_o", PO, n_rhs, &bo));
+    WL_TRY(make_vec(g, "mm_Dbo", PO, n_rhs, &dbo));
+    WL_TRY(make_vec(g, "mm_bprec", PO, n_rhs, &bprec));
     WL_TRY(import_spinors(geo, b, be, WL_EVEN, s));
     WL_TRY(import_spinors(geo, b, bo, WL_ODD, s));
+    // D_eo b_o once for all masses; b_prec(m) = b_e + kappa(m) D_eo b_o
+    WL_TRY(hop(g, bo, dbo, nullptr, 1.0, WL_EVEN, 0, 1, s));
     Scratch sc;
     WL_TRY(get_scratch(g, n_rhs, &sc, s));
     std::vector<double> ne, no, bn2(n_rhs);
@@ -533,7 +539,7 @@ extern "C" int multimass_solve(wl_gauge *g, const void *const *b, void *const *x
         Timer tm;
         const int im = order[k];
         const double m = m0[im];
-        WL_TRY(make_vec(g, "mm_sol" + std::to_string(k), WL_F64, n_rhs, &sol[k]));
+        WL_TRY(make_vec(g, "mm_sol" + std::to_string(k), PO, n_rhs, &sol[k]));
         if (k == 0 || p->guess == WL_GUESS_ZERO) {
             WL_CUDA_TRY(cudaMemsetAsync(sol[k].ptr, 0, sol[k].rhs_bytes * n_rhs, s));
         } else {
@@ -560,7 +566,8 @@ extern "C" int multimass_solve(wl_gauge *g, const void *const *b, void *const *x
             WL_TRY(blas_lincomb(geo, sc.coef, sc.coef + n_rhs * 16, ins.data(), k, sol[k], s));
         }
         for (int r = 0; r < n_rhs; ++r) std::memset(&st[r], 0, sizeof(wl_solver_stats));
-        WL_TRY(solve_one_mass(g, be, bo, sol[k], m, *p, bn2, x + im, n_mass, st, s));
+        WL_TRY(blas_xpay(geo, be, 1.0 / (2.0 * m + 8.0), dbo, bprec, s));
+        WL_TRY(solve_one_mass(g, be, bo, bprec, sol[k], m, *p, bn2, x + im, n_mass, st, s));
         WL_CUDA_TRY(cudaStreamSynchronize(s));
         const double sec = tm.sec();
         for (int r = 0; r < n_rhs; ++r) {

@@ -18,8 +18,8 @@ import torch
 
 from . import api, synth
 
-LINK_B = {"f64": 96, "f32": 48, "f16": 24}
-SPINOR_B = {"f64": 192, "f32": 96, "f16": 52}
+LINK_B = {"f64": 96, "df": 96, "f32": 48, "f16": 24}
+SPINOR_B = {"f64": 192, "df": 192, "f32": 96, "f16": 52}
 
 
 def run(dims, precs, nrhs=1, launches=50, eps=0.5, seed=2, rhs_block=1):
@@ -57,7 +57,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--dims", nargs="+", default=["8x8x8x8", "16x16x16x16", "16x16x16x32", "24x24x24x64",
                                                   "32x32x32x64"])
-    ap.add_argument("--prec", nargs="+", default=["f64", "f32", "f16"])
+    ap.add_argument("--prec", nargs="+", default=["f64", "df", "f32", "f16"])
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--rhs-block", type=int, default=1)
     ap.add_argument("--launches", type=int, default=50)

@@ -8,4 +8,4 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-TOL = {"f64": 1e-12, "f32": 1e-6, "f16": 5e-3}
+TOL = {"f64": 1e-12, "df": 1e-12, "f32": 1e-6, "f16": 5e-3}

@@ -24,7 +24,7 @@ def _field(dims, kind, seed=1):
     return synth.unit_gauge_field(dims) if kind == "free" else synth.gauge_field(dims, 0.5, seed=seed)
 
 
-def _setup(api, dims, kind, antiperiodic=True, precs=("f64", "f32", "f16")):
+def _setup(api, dims, kind, antiperiodic=True, precs=("f64", "f32", "f16", "df")):
     U = _field(dims, kind)
     lat = api.Lattice(dims, antiperiodic)
     g = api.Gauge(lat, torch.from_numpy(U).cuda(), precs=precs)
@@ -37,7 +37,7 @@ def _cuda(a):
 
 @pytest.mark.parametrize("dims", LATTICES)
 @pytest.mark.parametrize("kind", ["free", "random"])
-@pytest.mark.parametrize("prec", ["f64", "f32", "f16"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16", "df"])
 def test_dslash_ops_vs_oracle(api, dims, kind, prec):
     U, lat, g = _setup(api, dims, kind)
     psi = synth.gaussian_source(dims, seed=5)
@@ -69,7 +69,7 @@ def test_boundary_conditions(api, antiperiodic):
     assert rel(out.cpu().numpy(), want) < 1e-12
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32", "f16"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16", "df"])
 def test_internal_layout_roundtrip(api, prec):
     dims = (6, 4, 4, 8)
     lat = api.Lattice(dims)
@@ -85,10 +85,10 @@ def test_internal_layout_roundtrip(api, prec):
     if prec == "f64":
         assert err == 0.0
     else:
-        assert err < {"f32": 1e-7, "f16": 1e-3}[prec], err
+        assert err < {"df": 1e-14, "f32": 1e-7, "f16": 1e-3}[prec], err
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32", "f16"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16", "df"])
 @pytest.mark.parametrize("parity", [0, 1])
 def test_wilson_hop_internal_xpay(api, prec, parity):
     """out_p = x_p + coef * D_{p,1-p} in on internal buffers."""

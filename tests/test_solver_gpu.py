@@ -21,7 +21,7 @@ def _cuda(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def _gauge(api, dims, eps, seed, precs=("f64", "f32", "f16")):
+def _gauge(api, dims, eps, seed, precs=("f64", "f32", "f16", "df")):
     U = synth.gauge_field(dims, eps, seed=seed)
     lat = api.Lattice(dims)
     return U, lat, api.Gauge(lat, _cuda(U), precs=precs)
@@ -29,13 +29,15 @@ def _gauge(api, dims, eps, seed, precs=("f64", "f32", "f16")):
 
 @pytest.mark.parametrize("inner", ["f64", "f32", "f16"])
 @pytest.mark.parametrize("mode", ["graph", "host"])
-def test_bicgstab_solve_vs_oracle(api, inner, mode):
+@pytest.mark.parametrize("outer", ["df", "f64"])
+def test_bicgstab_solve_vs_oracle(api, inner, mode, outer):
     dims = (4, 4, 4, 8)
     U, lat, g = _gauge(api, dims, 0.3, 11)
     b = synth.z2_source(dims, seed=12)
     m0 = 0.1
     x = torch.zeros((lat.volume, 4, 3), dtype=torch.complex128, device="cuda")
-    prm = api.params(inner_prec=inner, mode=api.MODE_GRAPH if mode == "graph" else api.MODE_HOST)
+    prm = api.params(inner_prec=inner, mode=api.MODE_GRAPH if mode == "graph" else api.MODE_HOST,
+                     outer_prec=outer)
     st = api.bicgstab_solve(g, _cuda(b), x, m0, prm)
     assert st["status"] == 0 and st["true_relres"] <= 1e-10, st
     ref, _ = O.eo_solve(U, dims, b, m0, tol=1e-13)
@@ -44,13 +46,14 @@ def test_bicgstab_solve_vs_oracle(api, inner, mode):
 
 
 @pytest.mark.parametrize("inner", ["f32", "f16"])
-def test_multimass_c1_config(api, inner):
+@pytest.mark.parametrize("outer", ["df", "f64"])
+def test_multimass_c1_config(api, inner, outer):
     """8^4, eps 0.3, point source, masses {0.5, 0.3, 0.2, 0.1}."""
     dims = (8, 8, 8, 8)
     U, lat, g = _gauge(api, dims, 0.3, 1)
     b = synth.point_source(dims)
     masses = [0.5, 0.3, 0.2, 0.1]
-    xs, stats = api.multimass_solve(g, [_cuda(b)], masses, api.params(inner_prec=inner))
+    xs, stats = api.multimass_solve(g, [_cuda(b)], masses, api.params(inner_prec=inner, outer_prec=outer))
     ref, _ = O.multimass_solve(U, dims, b, masses, tol=1e-12)
     for i, m in enumerate(masses):
         st = stats[0][i]
@@ -108,7 +111,7 @@ def test_bicgstab_m_vs_oracle(api):
 
 def test_solver_rejects_bad_arguments(api):
     dims = (4, 4, 4, 4)
-    U, lat, g = _gauge(api, dims, 0.3, 1, precs=("f64", "f32"))
+    U, lat, g = _gauge(api, dims, 0.3, 1, precs=("f64", "f32", "df"))
     b = _cuda(synth.point_source(dims))
     with pytest.raises(api.WilsonError):
         api.multimass_solve(g, [b], [0.1, 0.1], api.params())           # duplicate masses
@@ -116,6 +119,8 @@ def test_solver_rejects_bad_arguments(api):
         api.multimass_solve(g, [b], [0.1], api.params(inner_prec="f16"))  # no FP16 links
     with pytest.raises(api.WilsonError):
         api.multimass_solve(g, [b], [-4.5], api.params())                 # 2 m0 + 8 <= 0
+    with pytest.raises(api.WilsonError):
+        api.multimass_solve(g, [b], [0.1], api.params(inner_prec="df"))   # DF is an outer precision only
 
 
 def test_noconv_status_keeps_last_iterate(api):
@@ -133,7 +138,7 @@ def test_profiling_counts_hop_launches(api, mode):
     """Live hop timing: events around the first hop of each iteration, in
     captured graphs too; no error leaks into later calls."""
     dims = (8, 8, 8, 8)
-    U, lat, g = _gauge(api, dims, 0.3, 61, precs=("f64", "f32"))
+    U, lat, g = _gauge(api, dims, 0.3, 61, precs=("f64", "f32", "df"))
     b = _cuda(synth.z2_source(dims, 62))
     api.profile_enable(g, True)
     n0 = api.launch_count()
