@@ -367,8 +367,8 @@ int full_relres(wl_gauge *g, const Vec &be, const Vec &bo, const Vec &xe, const 
 {
     const int nrhs = be.nrhs;
     Vec re, ro;
-    WL_TRY(make_vec(g, "rr_re", WL_F64, nrhs, &re));
-    WL_TRY(make_vec(g, "rr_ro", WL_F64, nrhs, &ro));
+    WL_TRY(make_vec(g, "rr_re", be.prec, nrhs, &re));
+    WL_TRY(make_vec(g, "rr_ro", be.prec, nrhs, &ro));
     // r_e = b_e - x_e + kappa D_eo x_o ; r_o = b_o - x_o + kappa D_oe x_e
     WL_TRY(hop_ex(g, xo, re, &be, 1.0, &xe, -1.0, kappa, WL_EVEN, 0, 1, nullptr, s));
     WL_TRY(hop_ex(g, xe, ro, &bo, 1.0, &xo, -1.0, kappa, WL_ODD, 0, 1, nullptr, s));
