@@ -213,7 +213,8 @@ def run_ours(args, cfg):
     nr, nm = len(bs_h), len(MASSES)
     bs = [torch.from_numpy(b).to(dev) for b in bs_h]
     xs = [[torch.empty((V, 4, 3), dtype=torch.complex128, device=dev) for _ in MASSES] for _ in bs]
-    prm = api.params(inner_prec=args.inner, rhs_block=args.rhs_block, outer_prec=args.outer)
+    prm = api.params(inner_prec=args.inner, rhs_block=args.rhs_block, outer_prec=args.outer,
+                     inner_tol=args.inner_tol)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -294,7 +295,7 @@ def run_ours(args, cfg):
         "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": args.inner, "data": "synthetic",
         "config": {"workload": cfg["name"], "sources": nr, "masses": MASSES, "inner_prec": args.inner,
-                   "outer_prec": args.outer,
+                   "outer_prec": args.outer, "inner_tol": args.inner_tol or "library default",
                    "tol": 1e-10, "l2": "flushed (256 MB write) before every step; working set > L2",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "e2e": {"value": t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
@@ -348,6 +349,7 @@ def main():
     ap.add_argument("--inner", choices=["f32", "f16", "f64"], default="f32")
     ap.add_argument("--outer", choices=["df", "f64"], default="df")
     ap.add_argument("--rhs-block", type=int, default=0)
+    ap.add_argument("--inner-tol", type=float, default=0.0)
     ap.add_argument("--baseline-sources", type=int, default=12)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-baseline", action="store_true")
