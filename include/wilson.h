@@ -111,7 +111,8 @@ typedef struct {
 } wl_solver_stats;
 
 /* Fill *p with defaults: tol 1e-10, max_iter 100000, inner WL_F32,
- * inner_tol 0 (1e-5 for FP32, 3e-3 for FP16, tol for FP64), max_restarts 100,
+ * inner_tol 0 (1e-6 for FP32, 3e-4 for FP16, 1e-12 for FP64; never below
+ * what the outer target needs), max_restarts 100,
  * WL_GUESS_POLY, WL_MODE_GRAPH, rhs_block 0, graph_iters 8, eo 1,
  * outer_prec WL_DF. */
 int wl_params_default(wl_solver_params *p);

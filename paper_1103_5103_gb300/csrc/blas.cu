@@ -421,6 +421,53 @@ int blas_lincomb(const Geom &g, const double *cre_dev, const double *cim_dev, co
     return WL_OK;
 }
 
+// ------------------------------ even-odd reconstruction with its residual
+// x_o = b_o + kappa * Dx (Dx = D_oe x_e from the last residual check) and
+// r_o = b_o - x_o + kappa * Dx, the odd part of the full-lattice residual,
+// reduced to norm2[r] = ||r_o||^2.
+
+template <int PO>
+__global__ void __launch_bounds__(kBlock) k_recon(Geom g, Vec bo, Vec dx, double kappa, Vec xo, double *norm2,
+                                                  double *partials, unsigned *tickets)
+{
+    using R = RT<PO>;
+    const SiteIdx q = site_idx(xo.nrhs);
+    double red[1] = {0.0};
+    if (q.i < g.Vh) {
+        cx<R> b[12], d[12], x[12];
+        SpinorIO<PO>::load(bo.rhs(q.r), g.stride, q.i, b);
+        SpinorIO<PO>::load(dx.rhs(q.r), g.stride, q.i, d);
+        const R k = Conv<R>::from(kappa);
+        double n = 0.0;
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            const cx<R> kd = k * d[c];
+            x[c] = b[c] + kd;
+            const cx<R> ro = (b[c] - x[c]) + kd;
+            const double re = to_double(ro.re), im = to_double(ro.im);
+            n += re * re + im * im;
+        }
+        SpinorIO<PO>::store(xo.rhs(q.r), g.stride, q.i, x);
+        red[0] = n;
+    }
+    double tot[1];
+    if (grid_sum<1>(red, partials + (size_t)q.r * q.nsb * kRedNV, &tickets[q.r], q.sb, q.nsb, tot) &&
+        threadIdx.x == 0)
+        norm2[q.r] = tot[0];
+}
+
+int blas_recon(const Geom &g, const Vec &bo, const Vec &dx, double kappa, const Vec &xo, double *norm2_dev,
+               double *partials, unsigned *tickets, cudaStream_t s)
+{
+    const int gr = grid_of(g, xo.nrhs);
+    if (xo.prec == WL_DF) k_recon<WL_DF><<<gr, kBlock, 0, s>>>(g, bo, dx, kappa, xo, norm2_dev, partials, tickets);
+    else if (xo.prec == WL_F64) k_recon<WL_F64><<<gr, kBlock, 0, s>>>(g, bo, dx, kappa, xo, norm2_dev, partials, tickets);
+    else { set_error("blas_recon: outer precision only"); return WL_ERR_ARG; }
+    WL_CUDA_TRY(cudaGetLastError());
+    note_launch(s);
+    return WL_OK;
+}
+
 // ------------------------------------------------------------- conversion
 
 template <int PI, int PO>

@@ -170,8 +170,8 @@ struct EpiStore {
             if (rr >= a.nrhs || rhs_done(a.st, rr)) continue;
             const size_t off = (size_t)rr * rhs_bytes;
             cx<R> o[12];
-#pragma unroll
             const R c = Conv<R>::from(coef);
+#pragma unroll
             for (int k = 0; k < 12; ++k) o[k] = c * acc[r][k];
             if (x1) {
                 cx<R> v[12];
@@ -218,6 +218,128 @@ __device__ __forceinline__ void hop_accumulate(const HopArgs &a, int i, int r0,
     hop_dir<P, DAG, NB, 1>(a, i, c, rowbase, r0, acc);
     hop_dir<P, DAG, NB, 2>(a, i, c, rowbase, r0, acc);
     hop_dir<P, DAG, NB, 3>(a, i, c, rowbase, r0, acc);
+}
+
+// ------------------------------------------------------- rolled variant
+// The same stencil with the eight transporters in a loop that is not
+// unrolled: projector, link orientation and neighbour are selected per trip
+// (warp-uniform), so the loop body is compiled once.  For the double-float
+// type the unrolled kernel is about 8x larger than the instruction cache
+// and stalls on instruction fetch; this variant keeps the body resident.
+
+// Runtime unit phase, code as in uphase: 0 -> 1, 1 -> i, 2 -> -1, 3 -> -i.
+template <typename R>
+__device__ __forceinline__ cx<R> uphase_rt(int c, cx<R> z)
+{
+    R re = (c & 1) ? z.im : z.re;
+    R im = (c & 1) ? z.re : z.im;
+    if (c == 1 || c == 2) re = -re;
+    if (c >= 2) im = -im;
+    return {re, im};
+}
+
+template <int P, bool DAG>
+__device__ __forceinline__ void hop_accumulate_rolled(const HopArgs &a, int i, cx<typename PrecTraits<P>::R> (&acc)[12])
+{
+    using R = typename PrecTraits<P>::R;
+    const Geom &g = a.g;
+    const Coord c = site_coord(g, i, a.out_parity);
+    const int rowbase = i - (c.x >> 1);
+    const int sy = g.Xh, sz = g.Xh * g.Y, st = g.Xh * g.Y * g.Z;
+    // neighbour indices [mu][fwd, bwd] and time-boundary sign flips
+    int nb[8];
+    nb[0] = rowbase + ((c.x + 1 == g.X ? 0 : c.x + 1) >> 1);
+    nb[1] = rowbase + ((c.x == 0 ? g.X - 1 : c.x - 1) >> 1);
+    nb[2] = c.y + 1 == g.Y ? i - (g.Y - 1) * sy : i + sy;
+    nb[3] = c.y == 0 ? i + (g.Y - 1) * sy : i - sy;
+    nb[4] = c.z + 1 == g.Z ? i - (g.Z - 1) * sz : i + sz;
+    nb[5] = c.z == 0 ? i + (g.Z - 1) * sz : i - sz;
+    nb[6] = c.t + 1 == g.T ? i - (g.T - 1) * st : i + st;
+    nb[7] = c.t == 0 ? i + (g.T - 1) * st : i - st;
+    const bool neg_f = g.antiperiodic && c.t + 1 == g.T, neg_b = g.antiperiodic && c.t == 0;
+#pragma unroll 1
+    for (int d = 0; d < 8; ++d) {
+        const int mu = d >> 1;
+        const bool fwd = (d & 1) == 0;
+        const int j = nb[d];
+        const bool neg = mu == 3 && (fwd ? neg_f : neg_b);
+        // Table 1 (see Proj): a1 in {0,1}, a2 = 1 - a1; phases of the (1 - gamma) projector
+        const int a1 = mu >> 1;
+        const int c1m = (0x0321 >> (4 * mu)) & 3;   // mu: 0->1, 1->2, 2->3, 3->0
+        const int c2m = (0x0101 >> (4 * mu)) & 3;   // mu: 0->1, 1->0, 2->1, 3->0
+        const bool plus = fwd == DAG;               // (1 + gamma) on backward hops (swapped for dagger)
+        const int c1 = (c1m + (plus ? 2 : 0)) & 3, c2 = (c2m + (plus ? 2 : 0)) & 3;
+        const int c1c = (4 - c1) & 3, c2c = (4 - c2) & 3;
+        cx<R> u[9];
+        const size_t dir_off = (size_t)mu * link_dir_bytes(P, g.stride);
+        LinkIO<P>::load(static_cast<const char *>(fwd ? a.links_out : a.links_in) + dir_off, g.stride, fwd ? i : j, u);
+        cx<R> psi[12];
+        SpinorIO<P>::load(a.in, g.stride, j, psi);
+        cx<R> h1[3], h2[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const cx<R> pa1 = a1 == 0 ? psi[k] : psi[3 + k];
+            const cx<R> pa2 = a1 == 0 ? psi[3 + k] : psi[k];
+            h1[k] = uphase_rt(c1c, pa1) + psi[9 + k];
+            h2[k] = uphase_rt(c2c, pa2) + psi[6 + k];
+        }
+        cx<R> w1[3], w2[3];
+        if (fwd) {
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                cx<R> s1 = {R(0), R(0)}, s2 = {R(0), R(0)};
+#pragma unroll
+                for (int b = 0; b < 3; ++b) {
+                    s1 = cmad(u[3 * r + b], h1[b], s1);
+                    s2 = cmad(u[3 * r + b], h2[b], s2);
+                }
+                w1[r] = s1;
+                w2[r] = s2;
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                cx<R> s1 = {R(0), R(0)}, s2 = {R(0), R(0)};
+#pragma unroll
+                for (int b = 0; b < 3; ++b) {
+                    s1 = conjmad(u[3 * b + r], h1[b], s1);
+                    s2 = conjmad(u[3 * b + r], h2[b], s2);
+                }
+                w1[r] = s1;
+                w2[r] = s2;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            if (neg) {
+                w1[k] = {-w1[k].re, -w1[k].im};
+                w2[k] = {-w2[k].re, -w2[k].im};
+            }
+            const cx<R> t1 = uphase_rt(c1, w1[k]), t2 = uphase_rt(c2, w2[k]);
+            acc[k] = acc[k] + (a1 == 0 ? t1 : t2);
+            acc[3 + k] = acc[3 + k] + (a1 == 0 ? t2 : t1);
+            acc[6 + k] = acc[6 + k] + w2[k];
+            acc[9 + k] = acc[9 + k] + w1[k];
+        }
+    }
+}
+
+template <int P, bool DAG>
+__global__ void __launch_bounds__(128) k_hop_rolled(HopArgs a, EpiStore epi)
+{
+    using R = typename PrecTraits<P>::R;
+    const int r = blockIdx.x % a.ngroups;
+    const int sb = blockIdx.x / a.ngroups;
+    if (rhs_done(a.st, r)) return;
+    const int i = sb * blockDim.x + threadIdx.x;
+    if (i >= a.g.Vh) return;
+    HopArgs b = a;
+    b.in = static_cast<const char *>(a.in) + (size_t)r * a.rhs_bytes;
+    cx<R> acc[1][12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[0][k] = {R(0), R(0)};
+    hop_accumulate_rolled<P, DAG>(b, i, acc[0]);
+    epi.template operator()<P, 1>(a, i, true, r, acc);
 }
 
 template <int P, bool DAG, int NB>
@@ -343,6 +465,12 @@ static void launch_hop_t(const HopArgs &a, const EpiStore &e, cudaStream_t s)
 template <int P, bool DAG>
 static void launch_hop_nb(int nb, HopArgs a, const EpiStore &e, cudaStream_t s)
 {
+    if constexpr (P == WL_DF) {  // rolled loop: the unrolled body overflows the instruction cache
+        a.ngroups = a.nrhs;
+        const int nsb = (a.g.Vh + 127) / 128;
+        k_hop_rolled<P, DAG><<<nsb * a.nrhs, 128, 0, s>>>(a, e);
+        return;
+    }
     if constexpr (P == WL_F32 || P == WL_F16) {  // wider types spill with 4 rhs per thread
         if (nb >= 4) { a.ngroups = (a.nrhs + 3) / 4; launch_hop_t<P, DAG, 4>(a, e, s); return; }
     }

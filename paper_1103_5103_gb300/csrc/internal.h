@@ -42,9 +42,7 @@ struct Workspace {
 };
 
 
-// ---- solver.cu
-int full_relres(wl_gauge *g, const Vec &be, const Vec &bo, const Vec &xe, const Vec &xo, double kappa,
-                const std::vector<double> &bnorm, std::vector<double> &relres, cudaStream_t s);
+
 
 }  // namespace wl
 
@@ -104,10 +102,14 @@ int blas_lincomb(const Geom &g, const double *cre_dev, const double *cim_dev, co
                  const Vec &out, cudaStream_t s);
 int blas_convert(const Geom &g, const Vec &in, const Vec &out, cudaStream_t s);
 int blas_xpay(const Geom &g, const Vec &x, double a, const Vec &y, const Vec &out, cudaStream_t s);  // out = x + a y
+// x_o = b_o + kappa Dx and ||b_o - x_o + kappa Dx||^2 per rhs into norm2_dev
+int blas_recon(const Geom &g, const Vec &bo, const Vec &dx, double kappa, const Vec &xo, double *norm2_dev,
+               double *partials, unsigned *tickets, cudaStream_t s);
 
 
 // ---- solver.cu
 int full_relres(wl_gauge *g, const Vec &be, const Vec &bo, const Vec &xe, const Vec &xo, double kappa,
-                const std::vector<double> &bnorm, std::vector<double> &relres, cudaStream_t s);
+                const std::vector<double> &bnorm, std::vector<double> &relres, cudaStream_t s,
+                const std::vector<double> *ro_norm2 = nullptr);
 
 }  // namespace wl
