@@ -406,13 +406,13 @@ extern "C" int bicgstab_m_solve(wl_gauge *g, const void *b, void *const *x, cons
         Vec se = half_of(sv, 0), so = half_of(sv, 1), te = half_of(t, 0), to = half_of(t, 1);
         Vec rhe = half_of(rhat, 0), rho = half_of(rhat, 1);
         // v = A p, <rhat, v> -> alpha
-        WL_TRY(hop_reduce(g, 0, po, pe, a1, ve, rhe, -0.5, WL_EVEN, 0, st, partials, 0, 2 * nsb, q));
-        WL_TRY(hop_reduce(g, 0, pe, po, a1, vo, rho, -0.5, WL_ODD, 0, st, partials, nsb, 2 * nsb, q));
+        WL_TRY(hop_reduce(g, 0, po, pe, a1, ve, rhe, -0.5, nullptr, WL_EVEN, 0, st, partials, 0, 2 * nsb, q));
+        WL_TRY(hop_reduce(g, 0, pe, po, a1, vo, rho, -0.5, nullptr, WL_ODD, 0, st, partials, nsb, 2 * nsb, q));
         k_m_s<<<2 * nsb, kBlock, 0, q>>>(geo, nsb, r, v, sv, st);
         note_launch(q);
         // t = A s, <t,s>, <t,t> -> omega
-        WL_TRY(hop_reduce(g, 1, so, se, a1, te, rhe, -0.5, WL_EVEN, 0, st, partials, 0, 2 * nsb, q));
-        WL_TRY(hop_reduce(g, 1, se, so, a1, to, rho, -0.5, WL_ODD, 0, st, partials, nsb, 2 * nsb, q));
+        WL_TRY(hop_reduce(g, 1, so, se, a1, te, rhe, -0.5, nullptr, WL_EVEN, 0, st, partials, 0, 2 * nsb, q));
+        WL_TRY(hop_reduce(g, 1, se, so, a1, to, rho, -0.5, nullptr, WL_ODD, 0, st, partials, nsb, 2 * nsb, q));
         if (ns) {
             k_shift_a<<<1, 32, 0, q>>>(sh, ns, st, mst);
             note_launch(q);

@@ -85,12 +85,13 @@ struct HopArgs {
     size_t rhs_bytes;
     const void *links_out;       // links at the output parity (forward links)
     const void *links_in;        // links at the input parity (backward links)
-    const BiState *st;           // optional per-rhs state: skip rhs with done != 0
+    const int *skip;             // optional per-rhs flags: skip rhs r when skip[r * skip_stride] != 0
+    int skip_stride;
 };
 
-__device__ __forceinline__ bool rhs_done(const BiState *st, int r)
+__device__ __forceinline__ bool rhs_done(const HopArgs &a, int r)
 {
-    return st != nullptr && __ldcg(&st[r].done) != 0;
+    return a.skip != nullptr && __ldcg(a.skip + (size_t)r * a.skip_stride) != 0;
 }
 
 // Accumulate the eight transporters of site i for NB right-hand sides.
@@ -167,7 +168,7 @@ struct EpiStore {
 #pragma unroll
         for (int r = 0; r < NB; ++r) {
             const int rr = r0 + r;
-            if (rr >= a.nrhs || rhs_done(a.st, rr)) continue;
+            if (rr >= a.nrhs || rhs_done(a, rr)) continue;
             const size_t off = (size_t)rr * rhs_bytes;
             cx<R> o[12];
             const R c = Conv<R>::from(coef);
@@ -200,6 +201,7 @@ struct EpiReduce {
     const void *rhat;   // KIND 0 only
     double a1;
     double coef;
+    const double *coef_dev;  // if set, the coefficient is read from here (graph replays across masses)
     int blk_off, blk_total;
     size_t rhs_bytes;
     BiState *st;
@@ -330,7 +332,7 @@ __global__ void __launch_bounds__(128) k_hop_rolled(HopArgs a, EpiStore epi)
     using R = typename PrecTraits<P>::R;
     const int r = blockIdx.x % a.ngroups;
     const int sb = blockIdx.x / a.ngroups;
-    if (rhs_done(a.st, r)) return;
+    if (rhs_done(a, r)) return;
     const int i = sb * blockDim.x + threadIdx.x;
     if (i >= a.g.Vh) return;
     HopArgs b = a;
@@ -349,9 +351,9 @@ __global__ void __launch_bounds__(128) k_hop(HopArgs a, EpiStore epi)
     const int grp = blockIdx.x % a.ngroups;
     const int sb = blockIdx.x / a.ngroups;
     const int r0 = grp * NB;
-    if (a.st) {
+    if (a.skip) {
         bool all_done = true;
-        for (int r = r0; r < r0 + NB && r < a.nrhs; ++r) all_done &= rhs_done(a.st, r);
+        for (int r = r0; r < r0 + NB && r < a.nrhs; ++r) all_done &= rhs_done(a, r);
         if (all_done) return;
     }
     const int i = sb * blockDim.x + threadIdx.x;
@@ -376,6 +378,7 @@ __global__ void __launch_bounds__(128) k_hop_reduce(HopArgs a, EpiReduce<KIND> e
     if (__ldcg(&st.done)) return;   // uniform over every block of this rhs
     const int i = sb * blockDim.x + threadIdx.x;
     const bool active = i < a.g.Vh;
+    const double coef = e.coef_dev ? __ldcg(e.coef_dev) : e.coef;
     double red[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k) red[k] = 0.0;
@@ -388,7 +391,7 @@ __global__ void __launch_bounds__(128) k_hop_reduce(HopArgs a, EpiReduce<KIND> e
         cx<R> xv[12], o[12];
         SpinorIO<P>::load(static_cast<const char *>(e.xin) + off, a.g.stride, i, xv);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) o[k] = R(e.a1) * xv[k] + R(e.coef) * acc[0][k];
+        for (int k = 0; k < 12; ++k) o[k] = R(e.a1) * xv[k] + R(coef) * acc[0][k];
         // Reductions use the stored (rounded) values so that they describe
         // exactly the vector the next kernels read.
         SpinorIO<P>::roundtrip(o);
@@ -482,7 +485,7 @@ static void launch_hop_nb(int nb, HopArgs a, const EpiStore &e, cudaStream_t s)
 }
 
 int hop_ex(wl_gauge *g, const Vec &in, const Vec &out, const Vec *x1, double a1, const Vec *x2, double a2,
-           double coef, int out_parity, int dagger, int rhs_block, const BiState *st, cudaStream_t s)
+           double coef, int out_parity, int dagger, int rhs_block, const int *skip, int skip_stride, cudaStream_t s)
 {
     WL_TRY(check_links(g, in.prec));
     if (in.prec != out.prec || (x1 && x1->prec != in.prec) || (x2 && x2->prec != in.prec)) {
@@ -498,7 +501,8 @@ int hop_ex(wl_gauge *g, const Vec &in, const Vec &out, const Vec *x1, double a1,
     a.rhs_bytes = in.rhs_bytes;
     a.links_out = links_of(g, in.prec, out_parity);
     a.links_in = links_of(g, in.prec, 1 - out_parity);
-    a.st = st;
+    a.skip = skip;
+    a.skip_stride = skip_stride;
     EpiStore e;
     e.out = out.ptr;
     e.x1 = x1 ? x1->ptr : nullptr;
@@ -524,7 +528,7 @@ int hop_ex(wl_gauge *g, const Vec &in, const Vec &out, const Vec *x1, double a1,
 int hop(wl_gauge *g, const Vec &in, const Vec &out, const Vec *x, double coef, int out_parity, int dagger,
         int rhs_block, cudaStream_t s)
 {
-    return hop_ex(g, in, out, x, 1.0, nullptr, 0.0, coef, out_parity, dagger, rhs_block, nullptr, s);
+    return hop_ex(g, in, out, x, 1.0, nullptr, 0.0, coef, out_parity, dagger, rhs_block, nullptr, 0, s);
 }
 
 template <int P, bool DAG, int KIND>
@@ -537,8 +541,8 @@ static void launch_reduce_t(const HopArgs &a, const EpiReduce<KIND> &e, cudaStre
 
 template <int KIND>
 static int hop_reduce_k(wl_gauge *g, const Vec &tmp, const Vec &xin, double a1, const Vec &out, const Vec &rhat,
-                        double coef, int out_parity, int dagger, BiState *state, double *partials, int blk_off,
-                        int blk_total, cudaStream_t s)
+                        double coef, const double *coef_dev, int out_parity, int dagger, BiState *state,
+                        double *partials, int blk_off, int blk_total, cudaStream_t s)
 {
     WL_TRY(check_links(g, tmp.prec));
     HopArgs a;
@@ -550,13 +554,15 @@ static int hop_reduce_k(wl_gauge *g, const Vec &tmp, const Vec &xin, double a1, 
     a.rhs_bytes = tmp.rhs_bytes;
     a.links_out = links_of(g, tmp.prec, out_parity);
     a.links_in = links_of(g, tmp.prec, 1 - out_parity);
-    a.st = state;
+    a.skip = &state[0].done;
+    a.skip_stride = sizeof(BiState) / sizeof(int);
     EpiReduce<KIND> e;
     e.out = out.ptr;
     e.xin = xin.ptr;
     e.rhat = rhat.ptr;
     e.a1 = a1;
     e.coef = coef;
+    e.coef_dev = coef_dev;
     e.blk_off = blk_off;
     e.blk_total = blk_total;
     e.rhs_bytes = out.rhs_bytes;
@@ -574,13 +580,13 @@ static int hop_reduce_k(wl_gauge *g, const Vec &tmp, const Vec &xin, double a1, 
 }
 
 int hop_reduce(wl_gauge *g, int kind, const Vec &tmp, const Vec &xin, double a1, const Vec &out, const Vec &rhat,
-               double coef, int out_parity, int dagger, BiState *state, double *partials, int blk_off,
-               int blk_total, cudaStream_t s)
+               double coef, const double *coef_dev, int out_parity, int dagger, BiState *state, double *partials,
+               int blk_off, int blk_total, cudaStream_t s)
 {
-    return kind == 0 ? hop_reduce_k<0>(g, tmp, xin, a1, out, rhat, coef, out_parity, dagger, state, partials,
-                                       blk_off, blk_total, s)
-                     : hop_reduce_k<1>(g, tmp, xin, a1, out, rhat, coef, out_parity, dagger, state, partials,
-                                       blk_off, blk_total, s);
+    return kind == 0 ? hop_reduce_k<0>(g, tmp, xin, a1, out, rhat, coef, coef_dev, out_parity, dagger, state,
+                                       partials, blk_off, blk_total, s)
+                     : hop_reduce_k<1>(g, tmp, xin, a1, out, rhat, coef, coef_dev, out_parity, dagger, state,
+                                       partials, blk_off, blk_total, s);
 }
 
 }  // namespace wl

@@ -46,7 +46,20 @@ struct Workspace {
 
 }  // namespace wl
 
+namespace wl {
+// A captured block of inner iterations, reused while its buffers and shape
+// are unchanged (the mass enters through device memory).
+struct GraphCache {
+    std::vector<uintptr_t> key;
+    cudaGraphExec_t exec = nullptr;
+    long long kernels = 0;
+    std::vector<cudaEvent_t> events;
+    void release();
+};
+}  // namespace wl
+
 struct wl_gauge {
+    wl::GraphCache inner_graph;
     wl_lattice *lat;
     unsigned prec_mask;
     void *links[4][2];  // [prec index][parity] -> 4 directions of 12-real links
@@ -73,10 +86,10 @@ int export_spinors(const Geom &g, const Vec &in, void *const *canon, int parity,
 
 // ---- dslash.cu
 // out[r] = a1 * x1[r] + a2 * x2[r] + coef * D_{p,1-p} in[r] for r < nrhs (x1, x2
-// optional).  rhs_block = rhs per thread (1, 2 or 4).  st (optional) skips
-// rhs whose solver state is done.
+// optional).  rhs_block = rhs per thread (1, 2 or 4).  skip (optional, device)
+// skips rhs r when skip[r * skip_stride] != 0.
 int hop_ex(wl_gauge *g, const Vec &in, const Vec &out, const Vec *x1, double a1, const Vec *x2, double a2,
-           double coef, int out_parity, int dagger, int rhs_block, const BiState *st, cudaStream_t s);
+           double coef, int out_parity, int dagger, int rhs_block, const int *skip, int skip_stride, cudaStream_t s);
 int hop(wl_gauge *g, const Vec &in, const Vec &out, const Vec *x, double coef, int out_parity, int dagger,
         int rhs_block, cudaStream_t s);
 
@@ -85,9 +98,10 @@ int hop(wl_gauge *g, const Vec &in, const Vec &out, const Vec *x, double coef, i
 // reduction spread over several launches (full-lattice vectors).
 //   kind 0:  v = a1 * xin + coef * D tmp;  <rhat, v>        -> alpha = rho / <rhat, v>
 //   kind 1:  t = a1 * xin + coef * D tmp;  <t, xin>, <t, t> -> omega
+// coef_dev (optional, device) overrides coef at run time.
 int hop_reduce(wl_gauge *g, int kind, const Vec &tmp, const Vec &xin, double a1, const Vec &out, const Vec &rhat,
-               double coef, int out_parity, int dagger, BiState *state, double *partials, int blk_off,
-               int blk_total, cudaStream_t s);
+               double coef, const double *coef_dev, int out_parity, int dagger, BiState *state, double *partials,
+               int blk_off, int blk_total, cudaStream_t s);
 
 // ---- blas.cu (all on one parity; nrhs from the vectors)
 int blas_s_update(const Geom &g, const Vec &r, const Vec &v, const Vec &s_out, BiState *st, cudaStream_t s);

@@ -328,6 +328,7 @@ extern "C" int wl_gauge_destroy(wl_gauge *g)
     for (int pi = 0; pi < 4; ++pi)
         for (int par = 0; par < 2; ++par)
             if (g->links[pi][par]) cudaFree(g->links[pi][par]);
+    g->inner_graph.release();
     g->ws.release();
     delete g;
     return WL_OK;

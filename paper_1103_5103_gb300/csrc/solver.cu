@@ -53,6 +53,8 @@ struct Scratch {
     int *active = nullptr;       // [nrhs]
     double *delta2 = nullptr;    // [nrhs]
     double *coef = nullptr;      // [2][nrhs * 16] lincomb coefficients
+    double *kappa2 = nullptr;    // [1] -kappa^2 of the current mass (read by graph-captured kernels)
+    int *outer_done = nullptr;   // [nrhs] 1 once the outer residual of rhs r has converged
 };
 
 static int get_scratch(wl_gauge *g, int nrhs, Scratch *sc, cudaStream_t s)
@@ -75,9 +77,23 @@ static int get_scratch(wl_gauge *g, int nrhs, Scratch *sc, cudaStream_t s)
     sc->delta2 = static_cast<double *>(p);
     WL_TRY(g->ws.get("coef", sizeof(double) * 2 * nrhs * 16, &p));
     sc->coef = static_cast<double *>(p);
+    WL_TRY(g->ws.get("kappa2", sizeof(double), &p));
+    sc->kappa2 = static_cast<double *>(p);
+    WL_TRY(g->ws.get("outer_done", sizeof(int) * nrhs, &p));
+    sc->outer_done = static_cast<int *>(p);
     // tickets inside BiState start at zero
     WL_CUDA_TRY(cudaMemsetAsync(sc->state, 0, sizeof(BiState) * nrhs, s));
     return WL_OK;
+}
+
+void GraphCache::release()
+{
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    for (auto e : events) cudaEventDestroy(e);
+    events.clear();
+    key.clear();
+    kernels = 0;
 }
 
 // --------------------------------------------------------------- inner loop
@@ -113,8 +129,10 @@ static int make_inner(wl_gauge *g, int prec, int nrhs, double kappa, Inner *in, 
 static int inner_iteration(Inner &in, int rhs_block, cudaStream_t s, cudaEvent_t *ev = nullptr)
 {
     const Geom &geo = in.g->lat->geom;
-    const double k2 = in.kappa * in.kappa;
     const int nsb = site_blocks(geo);
+    const int *skip = &in.sc.state[0].done;
+    const int ss = sizeof(BiState) / sizeof(int);
+    const double *k2 = in.sc.kappa2;  // -kappa^2, set per mass before the graph runs
     // Under stream capture a plain cudaEventRecord only orders work inside
     // the capture; cudaEventRecordExternal (legal only while capturing)
     // makes it a real record node.
@@ -125,14 +143,14 @@ static int inner_iteration(Inner &in, int rhs_block, cudaStream_t s, cudaEvent_t
         if (cs == cudaStreamCaptureStatusActive) evflags = cudaEventRecordExternal;
         WL_CUDA_TRY(cudaEventRecordWithFlags(ev[0], s, evflags));
     }
-    WL_TRY(hop_ex(in.g, in.p, in.tmp, nullptr, 0.0, nullptr, 0.0, 1.0, WL_ODD, 0, rhs_block, in.sc.state, s));
+    WL_TRY(hop_ex(in.g, in.p, in.tmp, nullptr, 0.0, nullptr, 0.0, 1.0, WL_ODD, 0, rhs_block, skip, ss, s));
     if (ev) WL_CUDA_TRY(cudaEventRecordWithFlags(ev[1], s, evflags));
-    WL_TRY(hop_reduce(in.g, 0, in.tmp, in.p, 1.0, in.v, in.rhat, -k2, WL_EVEN, 0, in.sc.state, in.sc.partials, 0,
-                      nsb, s));
+    WL_TRY(hop_reduce(in.g, 0, in.tmp, in.p, 1.0, in.v, in.rhat, 0.0, k2, WL_EVEN, 0, in.sc.state, in.sc.partials,
+                      0, nsb, s));
     WL_TRY(blas_s_update(geo, in.r, in.v, in.s, in.sc.state, s));
-    WL_TRY(hop_ex(in.g, in.s, in.tmp, nullptr, 0.0, nullptr, 0.0, 1.0, WL_ODD, 0, rhs_block, in.sc.state, s));
-    WL_TRY(hop_reduce(in.g, 1, in.tmp, in.s, 1.0, in.t, in.rhat, -k2, WL_EVEN, 0, in.sc.state, in.sc.partials, 0,
-                      nsb, s));
+    WL_TRY(hop_ex(in.g, in.s, in.tmp, nullptr, 0.0, nullptr, 0.0, 1.0, WL_ODD, 0, rhs_block, skip, ss, s));
+    WL_TRY(hop_reduce(in.g, 1, in.tmp, in.s, 1.0, in.t, in.rhat, 0.0, k2, WL_EVEN, 0, in.sc.state, in.sc.partials,
+                      0, nsb, s));
     WL_TRY(blas_xr_update(geo, in.e, in.p, in.s, in.t, in.r, in.rhat, in.sc.state, in.sc.partials, s));
     WL_TRY(blas_p_update(geo, in.r, in.p, in.v, in.sc.state, s));
     return WL_OK;
@@ -151,50 +169,72 @@ static int run_inner(Inner &in, const wl_solver_params &prm, int max_iter, std::
     host_state.resize(nrhs);
     const int K = prm.mode == WL_MODE_GRAPH ? std::max(1, prm.graph_iters) : 1;
     cudaGraphExec_t exec = nullptr;
-    cudaStream_t cap = nullptr;
     int status = WL_OK;
     // live timing of the first hop of each iteration (wl_profile_enable)
     const bool prof = in.g->profiling != 0;
-    std::vector<cudaEvent_t> ev(prof ? 2 * K : 0);
-    for (auto &e : ev) WL_CUDA_TRY(cudaEventCreate(&e));
+    std::vector<cudaEvent_t> host_ev;   // host mode: one pair
+    std::vector<int> it_before(nrhs, 0);
+    long long graph_kernels = 0;
+    cudaEvent_t *ev = nullptr;
+    if (prm.mode == WL_MODE_GRAPH) {
+        // Reuse the captured block while buffers and shape are unchanged.
+        GraphCache &gc = in.g->inner_graph;
+        std::vector<uintptr_t> key = {
+            (uintptr_t)in.p.ptr, (uintptr_t)in.tmp.ptr, (uintptr_t)in.v.ptr, (uintptr_t)in.r.ptr,
+            (uintptr_t)in.rhat.ptr, (uintptr_t)in.s.ptr, (uintptr_t)in.t.ptr, (uintptr_t)in.e.ptr,
+            (uintptr_t)in.sc.state, (uintptr_t)in.sc.partials, (uintptr_t)in.sc.kappa2, (uintptr_t)nrhs,
+            (uintptr_t)in.prec, (uintptr_t)in.xprec, (uintptr_t)K, (uintptr_t)rb, (uintptr_t)prof,
+            (uintptr_t)in.g->lat->geom.Vh};
+        if (gc.exec == nullptr || gc.key != key) {
+            gc.release();
+            gc.events.resize(prof ? 2 * K : 0);
+            for (auto &e : gc.events) WL_CUDA_TRY(cudaEventCreate(&e));
+            cudaStream_t cap = nullptr;
+            WL_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+            cudaGraph_t graph = nullptr;
+            cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                for (int k = 0; k < K && status == WL_OK; ++k)
+                    status = inner_iteration(in, rb, cap, prof ? &gc.events[2 * k] : nullptr);
+                e = cudaStreamEndCapture(cap, &graph);
+            }
+            if (e == cudaSuccess && status == WL_OK) e = cudaGraphInstantiate(&gc.exec, graph, 0);
+            if (graph) {
+                // kernel nodes only (event-record nodes are not launches)
+                size_t n = 0;
+                cudaGraphGetNodes(graph, nullptr, &n);
+                std::vector<cudaGraphNode_t> nodes(n);
+                if (n) cudaGraphGetNodes(graph, nodes.data(), &n);
+                gc.kernels = 0;
+                for (auto nd : nodes) {
+                    cudaGraphNodeType t;
+                    if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++gc.kernels;
+                }
+                cudaGraphDestroy(graph);
+            }
+            cudaStreamDestroy(cap);
+            if (e != cudaSuccess || status != WL_OK) {
+                gc.release();
+                if (status == WL_OK) {
+                    set_error(std::string("graph capture: ") + cudaGetErrorString(e));
+                    status = WL_ERR_CUDA;
+                }
+                return status;
+            }
+            gc.key = key;
+        }
+        exec = gc.exec;
+        graph_kernels = gc.kernels;
+        if (prof) ev = gc.events.data();
+    } else if (prof) {
+        host_ev.resize(2);
+        for (auto &e : host_ev) WL_CUDA_TRY(cudaEventCreate(&e));
+        ev = host_ev.data();
+    }
     struct EvFree {
         std::vector<cudaEvent_t> &v;
         ~EvFree() { for (auto e : v) cudaEventDestroy(e); }
-    } ev_free{ev};
-    std::vector<int> it_before(nrhs, 0);
-    long long graph_kernels = 0;
-    if (prm.mode == WL_MODE_GRAPH) {
-        WL_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-        cudaGraph_t graph = nullptr;
-        cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-        if (e == cudaSuccess) {
-            for (int k = 0; k < K && status == WL_OK; ++k)
-                status = inner_iteration(in, rb, cap, prof ? &ev[2 * k] : nullptr);
-            e = cudaStreamEndCapture(cap, &graph);
-        }
-        if (e == cudaSuccess && status == WL_OK) e = cudaGraphInstantiate(&exec, graph, 0);
-        if (graph) {
-            // kernel nodes only (event-record nodes are not launches)
-            size_t n = 0;
-            cudaGraphGetNodes(graph, nullptr, &n);
-            std::vector<cudaGraphNode_t> nodes(n);
-            if (n) cudaGraphGetNodes(graph, nodes.data(), &n);
-            for (auto nd : nodes) {
-                cudaGraphNodeType t;
-                if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++graph_kernels;
-            }
-            cudaGraphDestroy(graph);
-        }
-        if (e != cudaSuccess || status != WL_OK) {
-            if (exec) cudaGraphExecDestroy(exec);
-            cudaStreamDestroy(cap);
-            if (status == WL_OK) {
-                set_error(std::string("graph capture: ") + cudaGetErrorString(e));
-                status = WL_ERR_CUDA;
-            }
-            return status;
-        }
-    }
+    } ev_free{host_ev};
     int done_iters = 0;
     for (;;) {
         if (exec) {
@@ -207,7 +247,7 @@ static int run_inner(Inner &in, const wl_solver_params &prm, int max_iter, std::
             add_launches(graph_kernels);
             done_iters += K;
         } else {
-            status = inner_iteration(in, rb, s, prof ? &ev[0] : nullptr);
+            status = inner_iteration(in, rb, s, ev);
             if (status != WL_OK) break;
             done_iters += 1;
         }
@@ -247,8 +287,6 @@ static int run_inner(Inner &in, const wl_solver_params &prm, int max_iter, std::
         if (all || done_iters >= max_iter) break;
     }
     std::memcpy(host_state.data(), hs, sizeof(BiState) * nrhs);
-    if (exec) cudaGraphExecDestroy(exec);
-    if (cap) cudaStreamDestroy(cap);
     return status;
 }
 
@@ -285,20 +323,25 @@ static int eo_defect_correction(wl_gauge *g, const Vec &bprec, const Vec &x64, d
     WL_TRY(make_vec(g, "dc_r64", x64.prec, nrhs, &r64));
     WL_TRY(make_vec(g, "dc_tmp64", x64.prec, nrhs, &tmp64));
     Pinned pin;
-    WL_TRY(pin.reserve(nrhs * (sizeof(double) * 2 + sizeof(int))));
+    WL_TRY(pin.reserve(nrhs * (sizeof(double) * 2 + sizeof(int) * 2)));
     double *h_rn2 = static_cast<double *>(pin.p);
     double *h_delta2 = h_rn2 + nrhs;
     int *h_active = reinterpret_cast<int *>(h_delta2 + nrhs);
+    int *h_outer = h_active + nrhs;
     const double delta0 = prm.inner_tol > 0 ? prm.inner_tol : default_inner_tol(prec);
     std::vector<int> outer_done(nrhs, 0), iters(nrhs, 0), restarts(nrhs, 0), fails(nrhs, 0);
     std::vector<double> last_rn(nrhs, INFINITY);
     std::vector<BiState> hst;
     const double k2 = kappa * kappa;
+    const double mk2 = -k2;
+    WL_CUDA_TRY(cudaMemcpyAsync(in.sc.kappa2, &mk2, sizeof(double), cudaMemcpyHostToDevice, s));
+    WL_CUDA_TRY(cudaMemsetAsync(in.sc.outer_done, 0, sizeof(int) * nrhs, s));
     int total_restarts = 0;
     for (;;) {
-        // r64 = bprec - x + kappa^2 D_eo D_oe x
-        WL_TRY(hop(g, x64, tmp64, nullptr, 1.0, WL_ODD, 0, 1, s));
-        WL_TRY(hop_ex(g, tmp64, r64, &bprec, 1.0, &x64, -1.0, k2, WL_EVEN, 0, 1, nullptr, s));
+        // r = bprec - x + kappa^2 D_eo D_oe x for the rhs still iterating;
+        // D_oe x stays in tmp64 (the reconstruction uses the last one)
+        WL_TRY(hop_ex(g, x64, tmp64, nullptr, 0.0, nullptr, 0.0, 1.0, WL_ODD, 0, 1, in.sc.outer_done, 1, s));
+        WL_TRY(hop_ex(g, tmp64, r64, &bprec, 1.0, &x64, -1.0, k2, WL_EVEN, 0, 1, in.sc.outer_done, 1, s));
         WL_TRY(blas_norm2(geo, r64, in.sc.norms, in.sc.partials, in.sc.tickets, s));
         WL_CUDA_TRY(cudaMemcpyAsync(h_rn2, in.sc.norms, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
         WL_CUDA_TRY(cudaStreamSynchronize(s));
@@ -323,6 +366,8 @@ static int eo_defect_correction(wl_gauge *g, const Vec &bprec, const Vec &x64, d
             last_rn[r] = rn;
             ++n_active;
         }
+        for (int r = 0; r < nrhs; ++r) h_outer[r] = outer_done[r];
+        WL_CUDA_TRY(cudaMemcpyAsync(in.sc.outer_done, h_outer, sizeof(int) * nrhs, cudaMemcpyHostToDevice, s));
         if (n_active == 0) break;
         WL_CUDA_TRY(cudaMemcpyAsync(in.sc.active, h_active, sizeof(int) * nrhs, cudaMemcpyHostToDevice, s));
         WL_CUDA_TRY(cudaMemcpyAsync(in.sc.delta2, h_delta2, sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
@@ -370,7 +415,7 @@ int full_relres(wl_gauge *g, const Vec &be, const Vec &bo, const Vec &xe, const 
     Vec re, ro;
     WL_TRY(make_vec(g, "rr_re", be.prec, nrhs, &re));
     // r_e = b_e - x_e + kappa D_eo x_o ; r_o = b_o - x_o + kappa D_oe x_e
-    WL_TRY(hop_ex(g, xo, re, &be, 1.0, &xe, -1.0, kappa, WL_EVEN, 0, 1, nullptr, s));
+    WL_TRY(hop_ex(g, xo, re, &be, 1.0, &xe, -1.0, kappa, WL_EVEN, 0, 1, nullptr, 0, s));
     Scratch sc;
     WL_TRY(get_scratch(g, nrhs, &sc, s));
     std::vector<double> n2e, n2o;
@@ -379,7 +424,7 @@ int full_relres(wl_gauge *g, const Vec &be, const Vec &bo, const Vec &xe, const 
         n2o = *ro_norm2;
     } else {
         WL_TRY(make_vec(g, "rr_ro", be.prec, nrhs, &ro));
-        WL_TRY(hop_ex(g, xe, ro, &bo, 1.0, &xo, -1.0, kappa, WL_ODD, 0, 1, nullptr, s));
+        WL_TRY(hop_ex(g, xe, ro, &bo, 1.0, &xo, -1.0, kappa, WL_ODD, 0, 1, nullptr, 0, s));
         WL_TRY(norms2_host(g, ro, sc, n2o, s));
     }
     relres.resize(nrhs);
