@@ -167,8 +167,10 @@ int wilson_hop(wl_gauge *g, const void *in, void *out, const void *x, double coe
  *   out_r = x_r + coef * D_{p,1-p} in_r   (x may be NULL: out_r = coef D in_r).
  * Thread blocks are ordered with the rhs index fastest, so the blocks that
  * read a given link run together and the link comes from HBM once per
- * launch; rhs_block (1, 2 or 4; 0 = 1) rhs are handled by one thread, which
- * then loads each link into registers once for all of them. */
+ * launch; rhs_block (1, 2 or 4) rhs are handled by one thread, which then
+ * loads each link into registers once for all of them; rhs_block = 0 uses
+ * the variant chosen by wl_autotune for (prec, n_rhs), or 1 if untuned; a
+ * negative rhs_block selects the autotuner variant -rhs_block directly. */
 int wilson_hop_multi(wl_gauge *g, const void *in, void *out, const void *x, double coef, int prec,
                      int out_parity, int dagger, int n_rhs, size_t rhs_stride, int rhs_block, void *stream);
 
@@ -244,6 +246,15 @@ typedef struct {
 int wl_profile_enable(wl_gauge *g, int on);
 /* Counters per inner precision: out[0] FP64, out[1] FP32, out[2] FP16. */
 int wl_profile_read(wl_gauge *g, wl_kernel_profile out[3]);
+
+/* Autotune the hop for (prec, n_rhs) on this gauge handle: every variant
+ * (right-hand sides per thread, minimum resident blocks per SM) is timed
+ * with CUDA events on the stream and the fastest is cached in the handle;
+ * solvers and wilson_hop_multi with rhs_block = 0 use it.  With the
+ * environment variable WL_AUTOTUNE_CACHE naming a file, results are read
+ * from and appended to it.  *variant = 100 * rhs-per-thread + min-blocks,
+ * *best_us its time per launch.  Synchronises the stream. */
+int wl_autotune(wl_gauge *g, int prec, int n_rhs, void *stream, int *variant, double *best_us);
 
 /* Number of kernels this library has launched in the process so far (direct
  * launches plus, for every replay of a captured graph, its kernel nodes). */

@@ -89,6 +89,7 @@ _sig("wilson_dslash", [_vp, _vp, _vp, _dbl, _int, _int, _vp])
 _sig("wilson_dslash_dag", [_vp, _vp, _vp, _dbl, _int, _int, _vp])
 _sig("bicgstab_solve", [_vp, _vp, _vp, _dbl, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats), _vp])
 _sig("wl_launch_count", [ctypes.POINTER(ctypes.c_longlong)])
+_sig("wl_autotune", [_vp, _int, _int, _vp, ctypes.POINTER(_int), ctypes.POINTER(_dbl)])
 _sig("wl_profile_enable", [_vp, _int])
 _sig("wl_profile_read", [_vp, ctypes.POINTER(KernelProfile)])
 _sig("bicgstab_m_solve", [_vp, _vp, ctypes.POINTER(_vp), ctypes.POINTER(_dbl), _int, ctypes.POINTER(SolverParams),
@@ -307,3 +308,15 @@ def launch_count() -> int:
     n = ctypes.c_longlong()
     _check(_lib.wl_launch_count(ctypes.byref(n)))
     return n.value
+
+
+HOP_VARIANTS = {"f32": [101, 106, 108, 201, 205, 401, 404], "f16": [101, 108, 110, 201, 206, 401, 404],
+                "f64": [101, 103, 201], "df": [101, 105, 106]}
+
+
+def autotune(g: Gauge, prec, nrhs: int, stream=None):
+    """Time every hop variant for (prec, nrhs) and cache the fastest in g.
+    Returns (variant, microseconds per launch)."""
+    v, us = _int(), _dbl()
+    _check(_lib.wl_autotune(g.handle, _prec(prec), int(nrhs), _stream(stream), ctypes.byref(v), ctypes.byref(us)))
+    return v.value, us.value

@@ -1,0 +1,480 @@
+// Wilson hop kernels D_eo / D_oe (Section 2, Eq. 4; Algorithm 1) for sm_103a.
+// Device code shared by the per-precision translation units hop_*.cu.
+//
+// One thread per output site of one parity (the paper's granularity choice,
+// Section 4), NB right-hand sides per thread sharing each link load.  Per
+// direction the neighbour spinor is "shrunk" to two colour vectors with the
+// Table 1 projector vectors, multiplied by the (12-real, row-2 rebuilt)
+// link, and "expanded" back into the accumulator.  The projector entries
+// are unit phases {+-1, +-i}, so shrink and expand are only adds and
+// re/im swaps.  Epilogues fuse the xpay of M_prec and the BiCGstab inner
+// products so that v = A p and t = A s are produced together with the
+// scalars alpha and omega.
+#pragma once
+
+#include "internal.h"
+
+namespace wl {
+
+// Unit phase code: 0 -> 1, 1 -> i, 2 -> -1, 3 -> -i.
+template <int C, typename R>
+__device__ __forceinline__ cx<R> uphase(cx<R> z)
+{
+    if constexpr (C == 0) return z;
+    else if constexpr (C == 1) return {-z.im, z.re};
+    else if constexpr (C == 2) return {-z.re, -z.im};
+    else return {z.im, -z.re};
+}
+
+// Table 1, forward transporter T_mu^+ (spin matrix 1 - gamma_mu):
+// v1^dag = c1 at spin a1, 1 at spin 3;  v2^dag = c2 at spin a2, 1 at spin 2.
+// The backward transporter T_mu^- (1 + gamma_mu) has c1, c2 negated.
+template <int MU> struct Proj;
+template <> struct Proj<0> { static constexpr int a1 = 0, c1 = 1, a2 = 1, c2 = 1; };  // (i,0,0,1) (0,i,1,0)
+template <> struct Proj<1> { static constexpr int a1 = 0, c1 = 2, a2 = 1, c2 = 0; };  // (-1,0,0,1) (0,1,1,0)
+template <> struct Proj<2> { static constexpr int a1 = 1, c1 = 3, a2 = 0, c2 = 1; };  // (0,-i,0,1) (i,0,1,0)
+template <> struct Proj<3> { static constexpr int a1 = 1, c1 = 0, a2 = 0, c2 = 0; };  // (0,1,0,1) (1,0,1,0)
+
+// acc += (neg ? -1 : 1) * L psi (1 -/+ gamma_MU) with L = u (ADJ = false) or
+// u^dag.  PLUS = 0 selects (1 - gamma_MU), PLUS = 1 selects (1 + gamma_MU).
+// Spinor component k = 3*spin + colour.
+template <int MU, int PLUS, bool ADJ, typename R>
+__device__ __forceinline__ void transport(cx<R> (&acc)[12], const cx<R> (&psi)[12], const cx<R> (&u)[9], bool neg)
+{
+    constexpr int A1 = Proj<MU>::a1, A2 = Proj<MU>::a2;
+    constexpr int C1 = (Proj<MU>::c1 + 2 * PLUS) & 3, C2 = (Proj<MU>::c2 + 2 * PLUS) & 3;
+    constexpr int C1c = (4 - C1) & 3, C2c = (4 - C2) & 3;  // conjugate phases
+    // shrink: h_k = psi v_k (v_k = conj(v_k^dag))
+    cx<R> h1[3], h2[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        h1[c] = uphase<C1c>(psi[3 * A1 + c]) + psi[9 + c];
+        h2[c] = uphase<C2c>(psi[3 * A2 + c]) + psi[6 + c];
+    }
+    // colour multiplication
+    cx<R> w1[3], w2[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        cx<R> s1 = {R(0), R(0)}, s2 = {R(0), R(0)};
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            if constexpr (!ADJ) {
+                s1 = cmad(u[3 * a + b], h1[b], s1);
+                s2 = cmad(u[3 * a + b], h2[b], s2);
+            } else {
+                s1 = conjmad(u[3 * b + a], h1[b], s1);
+                s2 = conjmad(u[3 * b + a], h2[b], s2);
+            }
+        }
+        w1[a] = neg ? cx<R>{-s1.re, -s1.im} : s1;
+        w2[a] = neg ? cx<R>{-s2.re, -s2.im} : s2;
+    }
+    // expand: res_s += w_k v_k^dag[s]
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        acc[3 * A1 + c] = acc[3 * A1 + c] + uphase<C1>(w1[c]);
+        acc[9 + c] = acc[9 + c] + w1[c];
+        acc[3 * A2 + c] = acc[3 * A2 + c] + uphase<C2>(w2[c]);
+        acc[6 + c] = acc[6 + c] + w2[c];
+    }
+}
+
+struct HopArgs {
+    Geom g;
+    int out_parity;
+    int nrhs;
+    int ngroups;                 // ceil(nrhs / NB)
+    const void *in;              // rhs r at in + r*rhs_bytes
+    size_t rhs_bytes;
+    const void *links_out;       // links at the output parity (forward links)
+    const void *links_in;        // links at the input parity (backward links)
+    const int *skip;             // optional per-rhs flags: skip rhs r when skip[r * skip_stride] != 0
+    int skip_stride;
+};
+
+__device__ __forceinline__ bool rhs_done(const HopArgs &a, int r)
+{
+    return a.skip != nullptr && __ldcg(a.skip + (size_t)r * a.skip_stride) != 0;
+}
+
+// Accumulate the eight transporters of site i for NB right-hand sides.
+template <int P, bool DAG, int NB, int MU>
+__device__ __forceinline__ void hop_dir(const HopArgs &a, int i, const Coord &c, int rowbase, int r0,
+                                        cx<typename PrecTraits<P>::R> (&acc)[NB][12])
+{
+    using R = typename PrecTraits<P>::R;
+    const Geom &g = a.g;
+    int fwd, bwd;
+    bool sf = false, sb = false;  // antiperiodic sign flips
+    if constexpr (MU == 0) {
+        const int xf = c.x + 1 == g.X ? 0 : c.x + 1;
+        const int xb = c.x == 0 ? g.X - 1 : c.x - 1;
+        fwd = rowbase + (xf >> 1);
+        bwd = rowbase + (xb >> 1);
+    } else if constexpr (MU == 1) {
+        fwd = c.y + 1 == g.Y ? i - (g.Y - 1) * g.Xh : i + g.Xh;
+        bwd = c.y == 0 ? i + (g.Y - 1) * g.Xh : i - g.Xh;
+    } else if constexpr (MU == 2) {
+        const int s = g.Xh * g.Y;
+        fwd = c.z + 1 == g.Z ? i - (g.Z - 1) * s : i + s;
+        bwd = c.z == 0 ? i + (g.Z - 1) * s : i - s;
+    } else {
+        const int s = g.Xh * g.Y * g.Z;
+        const bool lastt = c.t + 1 == g.T, firstt = c.t == 0;
+        fwd = lastt ? i - (g.T - 1) * s : i + s;
+        bwd = firstt ? i + (g.T - 1) * s : i - s;
+        if (g.antiperiodic) {
+            sf = lastt;
+            sb = firstt;
+        }
+    }
+    const size_t dir_off = (size_t)MU * link_dir_bytes(P, g.stride);
+    cx<R> u[9];
+    // forward: U_mu(n) psi_{n+mu} (1 - gamma_mu)   [dagger: (1 + gamma_mu)]
+    LinkIO<P>::load(static_cast<const char *>(a.links_out) + dir_off, g.stride, i, u);
+#pragma unroll
+    for (int r = 0; r < NB; ++r) {
+        if (NB > 1 && r0 + r >= a.nrhs) break;
+        cx<R> psi[12];
+        SpinorIO<P>::load(static_cast<const char *>(a.in) + (size_t)(r0 + r) * a.rhs_bytes, g.stride, fwd, psi);
+        transport<MU, DAG ? 1 : 0, false>(acc[r], psi, u, sf);
+    }
+    // backward: U_mu(n-mu)^dag psi_{n-mu} (1 + gamma_mu)   [dagger: (1 - gamma_mu)]
+    LinkIO<P>::load(static_cast<const char *>(a.links_in) + dir_off, g.stride, bwd, u);
+#pragma unroll
+    for (int r = 0; r < NB; ++r) {
+        if (NB > 1 && r0 + r >= a.nrhs) break;
+        cx<R> psi[12];
+        SpinorIO<P>::load(static_cast<const char *>(a.in) + (size_t)(r0 + r) * a.rhs_bytes, g.stride, bwd, psi);
+        transport<MU, DAG ? 0 : 1, true>(acc[r], psi, u, sb);
+    }
+}
+
+// ---------------------------------------------------------------- epilogues
+
+// out = a1 * x1 + a2 * x2 + coef * acc  (x1, x2 optional), per rhs.
+struct EpiStore {
+    void *out;
+    const void *x1;
+    const void *x2;
+    double a1;
+    double a2;
+    double coef;
+    size_t rhs_bytes;
+    static constexpr int NV = 0;
+    template <int P, int NB>
+    __device__ __forceinline__ void operator()(const HopArgs &a, int i, bool active, int r0,
+                                               cx<typename PrecTraits<P>::R> (&acc)[NB][12]) const
+    {
+        using R = typename PrecTraits<P>::R;
+        if (!active) return;
+#pragma unroll
+        for (int r = 0; r < NB; ++r) {
+            const int rr = r0 + r;
+            if (rr >= a.nrhs || rhs_done(a, rr)) continue;
+            const size_t off = (size_t)rr * rhs_bytes;
+            cx<R> o[12];
+            const R c = Conv<R>::from(coef);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) o[k] = c * acc[r][k];
+            if (x1) {
+                cx<R> v[12];
+                SpinorIO<P>::load(static_cast<const char *>(x1) + off, a.g.stride, i, v);
+#pragma unroll
+                for (int k = 0; k < 12; ++k) o[k] = o[k] + Conv<R>::from(a1) * v[k];
+            }
+            if (x2) {
+                cx<R> v[12];
+                SpinorIO<P>::load(static_cast<const char *>(x2) + off, a.g.stride, i, v);
+#pragma unroll
+                for (int k = 0; k < 12; ++k) o[k] = o[k] + Conv<R>::from(a2) * v[k];
+            }
+            SpinorIO<P>::store(static_cast<char *>(out) + off, a.g.stride, i, o);
+        }
+    }
+};
+
+// Solver epilogues (NB = 1, one rhs per block):
+//   KIND 0: v = p + coef*acc, reduce <rhat, v>  -> alpha = rho / <rhat, v>
+//   KIND 1: t = s + coef*acc, reduce <t, s>, <t, t>  -> omega = <t,s>/<t,t>
+template <int KIND>
+struct EpiReduce {
+    void *out;
+    const void *xin;    // p (KIND 0) or s (KIND 1)
+    const void *rhat;   // KIND 0 only
+    double a1;
+    double coef;
+    const double *coef_dev;  // if set, the coefficient is read from here (graph replays across masses)
+    int blk_off, blk_total;
+    size_t rhs_bytes;
+    BiState *st;
+    double *partials;   // [rhs][block][kRedNV]
+    static constexpr int NV = KIND == 0 ? 2 : 3;
+};
+
+template <int P, bool DAG, int NB>
+__device__ __forceinline__ void hop_accumulate(const HopArgs &a, int i, int r0,
+                                               cx<typename PrecTraits<P>::R> (&acc)[NB][12])
+{
+    const Geom &g = a.g;
+    const Coord c = site_coord(g, i, a.out_parity);
+    const int rowbase = i - (c.x >> 1);
+    hop_dir<P, DAG, NB, 0>(a, i, c, rowbase, r0, acc);
+    hop_dir<P, DAG, NB, 1>(a, i, c, rowbase, r0, acc);
+    hop_dir<P, DAG, NB, 2>(a, i, c, rowbase, r0, acc);
+    hop_dir<P, DAG, NB, 3>(a, i, c, rowbase, r0, acc);
+}
+
+// ------------------------------------------------------- rolled variant
+// The same stencil with the eight transporters in a loop that is not
+// unrolled: projector, link orientation and neighbour are selected per trip
+// (warp-uniform), so the loop body is compiled once.  For the double-float
+// type the unrolled kernel is about 8x larger than the instruction cache
+// and stalls on instruction fetch; this variant keeps the body resident.
+
+// Runtime unit phase, code as in uphase: 0 -> 1, 1 -> i, 2 -> -1, 3 -> -i.
+template <typename R>
+__device__ __forceinline__ cx<R> uphase_rt(int c, cx<R> z)
+{
+    R re = (c & 1) ? z.im : z.re;
+    R im = (c & 1) ? z.re : z.im;
+    if (c == 1 || c == 2) re = -re;
+    if (c >= 2) im = -im;
+    return {re, im};
+}
+
+template <int P, bool DAG>
+__device__ __forceinline__ void hop_accumulate_rolled(const HopArgs &a, int i, cx<typename PrecTraits<P>::R> (&acc)[12])
+{
+    using R = typename PrecTraits<P>::R;
+    const Geom &g = a.g;
+    const Coord c = site_coord(g, i, a.out_parity);
+    const int rowbase = i - (c.x >> 1);
+    const int sy = g.Xh, sz = g.Xh * g.Y, st = g.Xh * g.Y * g.Z;
+    // neighbour indices [mu][fwd, bwd] and time-boundary sign flips
+    int nb[8];
+    nb[0] = rowbase + ((c.x + 1 == g.X ? 0 : c.x + 1) >> 1);
+    nb[1] = rowbase + ((c.x == 0 ? g.X - 1 : c.x - 1) >> 1);
+    nb[2] = c.y + 1 == g.Y ? i - (g.Y - 1) * sy : i + sy;
+    nb[3] = c.y == 0 ? i + (g.Y - 1) * sy : i - sy;
+    nb[4] = c.z + 1 == g.Z ? i - (g.Z - 1) * sz : i + sz;
+    nb[5] = c.z == 0 ? i + (g.Z - 1) * sz : i - sz;
+    nb[6] = c.t + 1 == g.T ? i - (g.T - 1) * st : i + st;
+    nb[7] = c.t == 0 ? i + (g.T - 1) * st : i - st;
+    const bool neg_f = g.antiperiodic && c.t + 1 == g.T, neg_b = g.antiperiodic && c.t == 0;
+#pragma unroll 1
+    for (int d = 0; d < 8; ++d) {
+        const int mu = d >> 1;
+        const bool fwd = (d & 1) == 0;
+        const int j = nb[d];
+        const bool neg = mu == 3 && (fwd ? neg_f : neg_b);
+        // Table 1 (see Proj): a1 in {0,1}, a2 = 1 - a1; phases of the (1 - gamma) projector
+        const int a1 = mu >> 1;
+        const int c1m = (0x0321 >> (4 * mu)) & 3;   // mu: 0->1, 1->2, 2->3, 3->0
+        const int c2m = (0x0101 >> (4 * mu)) & 3;   // mu: 0->1, 1->0, 2->1, 3->0
+        const bool plus = fwd == DAG;               // (1 + gamma) on backward hops (swapped for dagger)
+        const int c1 = (c1m + (plus ? 2 : 0)) & 3, c2 = (c2m + (plus ? 2 : 0)) & 3;
+        const int c1c = (4 - c1) & 3, c2c = (4 - c2) & 3;
+        cx<R> u[9];
+        const size_t dir_off = (size_t)mu * link_dir_bytes(P, g.stride);
+        LinkIO<P>::load(static_cast<const char *>(fwd ? a.links_out : a.links_in) + dir_off, g.stride, fwd ? i : j, u);
+        cx<R> psi[12];
+        SpinorIO<P>::load(a.in, g.stride, j, psi);
+        cx<R> h1[3], h2[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const cx<R> pa1 = a1 == 0 ? psi[k] : psi[3 + k];
+            const cx<R> pa2 = a1 == 0 ? psi[3 + k] : psi[k];
+            h1[k] = uphase_rt(c1c, pa1) + psi[9 + k];
+            h2[k] = uphase_rt(c2c, pa2) + psi[6 + k];
+        }
+        cx<R> w1[3], w2[3];
+        if (fwd) {
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                cx<R> s1 = {R(0), R(0)}, s2 = {R(0), R(0)};
+#pragma unroll
+                for (int b = 0; b < 3; ++b) {
+                    s1 = cmad(u[3 * r + b], h1[b], s1);
+                    s2 = cmad(u[3 * r + b], h2[b], s2);
+                }
+                w1[r] = s1;
+                w2[r] = s2;
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                cx<R> s1 = {R(0), R(0)}, s2 = {R(0), R(0)};
+#pragma unroll
+                for (int b = 0; b < 3; ++b) {
+                    s1 = conjmad(u[3 * b + r], h1[b], s1);
+                    s2 = conjmad(u[3 * b + r], h2[b], s2);
+                }
+                w1[r] = s1;
+                w2[r] = s2;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            if (neg) {
+                w1[k] = {-w1[k].re, -w1[k].im};
+                w2[k] = {-w2[k].re, -w2[k].im};
+            }
+            const cx<R> t1 = uphase_rt(c1, w1[k]), t2 = uphase_rt(c2, w2[k]);
+            acc[k] = acc[k] + (a1 == 0 ? t1 : t2);
+            acc[3 + k] = acc[3 + k] + (a1 == 0 ? t2 : t1);
+            acc[6 + k] = acc[6 + k] + w2[k];
+            acc[9 + k] = acc[9 + k] + w1[k];
+        }
+    }
+}
+
+template <int P, bool DAG, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_hop_rolled(HopArgs a, EpiStore epi)
+{
+    using R = typename PrecTraits<P>::R;
+    const int r = blockIdx.x % a.ngroups;
+    const int sb = blockIdx.x / a.ngroups;
+    if (rhs_done(a, r)) return;
+    const int i = sb * blockDim.x + threadIdx.x;
+    if (i >= a.g.Vh) return;
+    HopArgs b = a;
+    b.in = static_cast<const char *>(a.in) + (size_t)r * a.rhs_bytes;
+    cx<R> acc[1][12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[0][k] = {R(0), R(0)};
+    hop_accumulate_rolled<P, DAG>(b, i, acc[0]);
+    epi.template operator()<P, 1>(a, i, true, r, acc);
+}
+
+template <int P, bool DAG, int NB, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_hop(HopArgs a, EpiStore epi)
+{
+    using R = typename PrecTraits<P>::R;
+    const int grp = blockIdx.x % a.ngroups;
+    const int sb = blockIdx.x / a.ngroups;
+    const int r0 = grp * NB;
+    if (a.skip) {
+        bool all_done = true;
+        for (int r = r0; r < r0 + NB && r < a.nrhs; ++r) all_done &= rhs_done(a, r);
+        if (all_done) return;
+    }
+    const int i = sb * blockDim.x + threadIdx.x;
+    if (i >= a.g.Vh) return;
+    cx<R> acc[NB][12];
+#pragma unroll
+    for (int r = 0; r < NB; ++r)
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc[r][k] = {R(0), R(0)};
+    hop_accumulate<P, DAG, NB>(a, i, r0, acc);
+    epi.template operator()<P, NB>(a, i, true, r0, acc);
+}
+
+template <int P, bool DAG, int KIND>
+__global__ void __launch_bounds__(128) k_hop_reduce(HopArgs a, EpiReduce<KIND> e)
+{
+    using R = typename PrecTraits<P>::R;
+    constexpr int NV = EpiReduce<KIND>::NV;
+    const int r = blockIdx.x % a.nrhs;
+    const int sb = blockIdx.x / a.nrhs;
+    BiState &st = e.st[r];
+    if (__ldcg(&st.done)) return;   // uniform over every block of this rhs
+    const int i = sb * blockDim.x + threadIdx.x;
+    const bool active = i < a.g.Vh;
+    const double coef = e.coef_dev ? __ldcg(e.coef_dev) : e.coef;
+    double red[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) red[k] = 0.0;
+    if (active) {
+        cx<R> acc[1][12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc[0][k] = {R(0), R(0)};
+        hop_accumulate<P, DAG, 1>(a, i, r, acc);
+        const size_t off = (size_t)r * e.rhs_bytes;
+        cx<R> xv[12], o[12];
+        SpinorIO<P>::load(static_cast<const char *>(e.xin) + off, a.g.stride, i, xv);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) o[k] = R(e.a1) * xv[k] + R(coef) * acc[0][k];
+        // Reductions use the stored (rounded) values so that they describe
+        // exactly the vector the next kernels read.
+        SpinorIO<P>::roundtrip(o);
+        SpinorIO<P>::store(static_cast<char *>(e.out) + off, a.g.stride, i, o);
+        if constexpr (KIND == 0) {
+            cx<R> rh[12];
+            SpinorIO<P>::load(static_cast<const char *>(e.rhat) + off, a.g.stride, i, rh);
+            cx<R> d = {R(0), R(0)};
+#pragma unroll
+            for (int k = 0; k < 12; ++k) d = conjmad(rh[k], o[k], d);
+            red[0] = (double)d.re;
+            red[1] = (double)d.im;
+        } else {
+            cx<R> d = {R(0), R(0)};
+            R n = R(0);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+                d = conjmad(o[k], xv[k], d);
+                n = fma(o[k].re, o[k].re, fma(o[k].im, o[k].im, n));
+            }
+            red[0] = (double)d.re;
+            red[1] = (double)d.im;
+            red[2] = (double)n;
+        }
+    }
+    double tot[NV];
+    if (grid_sum<NV>(red, e.partials + (size_t)r * e.blk_total * kRedNV, &st.ticket[KIND], e.blk_off + sb,
+                     e.blk_total, tot) &&
+        threadIdx.x == 0) {
+        if constexpr (KIND == 0) {
+            const double dr = tot[0], di = tot[1];
+            const double den = dr * dr + di * di;
+            if (!(den > 0.0) || !isfinite(den)) {
+                st.breakdown = 1;
+                st.done = 1;
+            } else {  // alpha = rho / <rhat, v>
+                st.alpha_re = (st.rho_re * dr + st.rho_im * di) / den;
+                st.alpha_im = (st.rho_im * dr - st.rho_re * di) / den;
+            }
+        } else {
+            const double tt = tot[2];
+            if (tt > 0.0 && isfinite(tt)) {
+                st.omega_re = tot[0] / tt;
+                st.omega_im = tot[1] / tt;
+            } else {
+                st.omega_re = 0.0;
+                st.omega_im = 0.0;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------ launchers
+// Instantiated per precision in hop_<prec>.cu.
+
+template <int P, bool DAG, int NB, int MINB>
+void launch_k_hop(HopArgs a, const EpiStore &e, cudaStream_t s)
+{
+    a.ngroups = (a.nrhs + NB - 1) / NB;
+    const int nsb = (a.g.Vh + 127) / 128;
+    k_hop<P, DAG, NB, MINB><<<nsb * a.ngroups, 128, 0, s>>>(a, e);
+}
+
+template <int P, bool DAG, int MINB>
+void launch_k_hop_rolled(HopArgs a, const EpiStore &e, cudaStream_t s)
+{
+    a.ngroups = a.nrhs;
+    const int nsb = (a.g.Vh + 127) / 128;
+    k_hop_rolled<P, DAG, MINB><<<nsb * a.nrhs, 128, 0, s>>>(a, e);
+}
+
+template <int P, bool DAG, int KIND>
+void launch_k_hop_reduce(const HopArgs &a, const EpiReduce<KIND> &e, cudaStream_t s)
+{
+    const int nsb = (a.g.Vh + 127) / 128;
+    k_hop_reduce<P, DAG, KIND><<<nsb * a.nrhs, 128, 0, s>>>(a, e);
+}
+
+// Per-precision entry points (hop_<prec>.cu).  variant: see hop_variants().
+template <int P> int hop_launch_prec(int variant, int dagger, const HopArgs &a, const EpiStore &e, cudaStream_t s);
+template <int P> int hop_reduce_launch_prec(int kind, int dagger, const HopArgs &a, const void *epi, cudaStream_t s);
+
+}  // namespace wl

@@ -1,0 +1,54 @@
+// Hop kernel instantiations for F16 (one translation unit per precision so the
+// library builds in parallel).  Variant v = 100 * (rhs per thread) + (minimum resident
+// blocks per SM requested from the register allocator).
+#include "hop.cuh"
+
+namespace wl {
+
+template <>
+int hop_launch_prec<WL_F16>(int v, int dagger, const HopArgs &a, const EpiStore &e, cudaStream_t s)
+{
+    if (dagger) {
+        switch (v / 100) {
+        case 1: launch_k_hop<WL_F16, true, 1, 1>(a, e, s); break;
+        case 2: launch_k_hop<WL_F16, true, 2, 1>(a, e, s); break;
+        case 4: launch_k_hop<WL_F16, true, 4, 1>(a, e, s); break;
+        default: launch_k_hop<WL_F16, true, 1, 1>(a, e, s); break;
+        }
+    } else {
+        switch (v) {
+        case 101: launch_k_hop<WL_F16, false, 1, 1>(a, e, s); break;
+        case 108: launch_k_hop<WL_F16, false, 1, 8>(a, e, s); break;
+        case 110: launch_k_hop<WL_F16, false, 1, 10>(a, e, s); break;
+        case 201: launch_k_hop<WL_F16, false, 2, 1>(a, e, s); break;
+        case 206: launch_k_hop<WL_F16, false, 2, 6>(a, e, s); break;
+        case 401: launch_k_hop<WL_F16, false, 4, 1>(a, e, s); break;
+        case 404: launch_k_hop<WL_F16, false, 4, 4>(a, e, s); break;
+        default:
+            switch (v / 100) {
+            case 1: launch_k_hop<WL_F16, false, 1, 1>(a, e, s); break;
+            case 2: launch_k_hop<WL_F16, false, 2, 1>(a, e, s); break;
+            case 4: launch_k_hop<WL_F16, false, 4, 1>(a, e, s); break;
+            default: launch_k_hop<WL_F16, false, 1, 1>(a, e, s); break;
+            }
+        }
+    }
+    WL_CUDA_TRY(cudaGetLastError());
+    return WL_OK;
+}
+
+template <>
+int hop_reduce_launch_prec<WL_F16>(int kind, int dagger, const HopArgs &a, const void *epi, cudaStream_t s)
+{
+    if (kind == 0) {
+        const auto &e = *static_cast<const EpiReduce<0> *>(epi);
+        dagger ? launch_k_hop_reduce<WL_F16, true, 0>(a, e, s) : launch_k_hop_reduce<WL_F16, false, 0>(a, e, s);
+    } else {
+        const auto &e = *static_cast<const EpiReduce<1> *>(epi);
+        dagger ? launch_k_hop_reduce<WL_F16, true, 1>(a, e, s) : launch_k_hop_reduce<WL_F16, false, 1>(a, e, s);
+    }
+    WL_CUDA_TRY(cudaGetLastError());
+    return WL_OK;
+}
+
+}  // namespace wl

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <map>
+#include <utility>
 #include <mutex>
 #include <vector>
 
@@ -47,6 +48,13 @@ struct Workspace {
 }  // namespace wl
 
 namespace wl {
+// Autotuner result for one (precision, rhs count).
+struct TuneResult {
+    int variant = -1;
+    double us = 0.0;
+    std::vector<std::pair<int, double>> table;  // every candidate timed (fresh tuning only)
+};
+
 // A captured block of inner iterations, reused while its buffers and shape
 // are unchanged (the mass enters through device memory).
 struct GraphCache {
@@ -60,6 +68,7 @@ struct GraphCache {
 
 struct wl_gauge {
     wl::GraphCache inner_graph;
+    std::map<std::pair<int, int>, wl::TuneResult> tune;  // (prec, nrhs) -> chosen hop variant
     wl_lattice *lat;
     unsigned prec_mask;
     void *links[4][2];  // [prec index][parity] -> 4 directions of 12-real links
@@ -120,6 +129,13 @@ int blas_xpay(const Geom &g, const Vec &x, double a, const Vec &y, const Vec &ou
 int blas_recon(const Geom &g, const Vec &bo, const Vec &dx, double kappa, const Vec &xo, double *norm2_dev,
                double *partials, unsigned *tickets, cudaStream_t s);
 
+
+// ---- tune.cu
+// Hop variant for (prec, nrhs): rhs_block > 0 forces rhs_block rhs per
+// thread; rhs_block < 0 selects variant -rhs_block; 0 takes the tuned one.
+const std::vector<int> &hop_variants(int prec);
+int hop_variant_for(wl_gauge *g, int prec, int nrhs, int rhs_block);
+int autotune_hop(wl_gauge *g, int prec, int nrhs, cudaStream_t s, TuneResult *out);
 
 // ---- solver.cu
 int full_relres(wl_gauge *g, const Vec &be, const Vec &bo, const Vec &xe, const Vec &xo, double kappa,

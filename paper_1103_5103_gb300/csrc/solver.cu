@@ -162,7 +162,7 @@ static int run_inner(Inner &in, const wl_solver_params &prm, int max_iter, std::
                      cudaStream_t s)
 {
     const int nrhs = in.nrhs;
-    const int rb = prm.rhs_block > 0 ? prm.rhs_block : 1;
+    const int rb = prm.rhs_block;  // 0: the autotuned hop variant
     Pinned pin;
     WL_TRY(pin.reserve(sizeof(BiState) * nrhs));
     BiState *hs = static_cast<BiState *>(pin.p);
@@ -319,6 +319,10 @@ static int eo_defect_correction(wl_gauge *g, const Vec &bprec, const Vec &x64, d
     const int prec = prm.inner_prec;
     Inner in;
     WL_TRY(make_inner(g, prec, nrhs, kappa, &in, s));
+    if (prm.rhs_block == 0) {  // tune before any graph capture
+        WL_TRY(autotune_hop(g, prec, nrhs, s, nullptr));
+        WL_TRY(autotune_hop(g, x64.prec, nrhs, s, nullptr));
+    }
     Vec r64, tmp64;  // outer precision (FP64 or double-float)
     WL_TRY(make_vec(g, "dc_r64", x64.prec, nrhs, &r64));
     WL_TRY(make_vec(g, "dc_tmp64", x64.prec, nrhs, &tmp64));
@@ -340,8 +344,8 @@ static int eo_defect_correction(wl_gauge *g, const Vec &bprec, const Vec &x64, d
     for (;;) {
         // r = bprec - x + kappa^2 D_eo D_oe x for the rhs still iterating;
         // D_oe x stays in tmp64 (the reconstruction uses the last one)
-        WL_TRY(hop_ex(g, x64, tmp64, nullptr, 0.0, nullptr, 0.0, 1.0, WL_ODD, 0, 1, in.sc.outer_done, 1, s));
-        WL_TRY(hop_ex(g, tmp64, r64, &bprec, 1.0, &x64, -1.0, k2, WL_EVEN, 0, 1, in.sc.outer_done, 1, s));
+        WL_TRY(hop_ex(g, x64, tmp64, nullptr, 0.0, nullptr, 0.0, 1.0, WL_ODD, 0, 0, in.sc.outer_done, 1, s));
+        WL_TRY(hop_ex(g, tmp64, r64, &bprec, 1.0, &x64, -1.0, k2, WL_EVEN, 0, 0, in.sc.outer_done, 1, s));
         WL_TRY(blas_norm2(geo, r64, in.sc.norms, in.sc.partials, in.sc.tickets, s));
         WL_CUDA_TRY(cudaMemcpyAsync(h_rn2, in.sc.norms, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
         WL_CUDA_TRY(cudaStreamSynchronize(s));
@@ -415,7 +419,7 @@ int full_relres(wl_gauge *g, const Vec &be, const Vec &bo, const Vec &xe, const 
     Vec re, ro;
     WL_TRY(make_vec(g, "rr_re", be.prec, nrhs, &re));
     // r_e = b_e - x_e + kappa D_eo x_o ; r_o = b_o - x_o + kappa D_oe x_e
-    WL_TRY(hop_ex(g, xo, re, &be, 1.0, &xe, -1.0, kappa, WL_EVEN, 0, 1, nullptr, 0, s));
+    WL_TRY(hop_ex(g, xo, re, &be, 1.0, &xe, -1.0, kappa, WL_EVEN, 0, 0, nullptr, 0, s));
     Scratch sc;
     WL_TRY(get_scratch(g, nrhs, &sc, s));
     std::vector<double> n2e, n2o;

@@ -1,0 +1,144 @@
+// Project autotuner (spec batching item): for each (precision,
+// number of right-hand sides, lattice) it times the hop variants -- rhs per
+// thread and the minimum number of resident blocks requested from the
+// register allocator -- on the caller's stream with CUDA events, once, and
+// caches the fastest in the gauge handle.  With WL_AUTOTUNE_CACHE set to a
+// file path the choices are also read from / appended to that file, keyed by
+// lattice extents, precision, rhs count and device name.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <sstream>
+#include <string>
+
+#include "internal.h"
+
+namespace wl {
+
+const std::vector<int> &hop_variants(int prec)
+{
+    static const std::vector<int> f32 = {101, 106, 108, 201, 205, 401, 404};
+    static const std::vector<int> f16 = {101, 108, 110, 201, 206, 401, 404};
+    static const std::vector<int> f64 = {101, 103, 201};
+    static const std::vector<int> dfv = {101, 105, 106};
+    static const std::vector<int> none;
+    switch (prec) {
+    case WL_F32: return f32;
+    case WL_F16: return f16;
+    case WL_F64: return f64;
+    case WL_DF: return dfv;
+    default: return none;
+    }
+}
+
+int hop_variant_for(wl_gauge *g, int prec, int nrhs, int rhs_block)
+{
+    if (rhs_block < 0) return -rhs_block;
+    if (rhs_block > 0) return rhs_block * 100 + 1;
+    auto it = g->tune.find(std::make_pair(prec, nrhs));
+    return it == g->tune.end() ? 101 : it->second.variant;
+}
+
+static std::string tune_key(const wl_gauge *g, int prec, int nrhs)
+{
+    cudaDeviceProp prop;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaGetDeviceProperties(&prop, dev);
+    std::ostringstream os;
+    const int *d = g->lat->dims;
+    os << d[0] << "x" << d[1] << "x" << d[2] << "x" << d[3] << " prec" << prec << " nrhs" << nrhs << " ";
+    for (const char *c = prop.name; *c; ++c) os << (*c == ' ' ? '_' : *c);
+    return os.str();
+}
+
+int autotune_hop(wl_gauge *g, int prec, int nrhs, cudaStream_t s, TuneResult *out)
+{
+    const auto key = std::make_pair(prec, nrhs);
+    auto it = g->tune.find(key);
+    if (it != g->tune.end()) {
+        if (out) *out = it->second;
+        return WL_OK;
+    }
+    const std::vector<int> &vs = hop_variants(prec);
+    if (vs.empty()) { set_error("autotune: bad precision"); return WL_ERR_ARG; }
+    TuneResult best;
+    const char *path = std::getenv("WL_AUTOTUNE_CACHE");
+    const std::string fkey = tune_key(g, prec, nrhs);
+    if (path && *path) {
+        std::ifstream f(path);
+        std::string line;
+        while (std::getline(f, line)) {
+            if (line.compare(0, fkey.size(), fkey) == 0 && line.size() > fkey.size() && line[fkey.size()] == ' ') {
+                std::istringstream is(line.substr(fkey.size() + 1));
+                TuneResult r;
+                if (is >> r.variant >> r.us) best = r;
+            }
+        }
+        if (best.variant > 0) {
+            g->tune[key] = best;
+            if (out) *out = best;
+            return WL_OK;
+        }
+    }
+    Vec in, o;
+    WL_TRY(make_vec(g, "tune_in", prec, nrhs, &in));
+    WL_TRY(make_vec(g, "tune_out", prec, nrhs, &o));
+    WL_CUDA_TRY(cudaMemsetAsync(in.ptr, 0, in.rhs_bytes * nrhs, s));
+    cudaEvent_t e0, e1;
+    WL_CUDA_TRY(cudaEventCreate(&e0));
+    WL_CUDA_TRY(cudaEventCreate(&e1));
+    const int reps = 5;
+    for (int v : vs) {
+        int st = WL_OK;
+        for (int k = 0; k < 2 && st == WL_OK; ++k)
+            st = hop_ex(g, in, o, nullptr, 0.0, nullptr, 0.0, 1.0, WL_ODD, 0, -v, nullptr, 0, s);
+        cudaEventRecord(e0, s);
+        for (int k = 0; k < reps && st == WL_OK; ++k)
+            st = hop_ex(g, in, o, nullptr, 0.0, nullptr, 0.0, 1.0, WL_ODD, 0, -v, nullptr, 0, s);
+        cudaEventRecord(e1, s);
+        if (st != WL_OK) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return st;
+        }
+        float ms = 0.f;
+        WL_CUDA_TRY(cudaEventSynchronize(e1));
+        WL_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+        const double us = 1e3 * ms / reps;
+        if (out) out->table.emplace_back(v, us);
+        if (best.variant < 0 || us < best.us) {
+            best.variant = v;
+            best.us = us;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (out) best.table = out->table;
+    g->tune[key] = best;
+    if (out) *out = best;
+    if (path && *path) {
+        std::ofstream f(path, std::ios::app);
+        f << fkey << " " << best.variant << " " << best.us << "\n";
+    }
+    return WL_OK;
+}
+
+}  // namespace wl
+
+using namespace wl;
+
+extern "C" int wl_autotune(wl_gauge *g, int prec, int n_rhs, void *stream, int *variant, double *best_us)
+{
+    if (!g || n_rhs < 1 || !valid_prec(prec) || !(g->prec_mask & prec)) {
+        set_error("wl_autotune: bad argument");
+        return WL_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lock(g->mu);
+    TuneResult r;
+    WL_TRY(autotune_hop(g, prec, n_rhs, as_stream(stream), &r));
+    if (variant) *variant = r.variant;
+    if (best_us) *best_us = r.us;
+    return WL_OK;
+}

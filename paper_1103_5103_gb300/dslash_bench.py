@@ -22,7 +22,7 @@ LINK_B = {"f64": 96, "df": 96, "f32": 48, "f16": 24}
 SPINOR_B = {"f64": 192, "df": 192, "f32": 96, "f16": 52}
 
 
-def run(dims, precs, nrhs=1, launches=50, eps=0.5, seed=2, rhs_block=1):
+def run(dims, precs, nrhs=1, launches=50, eps=0.5, seed=2, rhs_block=1, variants=False):
     lat = api.Lattice(dims)
     U = torch.from_numpy(synth.gauge_field(dims, eps, seed=seed)).cuda()
     g = api.Gauge(lat, U, precs=precs)
@@ -37,19 +37,22 @@ def run(dims, precs, nrhs=1, launches=50, eps=0.5, seed=2, rhs_block=1):
         b = torch.empty_like(a)
         for r in range(nrhs):
             lat.spinor_import(psi, a[r * stride:(r + 1) * stride], prec, 1)
-        for _ in range(5):
-            api.hop_batch(g, a, b, nrhs, stride, 1.0, prec, 0, rhs_block)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(launches):
-            api.hop_batch(g, a, b, nrhs, stride, 1.0, prec, 0, rhs_block)
-        e1.record()
-        torch.cuda.synchronize()
-        s = e0.elapsed_time(e1) / launches / 1e3
-        byts = Vh * 8 * LINK_B[prec] + Vh * nrhs * 2 * SPINOR_B[prec]
-        rows.append({"dims": "x".join(map(str, dims)), "prec": prec, "nrhs": nrhs, "rhs_block": rhs_block,
-                     "us": s * 1e6, "GBps": byts / s / 1e9, "GFLOPs": 1320 * Vh * nrhs / s / 1e9})
+        choices = [-v for v in api.HOP_VARIANTS[prec]] if variants else [rhs_block]
+        for rb in choices:
+            for _ in range(5):
+                api.hop_batch(g, a, b, nrhs, stride, 1.0, prec, 0, rb)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(launches):
+                api.hop_batch(g, a, b, nrhs, stride, 1.0, prec, 0, rb)
+            e1.record()
+            torch.cuda.synchronize()
+            s = e0.elapsed_time(e1) / launches / 1e3
+            byts = Vh * 8 * LINK_B[prec] + Vh * nrhs * 2 * SPINOR_B[prec]
+            rows.append({"dims": "x".join(map(str, dims)), "prec": prec, "nrhs": nrhs,
+                         "variant" if rb < 0 else "rhs_block": -rb if rb < 0 else rb,
+                         "us": s * 1e6, "GBps": byts / s / 1e9, "GFLOPs": 1320 * Vh * nrhs / s / 1e9})
     return rows
 
 
@@ -61,10 +64,12 @@ def main():
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--rhs-block", type=int, default=1)
     ap.add_argument("--launches", type=int, default=50)
+    ap.add_argument("--variants", action="store_true", help="time every autotuner variant")
     args = ap.parse_args()
     for d in args.dims:
         dims = tuple(int(v) for v in d.split("x"))
-        for row in run(dims, args.prec, args.nrhs, args.launches, rhs_block=args.rhs_block):
+        for row in run(dims, args.prec, args.nrhs, args.launches, rhs_block=args.rhs_block,
+                       variants=args.variants):
             print(json.dumps(row), flush=True)
 
 

@@ -171,3 +171,30 @@ def test_hop_multi_rhs(api, prec, rhs_block, nrhs):
         src[odd] = 0
         want = xvs[r] + 0.5 * O.hop(U, dims, src)
         assert rel(out.cpu().numpy()[odd], want[odd]) < TOL[prec], r
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16", "df"])
+def test_every_hop_variant_and_autotune(api, prec):
+    """Every autotuner variant computes the same hop; wl_autotune picks one of them."""
+    dims = (8, 4, 4, 8)
+    U, lat, g = _setup(api, dims, "random")
+    nrhs = 5
+    odd = O.parity_mask(dims)
+    stride = (lat.spinor_bytes(prec) + 255) // 256 * 256
+    a = torch.empty(stride * nrhs, dtype=torch.uint8, device="cuda")
+    srcs = [synth.gaussian_source(dims, 300 + r) for r in range(nrhs)]
+    for r in range(nrhs):
+        lat.spinor_import(_cuda(srcs[r]), a[r * stride:(r + 1) * stride], prec, 0)
+    for v in api.HOP_VARIANTS[prec]:
+        b = torch.zeros_like(a)
+        api.hop_batch(g, a, b, nrhs, stride, 1.0, prec, 1, -v)
+        for r in range(nrhs):
+            out = torch.zeros((lat.volume, 4, 3), dtype=torch.complex128, device="cuda")
+            lat.spinor_export(b[r * stride:(r + 1) * stride], out, prec, 1)
+            src = srcs[r].copy()
+            src[odd] = 0
+            want = O.hop(U, dims, src)
+            assert rel(out.cpu().numpy()[odd], want[odd]) < TOL[prec], (v, r)
+    v, us = api.autotune(g, prec, nrhs)
+    assert v in api.HOP_VARIANTS[prec] and us > 0
+    assert api.autotune(g, prec, nrhs)[0] == v          # cached
