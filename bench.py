@@ -234,13 +234,17 @@ def run_ours(args, cfg):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     step_ms = []
     all_stats = None
-    for _ in range(args.steps):
+    for k in range(args.steps):
         flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if args.ncu_step and k == 0:
+            torch.cuda.profiler.start()   # with ncu --profile-from-start off: capture this step only
         a.record(stream)
         all_stats = step()
         b.record(stream)
         b.synchronize()
+        if args.ncu_step and k == 0:
+            torch.cuda.profiler.stop()
         step_ms.append(a.elapsed_time(b))
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -354,6 +358,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-baseline", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--ncu-step", action="store_true",
+                    help="bracket the first timed step with cudaProfilerStart/Stop (ncu --profile-from-start off)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

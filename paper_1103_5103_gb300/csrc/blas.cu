@@ -382,7 +382,7 @@ int blas_norm2(const Geom &g, const Vec &a, double *out_dev, double *partials, u
 // coefficients per rhs: c[r * k + j] (complex, re/im arrays on the device).
 
 struct LinIn {
-    const void *p[16];
+    const void *p[32];
 };
 
 template <int PO>
@@ -408,7 +408,7 @@ __global__ void __launch_bounds__(kBlock) k_lincomb(Geom g, LinIn in, int k, siz
 int blas_lincomb(const Geom &g, const double *cre_dev, const double *cim_dev, const Vec *const *in, int k,
                  const Vec &out, cudaStream_t s)
 {
-    if (k < 1 || k > 16) { set_error("blas_lincomb: 1..16 inputs"); return WL_ERR_ARG; }
+    if (k < 1 || k > 32) { set_error("blas_lincomb: 1..32 inputs"); return WL_ERR_ARG; }
     LinIn li;
     for (int j = 0; j < k; ++j) li.p[j] = in[j]->ptr;
     if (out.prec == WL_DF)

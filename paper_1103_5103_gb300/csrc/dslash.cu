@@ -17,7 +17,8 @@ static int check_links(wl_gauge *g, int prec)
 }
 
 int hop_ex(wl_gauge *g, const Vec &in, const Vec &out, const Vec *x1, double a1, const Vec *x2, double a2,
-           double coef, int out_parity, int dagger, int rhs_block, const int *skip, int skip_stride, cudaStream_t s)
+           double coef, int out_parity, int dagger, int rhs_block, const int *skip, int skip_stride, cudaStream_t s,
+           const Vec *out_raw)
 {
     WL_TRY(check_links(g, in.prec));
     if (in.prec != out.prec || (x1 && x1->prec != in.prec) || (x2 && x2->prec != in.prec)) {
@@ -37,6 +38,7 @@ int hop_ex(wl_gauge *g, const Vec &in, const Vec &out, const Vec *x1, double a1,
     a.skip_stride = skip_stride;
     EpiStore e;
     e.out = out.ptr;
+    e.out_raw = out_raw ? out_raw->ptr : nullptr;
     e.x1 = x1 ? x1->ptr : nullptr;
     e.x2 = x2 ? x2->ptr : nullptr;
     e.a1 = a1;

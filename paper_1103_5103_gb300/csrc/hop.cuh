@@ -155,6 +155,7 @@ __device__ __forceinline__ void hop_dir(const HopArgs &a, int i, const Coord &c,
 // out = a1 * x1 + a2 * x2 + coef * acc  (x1, x2 optional), per rhs.
 struct EpiStore {
     void *out;
+    void *out_raw;      // optional: also store the bare hop result D in
     const void *x1;
     const void *x2;
     double a1;
@@ -173,6 +174,7 @@ struct EpiStore {
             const int rr = r0 + r;
             if (rr >= a.nrhs || rhs_done(a, rr)) continue;
             const size_t off = (size_t)rr * rhs_bytes;
+            if (out_raw) SpinorIO<P>::store(static_cast<char *>(out_raw) + off, a.g.stride, i, acc[r]);
             cx<R> o[12];
             const R c = Conv<R>::from(coef);
 #pragma unroll

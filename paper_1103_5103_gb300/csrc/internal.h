@@ -98,7 +98,8 @@ int export_spinors(const Geom &g, const Vec &in, void *const *canon, int parity,
 // optional).  rhs_block = rhs per thread (1, 2 or 4).  skip (optional, device)
 // skips rhs r when skip[r * skip_stride] != 0.
 int hop_ex(wl_gauge *g, const Vec &in, const Vec &out, const Vec *x1, double a1, const Vec *x2, double a2,
-           double coef, int out_parity, int dagger, int rhs_block, const int *skip, int skip_stride, cudaStream_t s);
+           double coef, int out_parity, int dagger, int rhs_block, const int *skip, int skip_stride, cudaStream_t s,
+           const Vec *out_raw = nullptr);
 int hop(wl_gauge *g, const Vec &in, const Vec &out, const Vec *x, double coef, int out_parity, int dagger,
         int rhs_block, cudaStream_t s);
 
@@ -121,6 +122,7 @@ int blas_restart(const Geom &g, const Vec &r64, const Vec &r, const Vec &rhat, c
                  BiState *state, double *partials, const int *active, const double *delta2, cudaStream_t s);
 int blas_accum(const Geom &g, const Vec &e, const Vec &x64, const int *active, cudaStream_t s);
 int blas_norm2(const Geom &g, const Vec &a, double *out_dev, double *partials, unsigned *tickets, cudaStream_t s);
+// out = sum_j c_j in_j, 1 <= k <= 32 inputs, coefficients per rhs c[r * k + j]
 int blas_lincomb(const Geom &g, const double *cre_dev, const double *cim_dev, const Vec *const *in, int k,
                  const Vec &out, cudaStream_t s);
 int blas_convert(const Geom &g, const Vec &in, const Vec &out, cudaStream_t s);

@@ -52,7 +52,7 @@ struct Scratch {
     unsigned *tickets = nullptr; // [nrhs * 4]
     int *active = nullptr;       // [nrhs]
     double *delta2 = nullptr;    // [nrhs]
-    double *coef = nullptr;      // [2][nrhs * 16] lincomb coefficients
+    double *coef = nullptr;      // [2][nrhs * 32] lincomb coefficients
     double *kappa2 = nullptr;    // [1] -kappa^2 of the current mass (read by graph-captured kernels)
     int *outer_done = nullptr;   // [nrhs] 1 once the outer residual of rhs r has converged
 };
@@ -75,7 +75,7 @@ static int get_scratch(wl_gauge *g, int nrhs, Scratch *sc, cudaStream_t s)
     sc->active = static_cast<int *>(p);
     WL_TRY(g->ws.get("delta2", sizeof(double) * nrhs, &p));
     sc->delta2 = static_cast<double *>(p);
-    WL_TRY(g->ws.get("coef", sizeof(double) * 2 * nrhs * 16, &p));
+    WL_TRY(g->ws.get("coef", sizeof(double) * 2 * nrhs * 32, &p));
     sc->coef = static_cast<double *>(p);
     WL_TRY(g->ws.get("kappa2", sizeof(double), &p));
     sc->kappa2 = static_cast<double *>(p);
@@ -310,9 +310,15 @@ static double default_inner_tol(int prec)
 //   inner BiCGstab in prec on M_prec e = r to relative residual delta;
 //   x += e (FP64).
 // x64 holds the initial guesses and receives the solutions.
+// y_out (optional) receives D_eo D_oe x of each rhs's final x, so later masses
+// can form their first residual by linear combination.  With r0_given the
+// caller has already put b_prec - M_prec x into dc_r64: the first check
+// uses it without hops; it never declares convergence by itself (that needs
+// a hop-based check, which also produces D_oe x for the reconstruction).
 static int eo_defect_correction(wl_gauge *g, const Vec &bprec, const Vec &x64, double kappa,
                                 const wl_solver_params &prm, const std::vector<double> &bnorm,
-                                std::vector<wl_solver_stats> &stats, cudaStream_t s)
+                                std::vector<wl_solver_stats> &stats, cudaStream_t s, const Vec *y_out = nullptr,
+                                bool r0_given = false)
 {
     const Geom &geo = g->lat->geom;
     const int nrhs = bprec.nrhs;
@@ -341,11 +347,15 @@ static int eo_defect_correction(wl_gauge *g, const Vec &bprec, const Vec &x64, d
     WL_CUDA_TRY(cudaMemcpyAsync(in.sc.kappa2, &mk2, sizeof(double), cudaMemcpyHostToDevice, s));
     WL_CUDA_TRY(cudaMemsetAsync(in.sc.outer_done, 0, sizeof(int) * nrhs, s));
     int total_restarts = 0;
+    bool lincomb_check = r0_given;
     for (;;) {
         // r = bprec - x + kappa^2 D_eo D_oe x for the rhs still iterating;
         // D_oe x stays in tmp64 (the reconstruction uses the last one)
-        WL_TRY(hop_ex(g, x64, tmp64, nullptr, 0.0, nullptr, 0.0, 1.0, WL_ODD, 0, 0, in.sc.outer_done, 1, s));
-        WL_TRY(hop_ex(g, tmp64, r64, &bprec, 1.0, &x64, -1.0, k2, WL_EVEN, 0, 0, in.sc.outer_done, 1, s));
+        if (!lincomb_check) {
+            WL_TRY(hop_ex(g, x64, tmp64, nullptr, 0.0, nullptr, 0.0, 1.0, WL_ODD, 0, 0, in.sc.outer_done, 1, s));
+            WL_TRY(hop_ex(g, tmp64, r64, &bprec, 1.0, &x64, -1.0, k2, WL_EVEN, 0, 0, in.sc.outer_done, 1, s,
+                          y_out));
+        }
         WL_TRY(blas_norm2(geo, r64, in.sc.norms, in.sc.partials, in.sc.tickets, s));
         WL_CUDA_TRY(cudaMemcpyAsync(h_rn2, in.sc.norms, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
         WL_CUDA_TRY(cudaStreamSynchronize(s));
@@ -355,7 +365,12 @@ static int eo_defect_correction(wl_gauge *g, const Vec &bprec, const Vec &x64, d
             h_active[r] = 0;
             if (outer_done[r]) continue;
             if (!std::isfinite(rn)) { outer_done[r] = 1; stats[r].status = WL_ERR_BREAKDOWN; continue; }
-            if (rn <= prm.tol * bnorm[r]) { outer_done[r] = 1; stats[r].status = WL_OK; continue; }
+            if (rn <= prm.tol * bnorm[r]) {
+                if (lincomb_check) continue;  // confirmed by the next, hop-based check
+                outer_done[r] = 1;
+                stats[r].status = WL_OK;
+                continue;
+            }
             if (iters[r] >= prm.max_iter || restarts[r] >= prm.max_restarts || fails[r] >= 5) {
                 outer_done[r] = 1;
                 stats[r].status = fails[r] >= 5 ? WL_ERR_BREAKDOWN : WL_ERR_NOCONV;
@@ -372,7 +387,12 @@ static int eo_defect_correction(wl_gauge *g, const Vec &bprec, const Vec &x64, d
         }
         for (int r = 0; r < nrhs; ++r) h_outer[r] = outer_done[r];
         WL_CUDA_TRY(cudaMemcpyAsync(in.sc.outer_done, h_outer, sizeof(int) * nrhs, cudaMemcpyHostToDevice, s));
-        if (n_active == 0) break;
+        const bool was_lincomb = lincomb_check;
+        lincomb_check = false;
+        if (n_active == 0) {
+            if (was_lincomb) continue;  // every guess already good: confirm with hops
+            break;
+        }
         WL_CUDA_TRY(cudaMemcpyAsync(in.sc.active, h_active, sizeof(int) * nrhs, cudaMemcpyHostToDevice, s));
         WL_CUDA_TRY(cudaMemcpyAsync(in.sc.delta2, h_delta2, sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
         WL_TRY(blas_restart(geo, r64, in.r, in.rhat, in.p, in.e, in.sc.state, in.sc.partials, in.sc.active,
@@ -441,7 +461,8 @@ int full_relres(wl_gauge *g, const Vec &be, const Vec &bo, const Vec &xe, const 
 // x_o = b_o + kappa D_oe x_e, compute the full-lattice residual, export x.
 static int solve_one_mass(wl_gauge *g, const Vec &be, const Vec &bo, const Vec &bprec, const Vec &xe, double m0,
                           const wl_solver_params &prm, const std::vector<double> &bnorm2, void *const *x_out,
-                          int x_out_stride, std::vector<wl_solver_stats> &stats, cudaStream_t s)
+                          int x_out_stride, std::vector<wl_solver_stats> &stats, cudaStream_t s,
+                          const Vec *y_out = nullptr, bool r0_given = false)
 {
     const Geom &geo = g->lat->geom;
     const int nrhs = be.nrhs;
@@ -450,7 +471,7 @@ static int solve_one_mass(wl_gauge *g, const Vec &be, const Vec &bo, const Vec &
     WL_TRY(make_vec(g, "mm_xo", xe.prec, nrhs, &xo));
     std::vector<double> bnorm(nrhs);
     for (int r = 0; r < nrhs; ++r) bnorm[r] = std::sqrt(bnorm2[r]);
-    WL_TRY(eo_defect_correction(g, bprec, xe, kappa, prm, bnorm, stats, s));
+    WL_TRY(eo_defect_correction(g, bprec, xe, kappa, prm, bnorm, stats, s, y_out, r0_given));
     // The last residual check left D_oe x_e (final x_e) in dc_tmp64:
     // x_o = b_o + kappa D_oe x_e and the odd residual in one vector pass.
     Vec dx;
@@ -554,8 +575,8 @@ extern "C" int bicgstab_solve(wl_gauge *g, const void *b, void *x, double m0, co
 extern "C" int multimass_solve(wl_gauge *g, const void *const *b, void *const *x, int n_rhs, const double *m0,
                                int n_mass, const wl_solver_params *p, wl_solver_stats *stats, void *stream)
 {
-    if (!g || !b || !x || !m0 || !stats || n_rhs < 1 || n_mass < 1 || n_mass > 17) {
-        set_error("multimass_solve: bad argument (1 <= n_mass <= 17)");
+    if (!g || !b || !x || !m0 || !stats || n_rhs < 1 || n_mass < 1 || n_mass > 16) {
+        set_error("multimass_solve: bad argument (1 <= n_mass <= 16)");
         return WL_ERR_ARG;
     }
     WL_TRY(check_params(g, p));
@@ -592,10 +613,11 @@ extern "C" int multimass_solve(wl_gauge *g, const void *const *b, void *const *x
     std::vector<int> order(n_mass);
     std::iota(order.begin(), order.end(), 0);
     std::sort(order.begin(), order.end(), [&](int a, int c) { return m0[a] > m0[c]; });
-    std::vector<Vec> sol(n_mass);  // even-site FP64 solutions in solve order
+    std::vector<Vec> sol(n_mass);  // even-site solutions (outer precision) in solve order
+    std::vector<Vec> ys(n_mass);   // y_j = D_eo D_oe x_j of those solutions
     std::vector<wl_solver_stats> st(n_rhs);
     Pinned pin;
-    WL_TRY(pin.reserve(sizeof(double) * 2 * n_rhs * 16));
+    WL_TRY(pin.reserve(sizeof(double) * 128 * n_rhs));
     double *hc = static_cast<double *>(pin.p);
     int worst = WL_OK;
     for (int k = 0; k < n_mass; ++k) {
@@ -603,34 +625,57 @@ extern "C" int multimass_solve(wl_gauge *g, const void *const *b, void *const *x
         const int im = order[k];
         const double m = m0[im];
         WL_TRY(make_vec(g, "mm_sol" + std::to_string(k), PO, n_rhs, &sol[k]));
-        if (k == 0 || p->guess == WL_GUESS_ZERO) {
+        WL_TRY(make_vec(g, "mm_y" + std::to_string(k), PO, n_rhs, &ys[k]));
+        WL_TRY(blas_xpay(geo, be, 1.0 / (2.0 * m + 8.0), dbo, bprec, s));
+        Vec r0;
+        WL_TRY(make_vec(g, "dc_r64", PO, n_rhs, &r0));
+        const double k2 = 1.0 / ((2.0 * m + 8.0) * (2.0 * m + 8.0));
+        const int kk = (p->guess == WL_GUESS_ZERO) ? 0 : k;
+        // Lagrange extrapolation of psi = x / (m + 4) through all previous
+        // masses (Eq. Poly): x_guess = (m + 4) sum_j w_j x_j / (m_j + 4),
+        // w_j = prod_{i != j} (m - m_i) / (m_j - m_i).  By linearity the
+        // first residual b_prec - x_guess + kappa^2 sum_j c_j y_j, with
+        // y_j = D_eo D_oe x_j kept from mass j, needs no hop.
+        std::vector<double> cj(kk);
+        for (int j = 0; j < kk; ++j) {
+            const double mj = m0[order[j]];
+            double w = 1.0;
+            for (int i = 0; i < kk; ++i)
+                if (i != j) {
+                    const double mi = m0[order[i]];
+                    w *= (m - mi) / (mj - mi);
+                }
+            cj[j] = (m + 4.0) * w / (mj + 4.0);
+        }
+        const int ni = 2 * kk + 1;  // inputs of the residual combination
+        for (int r = 0; r < n_rhs; ++r) {
+            for (int j = 0; j < kk; ++j) {
+                hc[r * kk + j] = cj[j];                        // x_guess
+                hc[32 * n_rhs + r * ni + j] = -cj[j];          // - x_j
+                hc[32 * n_rhs + r * ni + kk + j] = k2 * cj[j]; // + kappa^2 y_j
+            }
+            hc[32 * n_rhs + r * ni + 2 * kk] = 1.0;            // + b_prec
+        }
+        std::fill(hc + 64 * n_rhs, hc + 128 * n_rhs, 0.0);  // imaginary parts
+        WL_CUDA_TRY(cudaMemcpyAsync(sc.coef, hc, sizeof(double) * 128 * n_rhs, cudaMemcpyHostToDevice, s));
+        if (kk == 0) {
             WL_CUDA_TRY(cudaMemsetAsync(sol[k].ptr, 0, sol[k].rhs_bytes * n_rhs, s));
         } else {
-            // Lagrange extrapolation of psi = x / (m + 4) through all previous
-            // masses (Eq. Poly): x_guess = (m + 4) sum_j w_j x_j / (m_j + 4),
-            // w_j = prod_{i != j} (m - m_i) / (m_j - m_i).
-            for (int j = 0; j < k; ++j) {
-                const double mj = m0[order[j]];
-                double w = 1.0;
-                for (int i = 0; i < k; ++i)
-                    if (i != j) {
-                        const double mi = m0[order[i]];
-                        w *= (m - mi) / (mj - mi);
-                    }
-                const double c = (m + 4.0) * w / (mj + 4.0);
-                for (int r = 0; r < n_rhs; ++r) {
-                    hc[r * k + j] = c;
-                    hc[n_rhs * 16 + r * k + j] = 0.0;
-                }
+            std::vector<const Vec *> ins(kk);
+            for (int j = 0; j < kk; ++j) ins[j] = &sol[j];
+            WL_TRY(blas_lincomb(geo, sc.coef, sc.coef + 64 * n_rhs, ins.data(), kk, sol[k], s));
+        }
+        {
+            std::vector<const Vec *> ins(ni);
+            for (int j = 0; j < kk; ++j) {
+                ins[j] = &sol[j];
+                ins[kk + j] = &ys[j];
             }
-            WL_CUDA_TRY(cudaMemcpyAsync(sc.coef, hc, sizeof(double) * 2 * n_rhs * 16, cudaMemcpyHostToDevice, s));
-            std::vector<const Vec *> ins(k);
-            for (int j = 0; j < k; ++j) ins[j] = &sol[j];
-            WL_TRY(blas_lincomb(geo, sc.coef, sc.coef + n_rhs * 16, ins.data(), k, sol[k], s));
+            ins[2 * kk] = &bprec;
+            WL_TRY(blas_lincomb(geo, sc.coef + 32 * n_rhs, sc.coef + 96 * n_rhs, ins.data(), ni, r0, s));
         }
         for (int r = 0; r < n_rhs; ++r) std::memset(&st[r], 0, sizeof(wl_solver_stats));
-        WL_TRY(blas_xpay(geo, be, 1.0 / (2.0 * m + 8.0), dbo, bprec, s));
-        WL_TRY(solve_one_mass(g, be, bo, bprec, sol[k], m, *p, bn2, x + im, n_mass, st, s));
+        WL_TRY(solve_one_mass(g, be, bo, bprec, sol[k], m, *p, bn2, x + im, n_mass, st, s, &ys[k], true));
         WL_CUDA_TRY(cudaStreamSynchronize(s));
         const double sec = tm.sec();
         for (int r = 0; r < n_rhs; ++r) {
