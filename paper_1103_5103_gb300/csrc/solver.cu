@@ -52,7 +52,7 @@ struct Scratch {
     unsigned *tickets = nullptr; // [nrhs * 4]
     int *active = nullptr;       // [nrhs]
     double *delta2 = nullptr;    // [nrhs]
-    double *coef = nullptr;      // [2][nrhs * 32] lincomb coefficients
+    double *coef = nullptr;      // [4][nrhs * 32] lincomb coefficients (two sets, re and im)
     double *kappa2 = nullptr;    // [1] -kappa^2 of the current mass (read by graph-captured kernels)
     int *outer_done = nullptr;   // [nrhs] 1 once the outer residual of rhs r has converged
 };
@@ -75,7 +75,7 @@ static int get_scratch(wl_gauge *g, int nrhs, Scratch *sc, cudaStream_t s)
     sc->active = static_cast<int *>(p);
     WL_TRY(g->ws.get("delta2", sizeof(double) * nrhs, &p));
     sc->delta2 = static_cast<double *>(p);
-    WL_TRY(g->ws.get("coef", sizeof(double) * 2 * nrhs * 32, &p));
+    WL_TRY(g->ws.get("coef", sizeof(double) * 4 * nrhs * 32, &p));
     sc->coef = static_cast<double *>(p);
     WL_TRY(g->ws.get("kappa2", sizeof(double), &p));
     sc->kappa2 = static_cast<double *>(p);
