@@ -350,13 +350,13 @@ __global__ void __launch_bounds__(kBlock) k_norm2(Geom g, Vec a, double *out, do
     if (q.i < g.Vh) {
         cx<RT<P>> v[12];
         ld<P>(a, q.r, g.stride, q.i, v);
-        double n = 0.0;
+        typename NormT<RT<P>>::T n = 0;
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
-            const double re = to_double(v[k].re), im = to_double(v[k].im);
-            n += re * re + im * im;
+            norm_acc(n, v[k].re);
+            norm_acc(n, v[k].im);
         }
-        red[0] = n;
+        red[0] = (double)n;
     }
     double tot[1];
     if (grid_sum<1>(red, partials + (size_t)q.r * q.nsb * kRedNV, &tickets[q.r], q.sb, q.nsb, tot) &&
@@ -385,40 +385,62 @@ struct LinIn {
     const void *p[32];
 };
 
+// out = sum_{j<k} c_j in_j and, optionally, out2 = sum_{j<k2} c2_j in_j
+// (k <= k2: the first k inputs are shared and read once).  Coefficients are
+// real, per rhs: c[r * k + j], c2[r * k2 + j].
 template <int PO>
-__global__ void __launch_bounds__(kBlock) k_lincomb(Geom g, LinIn in, int k, size_t rhs_bytes, int nrhs,
-                                                    const double *cre, const double *cim, Vec out)
+__global__ void __launch_bounds__(kBlock) k_lincomb(Geom g, LinIn in, int k, int k2, size_t rhs_bytes, int nrhs,
+                                                    const double *c1, const double *c2, Vec out, Vec out2)
 {
     using R = RT<PO>;
     const SiteIdx q = site_idx(nrhs);
     if (q.i >= g.Vh) return;
-    cx<R> acc[12];
+    cx<R> acc[12], acc2[12];
 #pragma unroll
-    for (int c = 0; c < 12; ++c) acc[c] = {R(0), R(0)};
-    for (int j = 0; j < k; ++j) {
-        const cx<R> w = {Conv<R>::from(cre[q.r * k + j]), Conv<R>::from(cim[q.r * k + j])};
+    for (int c = 0; c < 12; ++c) acc[c] = acc2[c] = {R(0), R(0)};
+    const int kmax = k > k2 ? k : k2;
+    for (int j = 0; j < kmax; ++j) {
         cx<R> v[12];
         SpinorIO<PO>::load(static_cast<const char *>(in.p[j]) + (size_t)q.r * rhs_bytes, g.stride, q.i, v);
+        if (j < k) {
+            const R w = Conv<R>::from(c1[q.r * k + j]);
 #pragma unroll
-        for (int c = 0; c < 12; ++c) acc[c] = cmad(w, v[c], acc[c]);
+            for (int c = 0; c < 12; ++c) acc[c] = {fma(w, v[c].re, acc[c].re), fma(w, v[c].im, acc[c].im)};
+        }
+        if (j < k2) {
+            const R w = Conv<R>::from(c2[q.r * k2 + j]);
+#pragma unroll
+            for (int c = 0; c < 12; ++c) acc2[c] = {fma(w, v[c].re, acc2[c].re), fma(w, v[c].im, acc2[c].im)};
+        }
     }
-    SpinorIO<PO>::store(out.rhs(q.r), g.stride, q.i, acc);
+    if (k > 0) SpinorIO<PO>::store(out.rhs(q.r), g.stride, q.i, acc);
+    if (k2 > 0) SpinorIO<PO>::store(out2.rhs(q.r), g.stride, q.i, acc2);
 }
 
-int blas_lincomb(const Geom &g, const double *cre_dev, const double *cim_dev, const Vec *const *in, int k,
-                 const Vec &out, cudaStream_t s)
+int blas_lincomb2(const Geom &g, const double *c1_dev, const Vec *const *in, int k, const Vec *out,
+                  const double *c2_dev, int k2, const Vec *out2, cudaStream_t s)
 {
-    if (k < 1 || k > 32) { set_error("blas_lincomb: 1..32 inputs"); return WL_ERR_ARG; }
+    if (k < 0 || k2 < 0 || k + k2 < 1 || k > 32 || k2 > 32) { set_error("blas_lincomb: 1..32 inputs"); return WL_ERR_ARG; }
     LinIn li;
-    for (int j = 0; j < k; ++j) li.p[j] = in[j]->ptr;
-    if (out.prec == WL_DF)
-        k_lincomb<WL_DF><<<grid_of(g, out.nrhs), kBlock, 0, s>>>(g, li, k, out.rhs_bytes, out.nrhs, cre_dev, cim_dev, out);
-    else if (out.prec == WL_F64)
-        k_lincomb<WL_F64><<<grid_of(g, out.nrhs), kBlock, 0, s>>>(g, li, k, out.rhs_bytes, out.nrhs, cre_dev, cim_dev, out);
+    const int kmax = k > k2 ? k : k2;
+    for (int j = 0; j < kmax; ++j) li.p[j] = in[j]->ptr;
+    const Vec &o = k > 0 ? *out : *out2;
+    Vec o2 = k2 > 0 ? *out2 : o;
+    const Vec o1 = k > 0 ? *out : o2;
+    if (o.prec == WL_DF)
+        k_lincomb<WL_DF><<<grid_of(g, o.nrhs), kBlock, 0, s>>>(g, li, k, k2, o.rhs_bytes, o.nrhs, c1_dev, c2_dev, o1, o2);
+    else if (o.prec == WL_F64)
+        k_lincomb<WL_F64><<<grid_of(g, o.nrhs), kBlock, 0, s>>>(g, li, k, k2, o.rhs_bytes, o.nrhs, c1_dev, c2_dev, o1, o2);
     else { set_error("blas_lincomb: outer precision only"); return WL_ERR_ARG; }
     WL_CUDA_TRY(cudaGetLastError());
     note_launch(s);
     return WL_OK;
+}
+
+int blas_lincomb(const Geom &g, const double *cre_dev, const double *, const Vec *const *in, int k,
+                 const Vec &out, cudaStream_t s)
+{
+    return blas_lincomb2(g, cre_dev, in, k, &out, nullptr, 0, nullptr, s);
 }
 
 // ------------------------------ even-odd reconstruction with its residual
@@ -438,17 +460,17 @@ __global__ void __launch_bounds__(kBlock) k_recon(Geom g, Vec bo, Vec dx, double
         SpinorIO<PO>::load(bo.rhs(q.r), g.stride, q.i, b);
         SpinorIO<PO>::load(dx.rhs(q.r), g.stride, q.i, d);
         const R k = Conv<R>::from(kappa);
-        double n = 0.0;
+        typename NormT<R>::T n = 0;
 #pragma unroll
         for (int c = 0; c < 12; ++c) {
             const cx<R> kd = k * d[c];
             x[c] = b[c] + kd;
             const cx<R> ro = (b[c] - x[c]) + kd;
-            const double re = to_double(ro.re), im = to_double(ro.im);
-            n += re * re + im * im;
+            norm_acc(n, ro.re);
+            norm_acc(n, ro.im);
         }
         SpinorIO<PO>::store(xo.rhs(q.r), g.stride, q.i, x);
-        red[0] = n;
+        red[0] = (double)n;
     }
     double tot[1];
     if (grid_sum<1>(red, partials + (size_t)q.r * q.nsb * kRedNV, &tickets[q.r], q.sb, q.nsb, tot) &&

@@ -139,13 +139,17 @@ __device__ __forceinline__ df df_fast_two_sum(float a, float b)  // |a| >= |b|
     return df(s, b - (s - a));
 }
 
+// Arithmetic results are kept "lazy": the low word collects the exact
+// rounding error of the high operation plus the low-order terms, without the
+// final renormalisation; |lo| stays within a few ulp(hi), so further
+// operations lose nothing measurable, and SpinorIO<WL_DF>::store
+// renormalises before anything is written to memory.
 __device__ __forceinline__ df operator+(df a, df b)
 {
     const float s = a.hi + b.hi;
     const float bb = s - a.hi;
-    float e = (a.hi - (s - bb)) + (b.hi - bb);  // two-sum error of the high parts
-    e += a.lo + b.lo;
-    return df_fast_two_sum(s, e);
+    const float e = (a.hi - (s - bb)) + (b.hi - bb);  // Knuth two-sum error of the high parts
+    return df(s, e + (a.lo + b.lo));
 }
 __device__ __forceinline__ df operator-(df a) { return df(-a.hi, -a.lo); }
 __device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
@@ -155,8 +159,9 @@ __device__ __forceinline__ df operator*(df a, df b)
     float e = fmaf(a.hi, b.hi, -p);  // exact error of the high product
     e = fmaf(a.hi, b.lo, e);
     e = fmaf(a.lo, b.hi, e);
-    return df_fast_two_sum(p, e);
+    return df(p, e);
 }
+__device__ __forceinline__ df df_normalize(df a) { return df_fast_two_sum(a.hi, a.lo); }
 __device__ __forceinline__ df fma(df a, df b, df c) { return a * b + c; }
 __device__ __forceinline__ double to_double(df a) { return (double)a.hi + (double)a.lo; }
 __device__ __forceinline__ double to_double(float a) { return (double)a; }
@@ -199,6 +204,16 @@ __host__ __device__ constexpr int link_site_bytes(int prec)
 {
     return prec == WL_F64 ? 96 : prec == WL_F32 ? 48 : prec == WL_DF ? 96 : 24;
 }
+
+// Squared magnitude accumulated per site: FP32 for FP32 and double-float
+// data (high words only -- a relative 2^-23 on a norm is plenty for
+// stopping tests and reported residuals), FP64 for FP64 data.  Sites are
+// then summed in FP64.
+__device__ __forceinline__ void norm_acc(float &n, float x) { n = fmaf(x, x, n); }
+__device__ __forceinline__ void norm_acc(float &n, df x) { n = fmaf(x.hi, x.hi, fmaf(2.0f * x.hi, x.lo, n)); }
+__device__ __forceinline__ void norm_acc(double &n, double x) { n = fma(x, x, n); }
+template <typename R> struct NormT { using T = float; };
+template <> struct NormT<double> { using T = double; };
 
 template <typename To, typename From>
 __device__ __forceinline__ cx<To> cconv(cx<From> z)
@@ -336,7 +351,10 @@ template <> struct SpinorIO<WL_DF> {
     {
         float4 *p = static_cast<float4 *>(base);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) p[(size_t)k * stride + i] = make_float4(v[k].re.hi, v[k].re.lo, v[k].im.hi, v[k].im.lo);
+        for (int k = 0; k < 12; ++k) {
+            const df re = df_normalize(v[k].re), im = df_normalize(v[k].im);
+            p[(size_t)k * stride + i] = make_float4(re.hi, re.lo, im.hi, im.lo);
+        }
     }
 };
 

@@ -122,9 +122,13 @@ int blas_restart(const Geom &g, const Vec &r64, const Vec &r, const Vec &rhat, c
                  BiState *state, double *partials, const int *active, const double *delta2, cudaStream_t s);
 int blas_accum(const Geom &g, const Vec &e, const Vec &x64, const int *active, cudaStream_t s);
 int blas_norm2(const Geom &g, const Vec &a, double *out_dev, double *partials, unsigned *tickets, cudaStream_t s);
-// out = sum_j c_j in_j, 1 <= k <= 32 inputs, coefficients per rhs c[r * k + j]
+// out = sum_j c_j in_j, 1 <= k <= 32 inputs, real coefficients per rhs
+// c[r * k + j] (cim_dev is ignored)
 int blas_lincomb(const Geom &g, const double *cre_dev, const double *cim_dev, const Vec *const *in, int k,
                  const Vec &out, cudaStream_t s);
+// out = sum_{j<k} c1_j in_j and out2 = sum_{j<k2} c2_j in_j in one pass
+int blas_lincomb2(const Geom &g, const double *c1_dev, const Vec *const *in, int k, const Vec *out,
+                  const double *c2_dev, int k2, const Vec *out2, cudaStream_t s);
 int blas_convert(const Geom &g, const Vec &in, const Vec &out, cudaStream_t s);
 int blas_xpay(const Geom &g, const Vec &x, double a, const Vec &y, const Vec &out, cudaStream_t s);  // out = x + a y
 // x_o = b_o + kappa Dx and ||b_o - x_o + kappa Dx||^2 per rhs into norm2_dev

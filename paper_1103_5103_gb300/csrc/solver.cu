@@ -656,23 +656,17 @@ extern "C" int multimass_solve(wl_gauge *g, const void *const *b, void *const *x
             }
             hc[32 * n_rhs + r * ni + 2 * kk] = 1.0;            // + b_prec
         }
-        std::fill(hc + 64 * n_rhs, hc + 128 * n_rhs, 0.0);  // imaginary parts
-        WL_CUDA_TRY(cudaMemcpyAsync(sc.coef, hc, sizeof(double) * 128 * n_rhs, cudaMemcpyHostToDevice, s));
-        if (kk == 0) {
-            WL_CUDA_TRY(cudaMemsetAsync(sol[k].ptr, 0, sol[k].rhs_bytes * n_rhs, s));
-        } else {
-            std::vector<const Vec *> ins(kk);
-            for (int j = 0; j < kk; ++j) ins[j] = &sol[j];
-            WL_TRY(blas_lincomb(geo, sc.coef, sc.coef + 64 * n_rhs, ins.data(), kk, sol[k], s));
-        }
+        WL_CUDA_TRY(cudaMemcpyAsync(sc.coef, hc, sizeof(double) * 64 * n_rhs, cudaMemcpyHostToDevice, s));
+        if (kk == 0) WL_CUDA_TRY(cudaMemsetAsync(sol[k].ptr, 0, sol[k].rhs_bytes * n_rhs, s));
         {
+            // x_guess and the first residual in one pass over the stored x_j, y_j
             std::vector<const Vec *> ins(ni);
             for (int j = 0; j < kk; ++j) {
                 ins[j] = &sol[j];
                 ins[kk + j] = &ys[j];
             }
             ins[2 * kk] = &bprec;
-            WL_TRY(blas_lincomb(geo, sc.coef + 32 * n_rhs, sc.coef + 96 * n_rhs, ins.data(), ni, r0, s));
+            WL_TRY(blas_lincomb2(geo, sc.coef, ins.data(), kk, &sol[k], sc.coef + 32 * n_rhs, ni, &r0, s));
         }
         for (int r = 0; r < n_rhs; ++r) std::memset(&st[r], 0, sizeof(wl_solver_stats));
         WL_TRY(solve_one_mass(g, be, bo, bprec, sol[k], m, *p, bn2, x + im, n_mass, st, s, &ys[k], true));
