@@ -133,10 +133,14 @@ struct df {
 
 using ::fma;  // keep the float/double overloads visible next to the df one
 
+// The error-free transformations below must be evaluated exactly as
+// written: the compiler may otherwise contract a product with a later sum
+// into one FMA, which changes the rounding the error terms assume.  The
+// __fmul_rn / __fadd_rn / __fsub_rn intrinsics are never contracted.
 __device__ __forceinline__ df df_fast_two_sum(float a, float b)  // |a| >= |b|
 {
-    const float s = a + b;
-    return df(s, b - (s - a));
+    const float s = __fadd_rn(a, b);
+    return df(s, __fsub_rn(b, __fsub_rn(s, a)));
 }
 
 // Arithmetic results are kept "lazy": the low word collects the exact
@@ -146,16 +150,17 @@ __device__ __forceinline__ df df_fast_two_sum(float a, float b)  // |a| >= |b|
 // renormalises before anything is written to memory.
 __device__ __forceinline__ df operator+(df a, df b)
 {
-    const float s = a.hi + b.hi;
-    const float bb = s - a.hi;
-    const float e = (a.hi - (s - bb)) + (b.hi - bb);  // Knuth two-sum error of the high parts
-    return df(s, e + (a.lo + b.lo));
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float bb = __fsub_rn(s, a.hi);
+    // Knuth two-sum error of the high parts
+    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+    return df(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
 }
 __device__ __forceinline__ df operator-(df a) { return df(-a.hi, -a.lo); }
 __device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
 __device__ __forceinline__ df operator*(df a, df b)
 {
-    const float p = a.hi * b.hi;
+    const float p = __fmul_rn(a.hi, b.hi);
     float e = fmaf(a.hi, b.hi, -p);  // exact error of the high product
     e = fmaf(a.hi, b.lo, e);
     e = fmaf(a.lo, b.hi, e);
