@@ -215,7 +215,11 @@ __host__ __device__ constexpr int link_site_bytes(int prec)
 // stopping tests and reported residuals), FP64 for FP64 data.  Sites are
 // then summed in FP64.
 __device__ __forceinline__ void norm_acc(float &n, float x) { n = fmaf(x, x, n); }
-__device__ __forceinline__ void norm_acc(float &n, df x) { n = fmaf(x.hi, x.hi, fmaf(2.0f * x.hi, x.lo, n)); }
+__device__ __forceinline__ void norm_acc(float &n, df x)
+{
+    const float v = x.hi + x.lo;  // lazy values may have |lo| ~ |hi|: square the sum, never negative
+    n = fmaf(v, v, n);
+}
 __device__ __forceinline__ void norm_acc(double &n, double x) { n = fma(x, x, n); }
 template <typename R> struct NormT { using T = float; };
 template <> struct NormT<double> { using T = double; };
