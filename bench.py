@@ -49,7 +49,7 @@ SPINOR_B = {"f64": 192, "df": 192, "f32": 96, "f16": 52}
 # oracle BiCGstab iterations and scales by this many inner iterations per
 # step (the paper scheme's FP32-inner count on the c3 workload, from the
 # optimised arm's own JSON line `iterations_per_step`).
-REF_ITERS_PER_STEP = {"c3": None, "c2": None}
+REF_ITERS_PER_STEP = {"c3": 963, "c2": None}
 
 
 def sources(cfg):
