@@ -225,6 +225,27 @@ int bicgstab_m_solve(wl_gauge *g, const void *b, void *const *x, const double *m
 int multimass_solve(wl_gauge *g, const void *const *b, void *const *x, int n_rhs, const double *m0,
                     int n_mass, const wl_solver_params *p, wl_solver_stats *stats, void *stream);
 
+/* Backward of the multi-mass solve (gradient of a real loss L(x_1..x_n),
+ * x_i = M_k(m0[i])^{-1} b, Eq. 3-4 in kappa form).  g[i] is the loss
+ * gradient with respect to x_i in PyTorch's complex convention,
+ * dL/dRe x + i dL/dIm x (canonical complex128, device).  For each mass the
+ * adjoint system M_k^dag lam = g[i] is solved through M^dag = gamma5 M gamma5
+ * (lam = gamma5 M^{-1} gamma5 g, the forward solver with parameters p), then
+ *   dU  [mu][n][a] += -kappa Im tr(T_a W_mu(n)),  T_a = lambda_a / 2,
+ *        W_mu(n) = s [U_mu(n) x_{n+mu} (1 - gamma_mu) lam_n^dag
+ *                     - x_n (1 + gamma_mu) lam_{n+mu}^dag U_mu(n)^dag],
+ *        s = -1 across the antiperiodic time boundary: the derivative along
+ *        U_mu(n) -> exp(i h T_a) U_mu(n) at h = 0 (device doubles [4][V][8],
+ *        accumulated: the caller zeroes them);
+ *   dm0 [i] = -Re <lam, 2 kappa^2 D x_i>   (host doubles, n_mass);
+ *   db      += lam                           (device complex128, optional).
+ * x[i] may be NULL (or x itself NULL): that solution is re-solved instead of
+ * stored.  Any of dU, dm0, db may be NULL (not computed).  Needs FP64 or
+ * double-float links.  Synchronises the stream. */
+int wilson_solve_backward(wl_gauge *g, const void *b, const void *const *x, const void *const *g_x,
+                          const double *m0, int n_mass, const wl_solver_params *p, double *dU, double *dm0,
+                          void *db, void *stream);
+
 /* ------------------------------------------------------------ profiling */
 
 /* Live timing of the dominant kernel, the hop D_oe p that opens every inner

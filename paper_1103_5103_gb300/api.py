@@ -92,6 +92,8 @@ _sig("wl_launch_count", [ctypes.POINTER(ctypes.c_longlong)])
 _sig("wl_autotune", [_vp, _int, _int, _vp, ctypes.POINTER(_int), ctypes.POINTER(_dbl)])
 _sig("wl_profile_enable", [_vp, _int])
 _sig("wl_profile_read", [_vp, ctypes.POINTER(KernelProfile)])
+_sig("wilson_solve_backward", [_vp, _vp, _vp, ctypes.POINTER(_vp), ctypes.POINTER(_dbl), _int,
+                               ctypes.POINTER(SolverParams), _vp, ctypes.POINTER(_dbl), _vp, _vp])
 _sig("bicgstab_m_solve", [_vp, _vp, ctypes.POINTER(_vp), ctypes.POINTER(_dbl), _int, ctypes.POINTER(SolverParams),
                           ctypes.POINTER(SolverStats), _vp])
 _sig("multimass_solve", [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _int, ctypes.POINTER(_dbl), _int,
@@ -320,3 +322,24 @@ def autotune(g: Gauge, prec, nrhs: int, stream=None):
     v, us = _int(), _dbl()
     _check(_lib.wl_autotune(g.handle, _prec(prec), int(nrhs), _stream(stream), ctypes.byref(v), ctypes.byref(us)))
     return v.value, us.value
+
+
+def solve_backward(g: Gauge, b: torch.Tensor, grads, masses, xs=None, prm: SolverParams | None = None,
+                   want_links=True, want_masses=True, want_source=True, stream=None):
+    """wilson_solve_backward.  Returns (dU (4, V, 8) float64 or None,
+    dm0 list or None, db (V, 4, 3) complex128 or None)."""
+    prm = prm or params()
+    V = g.lat.volume
+    nm = len(masses)
+    gp = (_vp * nm)(*[_canon(t, V, "g").value for t in grads])
+    xp = None
+    if xs is not None:
+        xp = (_vp * nm)(*[(_canon(x, V, "x").value if x is not None else None) for x in xs])
+    ms = (_dbl * nm)(*[float(m) for m in masses])
+    dU = torch.zeros((4, V, 8), dtype=torch.float64, device=b.device) if want_links else None
+    dm = (_dbl * nm)() if want_masses else None
+    db = torch.zeros_like(b) if want_source else None
+    _check(_lib.wilson_solve_backward(g.handle, _canon(b, V, "b"), xp, gp, ms, nm, ctypes.byref(prm),
+                                      None if dU is None else _ptr(dU), dm,
+                                      None if db is None else _ptr(db), _stream(stream)))
+    return dU, (list(dm) if dm is not None else None), db
