@@ -186,6 +186,25 @@ int wilson_dslash(wl_gauge *g, const void *in, void *out, double kappa, int prec
 int wilson_dslash_dag(wl_gauge *g, const void *in, void *out, double kappa, int prec, int op,
                       void *stream);
 
+/* The same operator application as wilson_dslash / wilson_dslash_dag
+ * (dagger = 0 / 1), for callers that must not allocate device memory: code
+ * running while another component owns the allocator (a caching allocator
+ * with a hard cap, a pool that must not fragment, a loop that cannot take
+ * cudaMalloc's implicit synchronisation).  The paper has no counterpart.
+ * wilson_dslash takes four internal half-lattice spinors from the gauge
+ * handle's workspace and allocates it on first use; this entry point takes
+ * them from a fixed 64 MiB array compiled into the library (held by every
+ * GPU that loads the library until the process exits) and calls no
+ * cudaMalloc, cudaFree or allocating routine.  Lattices whose four
+ * half-lattice spinors of precision prec exceed 64 MiB are rejected with
+ * WL_ERR_ARG.  The first call on a device looks up the array's device
+ * address (with lazy module loading this also makes the driver load the
+ * library's module); make that first call before any stream capture.  All
+ * calls share the array: calls whose work overlaps on the GPU (different
+ * streams or threads) race on it -- order them on one stream. */
+int wilson_dslash_noalloc(wl_gauge *g, const void *in, void *out, double kappa, int prec, int op, int dagger,
+                          void *stream);
+
 /* --------------------------------------------------------------- solvers */
 
 /* Solve M_k(m0) x = b (Section 6) with BiCGstab.  b, x: canonical

@@ -86,6 +86,7 @@ _sig("wl_gauge_destroy", [_vp])
 _sig("wilson_hop", [_vp, _vp, _vp, _vp, _dbl, _int, _int, _int, _vp])
 _sig("wilson_hop_multi", [_vp, _vp, _vp, _vp, _dbl, _int, _int, _int, _int, ctypes.c_size_t, _int, _vp])
 _sig("wilson_dslash", [_vp, _vp, _vp, _dbl, _int, _int, _vp])
+_sig("wilson_dslash_noalloc", [_vp, _vp, _vp, _dbl, _int, _int, _int, _vp])
 _sig("wilson_dslash_dag", [_vp, _vp, _vp, _dbl, _int, _int, _vp])
 _sig("bicgstab_solve", [_vp, _vp, _vp, _dbl, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats), _vp])
 _sig("wl_launch_count", [ctypes.POINTER(ctypes.c_longlong)])
@@ -241,6 +242,14 @@ def wilson_dslash_dag(g: Gauge, inp: torch.Tensor, out: torch.Tensor, kappa: flo
     V = g.lat.volume
     _check(_lib.wilson_dslash_dag(g.handle, _canon(inp, V, "in"), _canon(out, V, "out"), float(kappa), _prec(prec),
                                   int(op), _stream(stream)))
+
+
+def wilson_dslash_noalloc(g: Gauge, inp: torch.Tensor, out: torch.Tensor, kappa: float, prec, op=OP_M,
+                          dagger: bool = False, stream=None):
+    """wilson_dslash without any device allocation (fixed 64 MiB scratch in the library)."""
+    V = g.lat.volume
+    _check(_lib.wilson_dslash_noalloc(g.handle, _canon(inp, V, "in"), _canon(out, V, "out"), float(kappa),
+                                      _prec(prec), int(op), int(dagger), _stream(stream)))
 
 
 def bicgstab_solve(g: Gauge, b: torch.Tensor, x: torch.Tensor, m0: float, prm: SolverParams | None = None,
