@@ -101,6 +101,37 @@ def test_autograd_vs_finite_differences(mods, dims, inner):
     assert abs(fd - an) / abs(an) < 1e-6
 
 
+def test_autograd_16x4_fp32_directions(mods):
+    """C4 at 16^4 with an FP32 inner solve: four su(3) directions and one mass."""
+    api, ag = mods
+    dims = (16, 16, 16, 16)
+    U = synth.gauge_field(dims, 0.3, seed=85)
+    eta = synth.gaussian_source(dims, seed=86)
+    masses = [0.5, 0.3, 0.2, 0.1]
+    lat = api.Lattice(dims)
+    g = api.Gauge(lat, _cuda(U), precs=("f64", "f32", "df"))
+    prm = api.params(tol=1e-13, inner_prec="f32")
+    m0 = torch.tensor(masses, dtype=torch.float64, device="cuda", requires_grad=True)
+    omega = torch.zeros((4, lat.volume, 8), dtype=torch.float64, device="cuda", requires_grad=True)
+    x = ag.wilson_solve(g, _cuda(eta), m0, omega, prm, store_solutions=False)
+    torch.sum(torch.abs(x) ** 2).backward()
+    dU = omega.grad.cpu().numpy()
+    h = 1e-5
+    for k in range(4):
+        w = synth.su3_directions(dims, seed=2000 + k)
+        Up = np.einsum("mnab,mnbc->mnac", _exp_su3(h, w), U)
+        Um = np.einsum("mnab,mnbc->mnac", _exp_su3(-h, w), U)
+        fd = (_loss(api, lat, Up, eta, masses, prm) - _loss(api, lat, Um, eta, masses, prm)) / (2 * h)
+        an = float(np.sum(w * dU))
+        assert abs(fd - an) / abs(an) < 1e-6, (k, fd, an)
+    mp = list(masses)
+    mp[3] += h
+    mm = list(masses)
+    mm[3] -= h
+    fd = (_loss(api, lat, U, eta, mp, prm) - _loss(api, lat, U, eta, mm, prm)) / (2 * h)
+    assert abs(fd - m0.grad[3].item()) / abs(m0.grad[3].item()) < 1e-6
+
+
 def test_backward_resolve_equals_stored(mods):
     api, ag = mods
     dims = (4, 4, 4, 8)
