@@ -78,8 +78,10 @@ extern "C" {
 #define WL_GUESS_ZERO 0  /* zero initial guess for every mass                     */
 #define WL_GUESS_POLY 1  /* Lagrange extrapolation through all previous masses    */
 
-#define WL_MODE_HOST  0  /* one host round trip per iteration                      */
-#define WL_MODE_GRAPH 1  /* iterations captured in a CUDA graph, scalars on device */
+#define WL_MODE_HOST       0  /* one host round trip per iteration                      */
+#define WL_MODE_GRAPH      1  /* iterations captured in a CUDA graph, scalars on device */
+#define WL_MODE_PERSISTENT 2  /* one cooperative kernel runs whole iterations; phases
+                                 separated by grid barriers with a bounded wait        */
 
 typedef struct wl_lattice wl_lattice;
 typedef struct wl_gauge wl_gauge;
@@ -295,6 +297,16 @@ int wl_profile_read(wl_gauge *g, wl_kernel_profile out[3]);
  * from and appended to it.  *variant = 100 * rhs-per-thread + min-blocks,
  * *best_us its time per launch.  Synchronises the stream. */
 int wl_autotune(wl_gauge *g, int prec, int n_rhs, void *stream, int *variant, double *best_us);
+
+/* Failure-path check of the persistent solver (WL_MODE_PERSISTENT): runs
+ * one cooperative launch of the persistent BiCGstab on zero vectors with
+ * the barrier wait limited to wait_limit_s seconds.  With
+ * inject_missing_arrival = 1 one block skips its first barrier arrival, so
+ * every other block's bounded wait runs out: the kernel exits and the call
+ * returns WL_ERR_TIMEOUT while the context stays usable.  With 0 it returns
+ * WL_OK.  The paper has no counterpart (it concerns this library's own
+ * barrier).  Synchronises the stream. */
+int wl_persistent_selftest(wl_gauge *g, int prec, int inject_missing_arrival, double wait_limit_s, void *stream);
 
 /* Number of kernels this library has launched in the process so far (direct
  * launches plus, for every replay of a captured graph, its kernel nodes). */

@@ -24,7 +24,7 @@ F64, F32, F16, DF = 1, 2, 4, 8
 EVEN, ODD = 0, 1
 OP_HOP, OP_M, OP_MPREC = 0, 1, 2
 GUESS_ZERO, GUESS_POLY = 0, 1
-MODE_HOST, MODE_GRAPH = 0, 1
+MODE_HOST, MODE_GRAPH, MODE_PERSISTENT = 0, 1, 2
 _PREC_NAMES = {"f64": F64, "f32": F32, "f16": F16, "df": DF}
 
 
@@ -92,6 +92,7 @@ _sig("bicgstab_solve", [_vp, _vp, _vp, _dbl, ctypes.POINTER(SolverParams), ctype
 _sig("wl_launch_count", [ctypes.POINTER(ctypes.c_longlong)])
 _sig("wl_autotune", [_vp, _int, _int, _vp, ctypes.POINTER(_int), ctypes.POINTER(_dbl)])
 _sig("wl_profile_enable", [_vp, _int])
+_sig("wl_persistent_selftest", [_vp, _int, _int, _dbl, _vp])
 _sig("wl_profile_read", [_vp, ctypes.POINTER(KernelProfile)])
 _sig("wilson_solve_backward", [_vp, _vp, _vp, ctypes.POINTER(_vp), ctypes.POINTER(_dbl), _int,
                                ctypes.POINTER(SolverParams), _vp, ctypes.POINTER(_dbl), _vp, _vp])
@@ -352,3 +353,9 @@ def solve_backward(g: Gauge, b: torch.Tensor, grads, masses, xs=None, prm: Solve
                                       None if dU is None else _ptr(dU), dm,
                                       None if db is None else _ptr(db), _stream(stream)))
     return dU, (list(dm) if dm is not None else None), db
+
+
+def persistent_selftest(g: Gauge, prec="f32", inject_missing_arrival=False, wait_limit_s=0.05, stream=None) -> int:
+    """wl_persistent_selftest: status of one persistent launch (WL_ERR_TIMEOUT when an arrival is withheld)."""
+    return _lib.wl_persistent_selftest(g.handle, _prec(prec), int(inject_missing_arrival), float(wait_limit_s),
+                                       _stream(stream))

@@ -224,6 +224,16 @@ __device__ __forceinline__ void norm_acc(double &n, double x) { n = fma(x, x, n)
 template <typename R> struct NormT { using T = float; };
 template <> struct NormT<double> { using T = double; };
 
+// Vector loads: the read-only path (__ldg) for data that no block of the
+// running kernel writes; the L2-coherent path (__ldcg) for data that other
+// blocks of the same (persistent) kernel rewrite between grid barriers.
+template <bool CG, typename T>
+__device__ __forceinline__ T ldx(const T *p)
+{
+    if constexpr (CG) return __ldcg(p);
+    else return __ldg(p);
+}
+
 template <typename To, typename From>
 __device__ __forceinline__ cx<To> cconv(cx<From> z)
 {
@@ -240,12 +250,13 @@ template <int P> struct SpinorIO;
 
 template <> struct SpinorIO<WL_F64> {
     using R = double;
+    template <bool CG = false>
     static __device__ __forceinline__ void load(const void *base, int stride, int i, cx<R> (&v)[12])
     {
         const double2 *p = static_cast<const double2 *>(base);
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
-            double2 t = __ldg(p + (size_t)k * stride + i);
+            double2 t = ldx<CG>(p + (size_t)k * stride + i);
             v[k] = {t.x, t.y};
         }
     }
@@ -260,12 +271,13 @@ template <> struct SpinorIO<WL_F64> {
 
 template <> struct SpinorIO<WL_F32> {
     using R = float;
+    template <bool CG = false>
     static __device__ __forceinline__ void load(const void *base, int stride, int i, cx<R> (&v)[12])
     {
         const float4 *p = static_cast<const float4 *>(base);
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
-            float4 t = __ldg(p + (size_t)k * stride + i);
+            float4 t = ldx<CG>(p + (size_t)k * stride + i);
             v[2 * k] = {t.x, t.y};
             v[2 * k + 1] = {t.z, t.w};
         }
@@ -297,13 +309,14 @@ template <> struct SpinorIO<WL_F16> {
     {
         return reinterpret_cast<const float *>(static_cast<const uint4 *>(base) + 3 * (size_t)stride);
     }
+    template <bool CG = false>
     static __device__ __forceinline__ void load(const void *base, int stride, int i, cx<R> (&v)[12])
     {
         const uint4 *p = static_cast<const uint4 *>(base);
-        const float n = __ldg(norms(base, stride) + i);
+        const float n = ldx<CG>(norms(base, stride) + i);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            uint4 t = __ldg(p + (size_t)k * stride + i);
+            uint4 t = ldx<CG>(p + (size_t)k * stride + i);
             float2 a = unpack_half2(t.x), b = unpack_half2(t.y), c = unpack_half2(t.z), d = unpack_half2(t.w);
             v[4 * k + 0] = {a.x * n, a.y * n};
             v[4 * k + 1] = {b.x * n, b.y * n};
@@ -346,12 +359,13 @@ template <> struct SpinorIO<WL_F16> {
 
 template <> struct SpinorIO<WL_DF> {
     using R = df;
+    template <bool CG = false>
     static __device__ __forceinline__ void load(const void *base, int stride, int i, cx<R> (&v)[12])
     {
         const float4 *p = static_cast<const float4 *>(base);
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
-            float4 t = __ldg(p + (size_t)k * stride + i);
+            float4 t = ldx<CG>(p + (size_t)k * stride + i);
             v[k] = {df(t.x, t.y), df(t.z, t.w)};
         }
     }

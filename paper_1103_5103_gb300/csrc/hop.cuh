@@ -98,7 +98,7 @@ __device__ __forceinline__ bool rhs_done(const HopArgs &a, int r)
 }
 
 // Accumulate the eight transporters of site i for NB right-hand sides.
-template <int P, bool DAG, int NB, int MU>
+template <int P, bool DAG, int NB, int MU, bool CG = false>
 __device__ __forceinline__ void hop_dir(const HopArgs &a, int i, const Coord &c, int rowbase, int r0,
                                         cx<typename PrecTraits<P>::R> (&acc)[NB][12])
 {
@@ -136,7 +136,8 @@ __device__ __forceinline__ void hop_dir(const HopArgs &a, int i, const Coord &c,
     for (int r = 0; r < NB; ++r) {
         if (NB > 1 && r0 + r >= a.nrhs) break;
         cx<R> psi[12];
-        SpinorIO<P>::load(static_cast<const char *>(a.in) + (size_t)(r0 + r) * a.rhs_bytes, g.stride, fwd, psi);
+        SpinorIO<P>::template load<CG>(static_cast<const char *>(a.in) + (size_t)(r0 + r) * a.rhs_bytes, g.stride, fwd,
+                                       psi);
         transport<MU, DAG ? 1 : 0, false>(acc[r], psi, u, sf);
     }
     // backward: U_mu(n-mu)^dag psi_{n-mu} (1 + gamma_mu)   [dagger: (1 - gamma_mu)]
@@ -145,7 +146,8 @@ __device__ __forceinline__ void hop_dir(const HopArgs &a, int i, const Coord &c,
     for (int r = 0; r < NB; ++r) {
         if (NB > 1 && r0 + r >= a.nrhs) break;
         cx<R> psi[12];
-        SpinorIO<P>::load(static_cast<const char *>(a.in) + (size_t)(r0 + r) * a.rhs_bytes, g.stride, bwd, psi);
+        SpinorIO<P>::template load<CG>(static_cast<const char *>(a.in) + (size_t)(r0 + r) * a.rhs_bytes, g.stride, bwd,
+                                       psi);
         transport<MU, DAG ? 0 : 1, true>(acc[r], psi, u, sb);
     }
 }
@@ -214,17 +216,17 @@ struct EpiReduce {
     static constexpr int NV = KIND == 0 ? 2 : 3;
 };
 
-template <int P, bool DAG, int NB>
+template <int P, bool DAG, int NB, bool CG = false>
 __device__ __forceinline__ void hop_accumulate(const HopArgs &a, int i, int r0,
                                                cx<typename PrecTraits<P>::R> (&acc)[NB][12])
 {
     const Geom &g = a.g;
     const Coord c = site_coord(g, i, a.out_parity);
     const int rowbase = i - (c.x >> 1);
-    hop_dir<P, DAG, NB, 0>(a, i, c, rowbase, r0, acc);
-    hop_dir<P, DAG, NB, 1>(a, i, c, rowbase, r0, acc);
-    hop_dir<P, DAG, NB, 2>(a, i, c, rowbase, r0, acc);
-    hop_dir<P, DAG, NB, 3>(a, i, c, rowbase, r0, acc);
+    hop_dir<P, DAG, NB, 0, CG>(a, i, c, rowbase, r0, acc);
+    hop_dir<P, DAG, NB, 1, CG>(a, i, c, rowbase, r0, acc);
+    hop_dir<P, DAG, NB, 2, CG>(a, i, c, rowbase, r0, acc);
+    hop_dir<P, DAG, NB, 3, CG>(a, i, c, rowbase, r0, acc);
 }
 
 // ------------------------------------------------------- rolled variant

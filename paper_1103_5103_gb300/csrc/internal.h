@@ -136,6 +136,11 @@ int blas_recon(const Geom &g, const Vec &bo, const Vec &dx, double kappa, const 
                double *partials, unsigned *tickets, cudaStream_t s);
 
 
+// ---- persistent.cu
+int persistent_inner(wl_gauge *g, int prec, int nrhs, const Vec &r, const Vec &rhat, const Vec &p, const Vec &v,
+                     const Vec &sv, const Vec &t, const Vec &tmp, const Vec &e, BiState *state, const double *kappa2,
+                     int max_iter, double deadline_s, int skip_arrival, cudaStream_t s);
+
 // ---- tune.cu
 // Hop variant for (prec, nrhs): rhs_block > 0 forces rhs_block rhs per
 // thread; rhs_block < 0 selects variant -rhs_block; 0 takes the tuned one.

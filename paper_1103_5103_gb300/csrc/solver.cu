@@ -167,6 +167,15 @@ static int run_inner(Inner &in, const wl_solver_params &prm, int max_iter, std::
     WL_TRY(pin.reserve(sizeof(BiState) * nrhs));
     BiState *hs = static_cast<BiState *>(pin.p);
     host_state.resize(nrhs);
+    if (prm.mode == WL_MODE_PERSISTENT) {
+        // one cooperative launch for all iterations; 1 s bound on every barrier wait
+        WL_TRY(persistent_inner(in.g, in.prec, nrhs, in.r, in.rhat, in.p, in.v, in.s, in.t, in.tmp, in.e, in.sc.state,
+                                in.sc.kappa2, max_iter, 1.0, 0, s));
+        WL_CUDA_TRY(cudaMemcpyAsync(hs, in.sc.state, sizeof(BiState) * nrhs, cudaMemcpyDeviceToHost, s));
+        WL_CUDA_TRY(cudaStreamSynchronize(s));
+        std::memcpy(host_state.data(), hs, sizeof(BiState) * nrhs);
+        return WL_OK;
+    }
     const int K = prm.mode == WL_MODE_GRAPH ? std::max(1, prm.graph_iters) : 1;
     cudaGraphExec_t exec = nullptr;
     int status = WL_OK;
@@ -498,7 +507,8 @@ static int solve_one_mass(wl_gauge *g, const Vec &be, const Vec &bo, const Vec &
 static int check_params(const wl_gauge *g, const wl_solver_params *p)
 {
     if (!p || !(p->tol > 0) || p->max_iter < 1 || !valid_prec(p->inner_prec) || p->inner_prec == WL_DF ||
-        p->max_restarts < 1 || (p->mode != WL_MODE_HOST && p->mode != WL_MODE_GRAPH) || p->graph_iters < 0 ||
+        p->max_restarts < 1 || (p->mode != WL_MODE_HOST && p->mode != WL_MODE_GRAPH && p->mode != WL_MODE_PERSISTENT) ||
+        p->graph_iters < 0 ||
         p->rhs_block < 0 || p->rhs_block > 4 || (p->outer_prec != WL_F64 && p->outer_prec != WL_DF)) {
         set_error("solver parameters out of range");
         return WL_ERR_ARG;
@@ -515,6 +525,33 @@ static int check_params(const wl_gauge *g, const wl_solver_params *p)
 using namespace wl;
 
 // ---------------------------------------------------------------- C ABI
+
+extern "C" int wl_persistent_selftest(wl_gauge *g, int prec, int inject_missing_arrival, double wait_limit_s,
+                                      void *stream)
+{
+    if (!g || (prec != WL_F32 && prec != WL_F16 && prec != WL_F64) || !(g->prec_mask & prec) ||
+        !(wait_limit_s > 0.0) || wait_limit_s > 10.0) {
+        set_error("wl_persistent_selftest: bad argument");
+        return WL_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lock(g->mu);
+    cudaStream_t s = as_stream(stream);
+    Inner in;
+    WL_TRY(make_inner(g, prec, 1, 0.1, &in, s));
+    const size_t b = in.r.rhs_bytes;
+    for (Vec *v : {&in.r, &in.rhat, &in.p, &in.v, &in.s, &in.t, &in.tmp}) WL_CUDA_TRY(cudaMemsetAsync(v->ptr, 0, b, s));
+    WL_CUDA_TRY(cudaMemsetAsync(in.e.ptr, 0, in.e.rhs_bytes, s));
+    // one live rhs with a large target so the loop runs its iterations
+    BiState st;
+    std::memset(&st, 0, sizeof(st));
+    st.rho_re = 1.0;
+    st.target2 = -1.0;
+    WL_CUDA_TRY(cudaMemcpyAsync(in.sc.state, &st, sizeof(st), cudaMemcpyHostToDevice, s));
+    const double mk2 = -0.01;
+    WL_CUDA_TRY(cudaMemcpyAsync(in.sc.kappa2, &mk2, sizeof(double), cudaMemcpyHostToDevice, s));
+    return persistent_inner(g, prec, 1, in.r, in.rhat, in.p, in.v, in.s, in.t, in.tmp, in.e, in.sc.state, in.sc.kappa2,
+                            2, wait_limit_s, inject_missing_arrival ? 1 : 0, s);
+}
 
 extern "C" int wl_profile_enable(wl_gauge *g, int on)
 {

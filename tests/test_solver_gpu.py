@@ -155,3 +155,42 @@ def test_profiling_counts_hop_launches(api, mode):
     # a following solve is unaffected
     _, st2 = api.multimass_solve(g, [b], [0.2], api.params())
     assert st2[0][0]["status"] == 0
+
+
+@pytest.mark.parametrize("inner", ["f64", "f32", "f16"])
+def test_persistent_mode_vs_oracle(api, inner):
+    """WL_MODE_PERSISTENT: one cooperative kernel per inner solve, same answers."""
+    dims = (4, 4, 4, 8)
+    U, lat, g = _gauge(api, dims, 0.3, 11)
+    b = synth.z2_source(dims, seed=12)
+    x = torch.zeros((lat.volume, 4, 3), dtype=torch.complex128, device="cuda")
+    st = api.bicgstab_solve(g, _cuda(b), x, 0.1, api.params(inner_prec=inner, mode=api.MODE_PERSISTENT))
+    assert st["status"] == 0 and st["true_relres"] <= 1e-10, st
+    ref, _ = O.eo_solve(U, dims, b, 0.1, tol=1e-13)
+    assert rel(x.cpu().numpy(), ref) < 1e-8
+
+
+def test_persistent_multimass_batched(api):
+    dims = (8, 8, 8, 8)
+    U, lat, g = _gauge(api, dims, 0.3, 1)
+    bs = [synth.point_source(dims, s, c) for s in range(2) for c in range(2)]
+    masses = [0.5, 0.3, 0.2, 0.1]
+    xs, stats = api.multimass_solve(g, [_cuda(b) for b in bs], masses, api.params(mode=api.MODE_PERSISTENT))
+    xg, _ = api.multimass_solve(g, [_cuda(b) for b in bs], masses, api.params(mode=api.MODE_GRAPH))
+    for r in range(len(bs)):
+        for i in range(len(masses)):
+            assert stats[r][i]["status"] == 0 and stats[r][i]["true_relres"] <= 1e-10
+            assert rel(xs[r][i].cpu().numpy(), xg[r][i].cpu().numpy()) < 1e-8
+
+
+def test_persistent_barrier_wait_is_bounded(api):
+    """A withheld barrier arrival ends the persistent kernel with WL_ERR_TIMEOUT
+    after the wait limit; the context stays usable for the next solve."""
+    dims = (4, 4, 4, 8)
+    U, lat, g = _gauge(api, dims, 0.3, 5)
+    assert api.persistent_selftest(g, "f32", inject_missing_arrival=False, wait_limit_s=0.5) == api.WL_OK
+    assert api.persistent_selftest(g, "f32", inject_missing_arrival=True, wait_limit_s=0.05) == api.WL_ERR_TIMEOUT
+    b = _cuda(synth.z2_source(dims, 6))
+    x = torch.zeros_like(b)
+    st = api.bicgstab_solve(g, b, x, 0.2, api.params(mode=api.MODE_PERSISTENT))
+    assert st["status"] == 0 and st["true_relres"] <= 1e-10
