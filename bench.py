@@ -40,6 +40,8 @@ CONFIGS = {
                dims=(24, 24, 24, 64), eps=0.5, seed=3, sources="points12"),
     "c2": dict(name="16^3x32, 1 Z2 source x 8 masses (m0 0.40..0.05), eps 0.5",
                dims=(16, 16, 16, 32), eps=0.5, seed=2, sources="z2"),
+    "c1": dict(name="8^4, 1 point source x 4 masses (m0 0.5, 0.3, 0.2, 0.1), eps 0.3",
+               dims=(8, 8, 8, 8), eps=0.3, seed=1, sources="point1", masses=[0.5, 0.3, 0.2, 0.1]),
 }
 # algorithmic bytes of one hop: per output site 8 links, per output site and
 # rhs one input spinor (each read once) and one output spinor
@@ -57,6 +59,8 @@ def sources(cfg):
     d = cfg["dims"]
     if cfg["sources"] == "points12":
         return [synth.point_source(d, s, c) for s in range(4) for c in range(3)]
+    if cfg["sources"] == "point1":
+        return [synth.point_source(d)]
     return [synth.z2_source(d, seed=3)]
 
 
@@ -213,8 +217,10 @@ def run_ours(args, cfg):
     nr, nm = len(bs_h), len(MASSES)
     bs = [torch.from_numpy(b).to(dev) for b in bs_h]
     xs = [[torch.empty((V, 4, 3), dtype=torch.complex128, device=dev) for _ in MASSES] for _ in bs]
+    MASSES[:] = cfg.get("masses", MASSES)
     prm = api.params(inner_prec=args.inner, rhs_block=args.rhs_block, outer_prec=args.outer,
-                     inner_tol=args.inner_tol)
+                     inner_tol=args.inner_tol,
+                     mode={"graph": api.MODE_GRAPH, "persistent": api.MODE_PERSISTENT, "host": api.MODE_HOST}[args.mode])
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -300,6 +306,7 @@ def run_ours(args, cfg):
         "vs_baseline": None, "dtype": args.inner, "data": "synthetic",
         "config": {"workload": cfg["name"], "sources": nr, "masses": MASSES, "inner_prec": args.inner,
                    "outer_prec": args.outer, "inner_tol": args.inner_tol or "library default",
+                   "mode": args.mode,
                    "tol": 1e-10, "l2": "flushed (256 MB write) before every step; working set > L2",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "e2e": {"value": t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
@@ -354,6 +361,7 @@ def main():
     ap.add_argument("--outer", choices=["df", "f64"], default="df")
     ap.add_argument("--rhs-block", type=int, default=0)
     ap.add_argument("--inner-tol", type=float, default=0.0)
+    ap.add_argument("--mode", choices=["graph", "persistent", "host"], default="graph")
     ap.add_argument("--baseline-sources", type=int, default=12)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-baseline", action="store_true")
