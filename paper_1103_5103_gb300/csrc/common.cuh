@@ -225,12 +225,14 @@ template <typename R> struct NormT { using T = float; };
 template <> struct NormT<double> { using T = double; };
 
 // Vector loads: the read-only path (__ldg) for data that no block of the
-// running kernel writes; the L2-coherent path (__ldcg) for data that other
-// blocks of the same (persistent) kernel rewrite between grid barriers.
+// running kernel writes; ordinary loads for data that other blocks of the
+// same (persistent) kernel rewrite between grid barriers -- after the
+// barrier's release/acquire fences those are coherent, the non-coherent
+// read-only path is not.
 template <bool CG, typename T>
 __device__ __forceinline__ T ldx(const T *p)
 {
-    if constexpr (CG) return __ldcg(p);
+    if constexpr (CG) return *p;
     else return __ldg(p);
 }
 

@@ -48,8 +48,8 @@ __device__ __forceinline__ int ld_volatile(const int *p) { return *(volatile con
 
 // State written by one block and read by others between barriers (BiState,
 // the totals, the barrier words) is accessed through volatile lvalues, and
-// every vector the kernel rewrites is loaded through L2 (__ldcg): neither L1
-// nor the read-only path is coherent across SMs within a kernel.
+// every vector the kernel rewrites is read with ordinary loads (ordered by
+// the barrier's fences), never through the non-coherent read-only path.
 
 // Grid barrier with a bounded spin.  fin(), if given, runs in thread 0 of
 // the last block to arrive, before the others are released.  Returns false
@@ -78,7 +78,6 @@ __device__ __forceinline__ bool grid_barrier(PersistCtl *c, Fin fin)
                     atomicExch(&c->err, 1);
                     break;
                 }
-                __nanosleep(100);
             }
         }
         __threadfence();
@@ -112,8 +111,10 @@ __device__ __forceinline__ void flush_acc(double (*sacc)[4], PersistCtl *c, int 
             }
 }
 
+constexpr int kPersistBlock = 384;  // one block per SM: fewer arrivals per barrier
+
 template <int P, int PX>
-__global__ void __launch_bounds__(128) k_bicgstab_persistent(PersistArgs A)
+__global__ void __launch_bounds__(kPersistBlock, 1) k_bicgstab_persistent(PersistArgs A)
 {
     using R = typename PrecTraits<P>::R;
     using RX = typename PrecTraits<PX>::R;
@@ -121,14 +122,14 @@ __global__ void __launch_bounds__(128) k_bicgstab_persistent(PersistArgs A)
     for (int k = threadIdx.x; k < kPersistMaxRhs * 4; k += blockDim.x) (&sacc[0][0])[k] = 0.0;
     __syncthreads();
     const Geom &g = A.hop_odd.g;
-    const int nsb = (g.Vh + 127) / 128;
+    const int nsb = (g.Vh + kPersistBlock - 1) / kPersistBlock;
     const int nunits = nsb * A.nrhs;
     PersistCtl *c = A.ctl;
     BiState *st = A.st;
     auto done = [&](int r) { return ld_volatile(&st[r].done) != 0; };
     auto unit = [&](int u, int &r, int &i) {
         r = u % A.nrhs;
-        i = (u / A.nrhs) * 128 + threadIdx.x;
+        i = (u / A.nrhs) * kPersistBlock + threadIdx.x;
     };
     for (int it = 0; it < A.max_iter; ++it) {
         bool all = true;
@@ -375,14 +376,15 @@ static int launch_persistent_t(PersistArgs &A, cudaStream_t s)
     int dev = 0, nsm = 0, per = 0;
     WL_CUDA_TRY(cudaGetDevice(&dev));
     WL_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    WL_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bicgstab_persistent<P, PX>, 128, 0));
+    WL_CUDA_TRY(
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bicgstab_persistent<P, PX>, kPersistBlock, 0));
     if (per < 1) { set_error("persistent solver: kernel cannot be resident"); return WL_ERR_CUDA; }
-    const int nsb = (A.hop_odd.g.Vh + 127) / 128;
+    const int nsb = (A.hop_odd.g.Vh + kPersistBlock - 1) / kPersistBlock;
     int grid = nsm * per;
     if (grid > nsb * A.nrhs) grid = nsb * A.nrhs;
     void *args[] = {&A};
-    WL_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_bicgstab_persistent<P, PX>, dim3(grid), dim3(128), args, 0,
-                                            s));
+    WL_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_bicgstab_persistent<P, PX>, dim3(grid),
+                                            dim3(kPersistBlock), args, 0, s));
     note_launch(s);
     return WL_OK;
 }
