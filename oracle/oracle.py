@@ -71,6 +71,7 @@ def lib():
         _lib.or_bicgstab_m.restype = ctypes.c_int
         _lib.or_link_force.argtypes = [vp, ctypes.c_int, vp, vp, vp, ctypes.c_double, vp, vp]
         _lib.or_gamma_matrices.argtypes = [vp]
+        _lib.or_apply_mk_sites.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_double, vp, ctypes.c_long, vp]
     return _lib
 
 
@@ -170,6 +171,16 @@ def bicgstab_m(U, dims, b, masses, tol=1e-10, maxiter=10000, antiperiodic=True):
                                  ptrs, tol, maxiter, _p(iters))
     xs = [(m + 4.0) * o for m, o in zip(masses, outs)]
     return xs, dict(status=status, iterations=[int(i) for i in iters])
+
+
+def apply_mk_sites(U, dims, psi, kappa, sites, antiperiodic=True):
+    """(M_k psi)_n at the given lexicographic sites, shape (len(sites), 4, 3)."""
+    U, psi = _c128(U), _c128(psi)
+    sites = np.ascontiguousarray(sites, dtype=np.int64)
+    out = np.empty((len(sites), 4, 3), dtype=np.complex128)
+    lib().or_apply_mk_sites(_dims(dims), int(antiperiodic), _p(U), _p(psi), float(kappa), _p(sites), len(sites),
+                            _p(out))
+    return out
 
 
 def true_relres(U, dims, b, x, m0, antiperiodic=True):

@@ -194,6 +194,47 @@ void or_hop(const int d[4], int ap, const cplx *U, const cplx *in, cplx *out)
     }
 }
 
+/* (M_k psi)_n = psi_n - kappa (D psi)_n at the listed sites only (Eq. 4 per
+ * site), for checking large solutions at a sample of sites.  out[j] holds
+ * the 12 complex entries of site sites[j]. */
+void or_apply_mk_sites(const int d[4], int ap, const cplx *U, const cplx *in, double kappa, const long *sites,
+                       long nsites, cplx *out)
+{
+    cplx g[4][4][4];
+    or_gammas(g);
+    const long V = or_volume(d);
+    for (long j = 0; j < nsites; ++j) {
+        const long n = sites[j];
+        cplx acc[3][4] = {{0}};
+        for (int mu = 0; mu < 4; ++mu) {
+            for (int dir = +1; dir >= -1; dir -= 2) {
+                double sign;
+                long m = or_neighbour(d, ap, n, mu, dir, &sign);
+                cplx L[3][3];
+                const cplx *u = U + ((long)mu * V + (dir > 0 ? n : m)) * 9;
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b) L[a][b] = dir > 0 ? u[3 * a + b] : conj(u[3 * b + a]);
+                cplx tmp[3][4];
+                for (int a = 0; a < 3; ++a)
+                    for (int s = 0; s < 4; ++s) {
+                        cplx t = 0;
+                        for (int b = 0; b < 3; ++b) t += L[a][b] * in[12 * m + 3 * s + b];
+                        tmp[a][s] = t;
+                    }
+                for (int a = 0; a < 3; ++a)
+                    for (int s = 0; s < 4; ++s) {
+                        cplx t = 0;
+                        for (int k = 0; k < 4; ++k)
+                            t += tmp[a][k] * ((k == s ? 1.0 : 0.0) + (dir > 0 ? -1.0 : 1.0) * g[mu][k][s]);
+                        acc[a][s] += sign * t;
+                    }
+            }
+        }
+        for (int a = 0; a < 3; ++a)
+            for (int s = 0; s < 4; ++s) out[12 * j + 3 * s + a] = in[12 * n + 3 * s + a] - kappa * acc[a][s];
+    }
+}
+
 /* psi -> psi gamma_5 (gamma_5 = diag(1, 1, -1, -1) acting on the spin index). */
 void or_gamma5(const int d[4], const cplx *in, cplx *out)
 {

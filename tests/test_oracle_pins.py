@@ -139,6 +139,31 @@ def test_constant_abelian_field_closed_form():
     assert _rel(out, want) < 1e-14
 
 
+def test_site_sampled_operator_free_field():
+    """The site-sampled M_k reproduces the free-field closed form at the sites."""
+    dims = (4, 4, 2, 6)
+    g = O.gammas()
+    U = synth.unit_gauge_field(dims)
+    u = rng.standard_normal(4) + 1j * rng.standard_normal(4)
+    c = rng.standard_normal(3) + 1j * rng.standard_normal(3)
+    psi, p, phase = _plane_wave(dims, [1, 3, 1, 2], c, u)
+    kap = 0.12
+    sites = np.array([0, 5, 17, 63, synth.volume(dims) - 1])
+    out = O.apply_mk_sites(U, dims, psi, kap, sites)
+    row = u @ (np.eye(4) - kap * _Dp(p, g))
+    want = phase[sites][:, None, None] * np.einsum("s,c->sc", row, c)[None]
+    assert _rel(out, want) < 1e-14
+
+
+def test_site_sampled_operator_random_field():
+    dims = (4, 2, 2, 6)
+    U = synth.gauge_field(dims, 0.7, seed=4)
+    psi = synth.gaussian_source(dims, seed=5)
+    sites = np.arange(0, synth.volume(dims), 7)
+    full = O.apply(O.OP_MK, U, dims, psi, 0.11)
+    assert _rel(O.apply_mk_sites(U, dims, psi, 0.11, sites), full[sites]) < 1e-15
+
+
 # --------------------------------------------------------- gauge-field pins
 
 def test_gauge_covariance():
