@@ -66,7 +66,7 @@ def lib():
         _lib.or_bicgstab.argtypes = [ctypes.POINTER(_Op), vp, vp, ctypes.c_double, ctypes.c_double,
                                      ctypes.c_int, ctypes.POINTER(_Stats)]
         _lib.or_bicgstab.restype = ctypes.c_int
-        _lib.or_bicgstab_m.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_int, vp, vp,
+        _lib.or_bicgstab_m.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_int, vp, vp, vp,
                                        ctypes.c_double, ctypes.c_int, vp]
         _lib.or_bicgstab_m.restype = ctypes.c_int
         _lib.or_link_force.argtypes = [vp, ctypes.c_int, vp, vp, vp, ctypes.c_double, vp, vp]
@@ -160,15 +160,22 @@ def bicgstab(kind, U, dims, b, param, x0=None, tol=1e-10, bref=None, maxiter=100
                    restarts=st.restarts, true_relres=st.true_relres)
 
 
-def bicgstab_m(U, dims, b, masses, tol=1e-10, maxiter=10000, antiperiodic=True):
-    """BiCGstab-M on M_p(m_s) + sigma_i; returns kappa-form solutions x_i = (m_i+4) psi_i."""
+BREAKDOWN = 2
+
+
+def bicgstab_m(U, dims, b, masses, tol=1e-10, maxiter=10000, antiperiodic=True, rhat=None):
+    """BiCGstab-M on M_p(m_s) + sigma_i; returns kappa-form solutions x_i = (m_i+4) psi_i.
+    rhat is the shadow residual (default b); status BREAKDOWN when <rhat, v>
+    or rho vanishes, as it does after one iteration for a point source b
+    with rhat = b."""
     U, b = _c128(U), _c128(b)
+    rh = None if rhat is None else _c128(rhat)
     masses = np.ascontiguousarray(masses, dtype=np.float64)
     outs = [np.zeros_like(b) for _ in masses]
     ptrs = (ctypes.c_void_p * len(masses))(*[o.ctypes.data for o in outs])
     iters = np.zeros(len(masses), dtype=np.int32)
     status = lib().or_bicgstab_m(_dims(dims), int(antiperiodic), _p(U), _p(masses), len(masses), _p(b),
-                                 ptrs, tol, maxiter, _p(iters))
+                                 None if rh is None else _p(rh), ptrs, tol, maxiter, _p(iters))
     xs = [(m + 4.0) * o for m, o in zip(masses, outs)]
     return xs, dict(status=status, iterations=[int(i) for i in iters])
 

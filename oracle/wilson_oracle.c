@@ -405,8 +405,8 @@ int or_bicgstab(const or_op *A, const cplx *b, cplx *x, double tol, double bref,
  * Outputs psi_i in the paper's normalisation, one per entry of masses
  * (x_out[i] has V*12 entries).  Returns OR_OK or OR_NOCONV. */
 int or_bicgstab_m(const int d[4], int ap, const cplx *U, const double *masses, int nm,
-                  const cplx *b, cplx **x_out, double tol, int maxiter,
-                  int *iters_out /* per mass: iteration at which it froze */)
+                  const cplx *b, const cplx *rhat0 /* shadow residual, NULL: b */, cplx **x_out,
+                  double tol, int maxiter, int *iters_out /* per mass: iteration at which it froze */)
 {
     const long n = or_volume(d) * 12;
     int is = 0;
@@ -426,7 +426,7 @@ int or_bicgstab_m(const int d[4], int ap, const cplx *U, const double *masses, i
 
     const double bn = or_norm(n, b), target = tol * bn;
     memcpy(r, b, sizeof(cplx) * n);
-    memcpy(rh, b, sizeof(cplx) * n);
+    memcpy(rh, rhat0 ? rhat0 : b, sizeof(cplx) * n);
     memcpy(p, b, sizeof(cplx) * n);
     for (int i = 0; i < nm; ++i) {
         sig[i] = masses[i] - masses[is];
@@ -439,11 +439,24 @@ int or_bicgstab_m(const int d[4], int ap, const cplx *U, const double *masses, i
     }
     cplx *x = x_out[is];
     cplx rho = or_dot(n, rh, r), alpha_prev = 1, beta_prev = 0;
+    const double rhn = or_norm(n, rh);
+    double rn_cur = bn;
     int it = 0, status = OR_NOCONV;
     if (bn == 0) status = OR_OK;
-    while (status != OR_OK && it < maxiter) {
+    while (status == OR_NOCONV && it < maxiter) {
         or_apply(&A, p, v);
-        cplx alpha = rho / or_dot(n, rh, v);
+        /* Breakdown: rho = <rhat, r> or <rhat, v> vanishes to rounding
+         * (below 1e-12 of the Cauchy-Schwarz bound), and the recurrences are
+         * driven by noise from then on.  With rhat = b a point source, rho
+         * vanishes exactly after one iteration in exact arithmetic: r_1 at
+         * the source site comes from closed two-hop paths, all backtracks on
+         * extents >= 4, and (1 - gamma_mu)(1 + gamma_mu) = 0. */
+        const cplx rv = or_dot(n, rh, v);
+        if (!(cabs(rho) > 1e-12 * rhn * rn_cur) || !(cabs(rv) > 1e-12 * rhn * or_norm(n, v))) {
+            status = OR_ERR;
+            break;
+        }
+        cplx alpha = rho / rv;
         for (long k = 0; k < n; ++k) s[k] = r[k] - alpha * v[k];
         or_apply(&A, s, t);
         cplx omega = or_dot(n, t, s) / or_dot(n, t, t);
@@ -464,6 +477,7 @@ int or_bicgstab_m(const int d[4], int ap, const cplx *U, const double *masses, i
         cplx rho1 = or_dot(n, rh, r);
         cplx beta = (rho1 / rho) * (alpha / omega);
         const double rn = or_norm(n, r);
+        rn_cur = rn;
         for (int i = 0; i < nm; ++i) {
             if (i == is || !active[i]) continue;
             cplx lamn = lam[i] * (1.0 + omega * sig[i]);

@@ -291,6 +291,41 @@ def test_bicgstab_m_vs_dense_lu():
         assert _rel(x, xd) < 1e-9, m
 
 
+def test_bicgstab_m_point_source_rhat_b_breaks_down():
+    """With b a point source and the shadow residual rhat = b, rho_1 =
+    <b, r_1> is exactly zero: r_1 at the source site is built from closed
+    two-hop paths, all backtracks on extents >= 4, and (1 - gamma_mu)(1 +
+    gamma_mu) = 0.  The recurrences must stop with a breakdown at once."""
+    dims = (4, 4, 4, 4)
+    U = synth.gauge_field(dims, 0.5, seed=35)
+    b = synth.point_source(dims)
+    xs, st = O.bicgstab_m(U, dims, b, [0.4, 0.1], tol=1e-10, maxiter=50)
+    assert st["status"] == O.BREAKDOWN and max(st["iterations"]) == 1, st
+    # the same cancellation by hand: one BiCGstab step on M_p(0.1)
+    A = lambda v: O.apply(O.OP_MP, U, dims, v, 0.1)
+    v = A(b)
+    s_ = b - (np.vdot(b, b) / np.vdot(b, v)) * v
+    t = A(s_)
+    r1 = s_ - (np.vdot(t, s_) / np.vdot(t, t)) * t
+    assert abs(np.vdot(b, r1)) < 1e-16 * np.linalg.norm(r1)
+
+
+def test_bicgstab_m_point_source_random_shadow_vs_dense_lu():
+    """A Gaussian shadow residual removes the breakdown: every shifted
+    solution of the point source matches dense LU."""
+    dims = (4, 4, 4, 4)
+    U = synth.gauge_field(dims, 0.5, seed=36)
+    b = synth.point_source(dims, 2, 1)
+    rh = synth.gaussian_source(dims, seed=37)
+    masses = [0.4, 0.2, 0.05]
+    xs, st = O.bicgstab_m(U, dims, b, masses, tol=1e-12, rhat=rh)
+    assert st["status"] == O.OK, st
+    for m, x in zip(masses, xs):
+        M = O.dense_operator(O.OP_MK, U, dims, O.kappa(m))
+        xd = np.linalg.solve(M, b.reshape(-1)).reshape(b.shape)
+        assert _rel(x, xd) < 1e-9, m
+
+
 def test_bicgstab_m_collinearity():
     """Truncated after k iterations, every shifted true residual is the
     unshifted residual divided by the scalar pi_k lambda_k: the residual
@@ -420,3 +455,20 @@ def test_mass_gradient_free_field_closed_form():
     x, _ = O.bicgstab(O.OP_MK, U, dims, eta, k, tol=1e-14)
     _, dm = O.backward(U, dims, eta, [m], [2 * x], xs=[x], tol=1e-14)
     assert abs(dm[0] - want) / abs(want) < 1e-9
+
+
+def test_sampled_residual_helper_matches_full_residual():
+    """The sampled-site residual used for the large lattices: over all sites
+    its estimate is the full oracle residual, and the single-site peak never
+    exceeds it."""
+    from helpers import SampledResidual
+    dims = (4, 4, 2, 6)
+    U = synth.gauge_field(dims, 0.7, seed=5)
+    b = synth.point_source(dims, 1, 2)
+    m = 0.02
+    x, _ = O.bicgstab(O.OP_MK, U, dims, b, O.kappa(m), tol=1e-6)
+    full = O.true_relres(U, dims, b, x, m)
+    est, peak = SampledResidual(dims, U, n_random=10 ** 6)(x, b, m)
+    assert abs(est - full) <= 1e-12 * full
+    est, peak = SampledResidual(dims, U, n_random=40)(x, b, m)
+    assert peak <= full and 0.2 * full < est < 5 * full
