@@ -21,6 +21,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -42,6 +43,12 @@ CONFIGS = {
                dims=(16, 16, 16, 32), eps=0.5, seed=2, sources="z2"),
     "c1": dict(name="8^4, 1 point source x 4 masses (m0 0.5, 0.3, 0.2, 0.1), eps 0.3",
                dims=(8, 8, 8, 8), eps=0.3, seed=1, sources="point1", masses=[0.5, 0.3, 0.2, 0.1]),
+    # 10.6M sites: 16 solutions per source take 33 GB in canonical FP64 and
+    # as much again inside the solver, so the sources go two at a time
+    "c5": dict(name="48^3x96, 12 spin-colour point sources x 16 masses (m0 0.5*0.04^(i/15)), eps 0.7",
+               dims=(48, 48, 48, 96), eps=0.7, seed=5, sources="points12",
+               masses=[0.5 * 0.04 ** (i / 15.0) for i in range(16)], inner="f16", source_batch=2,
+               baseline_sources=1),
 }
 # algorithmic bytes of one hop: per output site 8 links, per output site and
 # rhs one input spinor (each read once) and one output spinor
@@ -62,6 +69,20 @@ def sources(cfg):
     if cfg["sources"] == "point1":
         return [synth.point_source(d)]
     return [synth.z2_source(d, seed=3)]
+
+
+def host_cpu():
+    """Host CPU model (lscpu) and logical core count, for the CPU baseline."""
+    model = platform.machine()
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return f"{model}, {os.cpu_count()} logical cores"
 
 
 def measured_peaks():
@@ -154,15 +175,18 @@ def max_over_ranks(v, ws):
 
 def oracle_sample(cfg, U, bs, target_s=15.0):
     """Time FP64 oracle applications of M_prec (lightest mass, first source)
-    for about target_s seconds.  One BiCGstab iteration applies the operator
-    twice; its six vector updates are not timed (under 2% of an oracle
-    iteration).  Returns (seconds per iteration, applications, seconds)."""
+    for about target_s seconds (at least one application).  One BiCGstab
+    iteration applies the operator twice; its six vector updates are not
+    timed (under 2% of an oracle iteration).  Returns (seconds per
+    iteration, applications, seconds)."""
     from oracle import oracle as O
     dims = cfg["dims"]
-    m = MASSES[-1]
-    bp = O.eo_source(U, dims, bs[0], m)
+    m = cfg.get("masses", MASSES)[-1]
+    # the cost of an application does not depend on the vector: start from
+    # the even part of the source
+    bp = np.where(O.parity_mask(dims)[:, None, None], 0, bs[0])
     n, t = 0, 0.0
-    while t < target_s or n < 2:
+    while t < target_s or n < 1:
         t0 = time.perf_counter()
         bp = O.apply(O.OP_MPREC, U, dims, bp, O.kappa(m))
         t += time.perf_counter() - t0
@@ -192,11 +216,16 @@ def run_reference(args, cfg):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": cfg["name"]},
-            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": v, "unit": UNIT,
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": v, "unit": UNIT, "host": host_cpu(),
                              "sample": f"FP64 oracle M_prec applications timed on one host core (2 per "
                                        f"BiCGstab iteration), scaled by {iters_per_step} inner iterations per step"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+def _used_bytes(torch):
+    free, total = torch.cuda.mem_get_info()
+    return total - free
 
 
 def run_ours(args, cfg):
@@ -207,37 +236,50 @@ def run_ours(args, cfg):
     dev = torch.device("cuda", local if ws > 1 else 0)
     torch.cuda.set_device(dev)
     dims = cfg["dims"]
+    masses = list(cfg.get("masses", MASSES))
+    inner = args.inner or cfg.get("inner", "f32")
     t0 = time.time()
     U = synth.gauge_field(dims, cfg["eps"], seed=cfg["seed"])
     bs_h = sources(cfg)
     gen_s = time.time() - t0
+    torch.cuda.synchronize()
+    mem0 = _used_bytes(torch)
     lat = api.Lattice(dims)
-    g = api.Gauge(lat, torch.from_numpy(U).to(dev))
+    U_dev = torch.from_numpy(U).to(dev)
+    g = api.Gauge(lat, U_dev)
     V = lat.volume
-    nr, nm = len(bs_h), len(MASSES)
+    nr, nm = len(bs_h), len(masses)
+    nb = args.source_batch or cfg.get("source_batch", nr)
+    batches = [list(range(i, min(nr, i + nb))) for i in range(0, nr, nb)]
     bs = [torch.from_numpy(b).to(dev) for b in bs_h]
-    xs = [[torch.empty((V, 4, 3), dtype=torch.complex128, device=dev) for _ in MASSES] for _ in bs]
-    MASSES[:] = cfg.get("masses", MASSES)
-    prm = api.params(inner_prec=args.inner, rhs_block=args.rhs_block, outer_prec=args.outer,
+    # solution buffers for one batch of sources, reused by every batch
+    xs = [[torch.empty((V, 4, 3), dtype=torch.complex128, device=dev) for _ in masses] for _ in range(nb)]
+    prm = api.params(inner_prec=inner, rhs_block=args.rhs_block, outer_prec=args.outer,
                      inner_tol=args.inner_tol,
                      mode={"graph": api.MODE_GRAPH, "persistent": api.MODE_PERSISTENT, "host": api.MODE_HOST}[args.mode])
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
+    def solve_batch(rows):
+        _, st = api.multimass_solve(g, [bs[r] for r in rows], masses, prm, xs=xs[:len(rows)])
+        return st
+
     def step():
-        _, st = api.multimass_solve(g, bs, MASSES, prm, xs=xs)
+        st = []
+        for rows in batches:
+            st += solve_batch(rows)
         return st
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    footprint = _used_bytes(torch) - mem0
     # timed region: flush L2 before each step (inputs are also larger than L2)
     barrier(ws)
     torch.cuda.synchronize()
     api.profile_enable(g, True)
     launches0 = api.launch_count()
     clocks = ClockSampler(dev.index or 0)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     step_ms = []
     all_stats = None
     for k in range(args.steps):
@@ -254,39 +296,46 @@ def run_ours(args, cfg):
         step_ms.append(a.elapsed_time(b))
     torch.cuda.synchronize()
     clk = clocks.stop()
-    launches = api.launch_count() - launches0
-    prof = api.profile_read(g)[args.inner]
+    launches = (api.launch_count() - launches0) / max(1, args.steps)
+    prof = api.profile_read(g)[inner]
     api.profile_enable(g, False)
     barrier(ws)
     t_step = max_over_ranks(float(np.mean(step_ms)) / 1e3, ws)
 
-    # end to end through the public API with pinned host buffers
+    # end to end through the public API: each batch's sources from pinned
+    # host memory, every solution back into pinned host staging slots (a
+    # ring when all of them do not fit in 8 GB)
     bs_pin = [torch.from_numpy(b).pin_memory() for b in bs_h]
-    xs_pin = [[torch.empty((V, 4, 3), dtype=torch.complex128).pin_memory() for _ in MASSES] for _ in bs_h]
+    x_bytes = V * 12 * 16
+    n_slots = max(1, min(nr * nm, (8 << 30) // x_bytes))
+    slots = [torch.empty((V, 4, 3), dtype=torch.complex128).pin_memory() for _ in range(n_slots)]
     h2d = sum(b.numel() * 16 for b in bs_pin)
-    d2h = sum(x.numel() * 16 for row in xs_pin for x in row)
+    d2h = nr * nm * x_bytes
     e2e_ms = []
     for _ in range(max(1, args.steps)):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for bd, bp in zip(bs, bs_pin):
-            bd.copy_(bp, non_blocking=True)
-        _, st = api.multimass_solve(g, bs, MASSES, prm, xs=xs)
-        for row_d, row_p in zip(xs, xs_pin):
-            for xd, xp in zip(row_d, row_p):
-                xp.copy_(xd, non_blocking=True)
+        k = 0
+        for rows in batches:
+            for r in rows:
+                bs[r].copy_(bs_pin[r], non_blocking=True)
+            solve_batch(rows)
+            for j in range(len(rows)):
+                for i in range(nm):
+                    slots[k % n_slots].copy_(xs[j][i], non_blocking=True)
+                    k += 1
         torch.cuda.synchronize()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     t_e2e = max_over_ranks(float(np.mean(e2e_ms)) / 1e3, ws)
+    del slots
 
     peak, peak_kind = measured_peaks()
-    Vh = V // 2
     # hop roofline from the live event timings of the solve's own hop launches
     if prof["launches"]:
         per_launch_sites = prof["sites"] / prof["launches"]
         per_launch_site_rhs = prof["site_rhs"] / prof["launches"]
-        bytes_launch = per_launch_sites * 8 * LINK_B[args.inner] + per_launch_site_rhs * 2 * SPINOR_B[args.inner]
+        bytes_launch = per_launch_sites * 8 * LINK_B[inner] + per_launch_site_rhs * 2 * SPINOR_B[inner]
         avg_s = prof["ms"] / prof["launches"] / 1e3
         achieved = bytes_launch / avg_s / 1e9
         hop_gflops = 1320 * per_launch_site_rhs / avg_s / 1e9
@@ -294,54 +343,78 @@ def run_ours(args, cfg):
         bytes_launch = avg_s = achieved = hop_gflops = None
     iters = sum(st["iterations"] for row in all_stats for st in row)
     worst = max(st["true_relres"] for row in all_stats for st in row)
-    per_mass = {f"{m:.2f}": {"iterations": int(sum(all_stats[r][i]["iterations"] for r in range(nr))),
-                             "restarts": int(sum(all_stats[r][i]["restarts"] for r in range(nr))),
-                             "seconds": float(all_stats[0][i]["seconds"]),
-                             "max_true_relres": float(max(all_stats[r][i]["true_relres"] for r in range(nr)))}
-                for i, m in enumerate(MASSES)}
+    per_mass = {}
+    for i, m in enumerate(masses):
+        e = {"iterations": int(sum(all_stats[r][i]["iterations"] for r in range(nr))),
+             "restarts": int(sum(all_stats[r][i]["restarts"] for r in range(nr))),
+             "seconds": float(sum(all_stats[rows[0]][i]["seconds"] for rows in batches)),
+             "max_true_relres": float(max(all_stats[r][i]["true_relres"] for r in range(nr)))}
+        per_mass[f"{m:.4g}"] = e
 
     line = {
         "metric": METRIC, "value": t_step, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": args.inner, "data": "synthetic",
-        "config": {"workload": cfg["name"], "sources": nr, "masses": MASSES, "inner_prec": args.inner,
-                   "outer_prec": args.outer, "inner_tol": args.inner_tol or "library default",
-                   "mode": args.mode,
+        "vs_baseline": None, "dtype": inner, "data": "synthetic",
+        "config": {"workload": cfg["name"], "sources": nr, "source_batch": nb, "masses": masses,
+                   "inner_prec": inner, "outer_prec": args.outer,
+                   "inner_tol": args.inner_tol or "library default", "mode": args.mode,
                    "tol": 1e-10, "l2": "flushed (256 MB write) before every step; working set > L2",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "e2e": {"value": t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-        "gpu_launches": int(launches),
+        "gpu_launches": int(round(launches)),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": None,
-                     "kernel": f"k_hop<{args.inner}> (D_oe p, first hop of each BiCGstab iteration)",
+                     "kernel": f"k_hop<{inner}> (D_oe p, first hop of each BiCGstab iteration)",
                      "peak_kind": peak_kind, "bytes_per_launch": bytes_launch,
                      "avg_launch_us": avg_s * 1e6 if avg_s else None, "timed_launches": prof["launches"],
                      "gflops_1320": hop_gflops},
         "clocks": clk,
         "iterations_per_step": int(iters), "max_true_relres": worst, "per_mass": per_mass,
+        "device_memory_gb": footprint / 1e9,
         "gauge_generation_s": gen_s,
     }
     if rank == 0 and ws == 1 and not args.no_baseline:
         # FP64 BiCGstab-M on the same GPU, same sources and masses (context for
-        # the paper's comparison; not part of the timed step)
-        t_m, it_m, worst_m = 0.0, 0, 0.0
-        nsrc = min(nr, args.baseline_sources)
+        # the paper's comparison; not part of the timed step).  A fresh handle
+        # with FP64 links only, so its footprint is its own.
+        g.close()
+        del g, xs
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        mem1 = _used_bytes(torch)
+        g64 = api.Gauge(lat, U_dev, precs=("f64",))
+        t_m, it_m, worst_m, mem_m, polished = 0.0, 0, 0.0, 0, 0
+        per_shift = None
+        # with rhat = b a point source breaks the recurrences down at once
+        # (<b, r_1> = 0): such sources get a Gaussian shadow residual
+        point = cfg["sources"].startswith("point")
+        shadow = torch.from_numpy(synth.gaussian_source(dims, seed=cfg["seed"] + 1000)).to(dev) if point else None
+        prm_m = api.params(shadow=shadow)
+        nsrc = min(nr, args.baseline_sources or cfg.get("baseline_sources", nr))
         for r in range(nsrc):
-            xm = [torch.empty((V, 4, 3), dtype=torch.complex128, device=dev) for _ in MASSES]
+            xm = [torch.empty((V, 4, 3), dtype=torch.complex128, device=dev) for _ in masses]
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            stm = api.bicgstab_m_solve(g, bs[r], xm, MASSES, api.params(), check=False)
+            stm = api.bicgstab_m_solve(g64, bs[r], xm, masses, prm_m, check=False)
             torch.cuda.synchronize()
             t_m += time.perf_counter() - t0
+            mem_m = max(mem_m, _used_bytes(torch) - mem1)
             it_m += max(s["iterations"] for s in stm)
             worst_m = max(worst_m, max(s["true_relres"] for s in stm))
+            per_shift = [int(s["iterations"]) for s in stm]
+            polished += sum(1 for s in stm if s["restarts"] > 0)
             del xm
+        g64.close()
         line["bicgstab_m_fp64"] = {"seconds_per_step": t_m * nr / nsrc, "sources_run": nsrc,
                                    "iterations_per_source": it_m / nsrc, "max_true_relres": worst_m,
+                                   "iterations_per_mass_last_source": per_shift,
+                                   "shadow_residual": "Gaussian noise" if point else "b",
+                                   "masses_polished_by_single_mass": polished,
+                                   "device_memory_gb": mem_m / 1e9,
                                    "speedup_of_single_mass_scheme": (t_m * nr / nsrc) / t_step}
     if rank == 0 and ws == 1 and not args.no_cpu:
         s_it, n_it, dt = oracle_sample(cfg, U, bs_h, target_s=args.cpu_seconds)
-        line["cpu_baseline"] = {"value": s_it * iters, "unit": UNIT, "cores": 1, "kind": "oracle",
+        line["cpu_baseline"] = {"value": s_it * iters, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
                                 "sample": f"{n_it} FP64 oracle applications of M_prec (lightest mass, source 0) "
                                           f"took {dt:.1f} s on one host core = {s_it:.2f} s per BiCGstab "
                                           f"iteration (2 applications); scaled by the step's {iters} inner "
@@ -357,12 +430,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", choices=sorted(CONFIGS), default="c3")
-    ap.add_argument("--inner", choices=["f32", "f16", "f64"], default="f32")
+    ap.add_argument("--inner", choices=["f32", "f16", "f64"], default=None,
+                    help="inner precision (default: the workload's, f32 unless it names one)")
     ap.add_argument("--outer", choices=["df", "f64"], default="df")
     ap.add_argument("--rhs-block", type=int, default=0)
     ap.add_argument("--inner-tol", type=float, default=0.0)
     ap.add_argument("--mode", choices=["graph", "persistent", "host"], default="graph")
-    ap.add_argument("--baseline-sources", type=int, default=12)
+    ap.add_argument("--baseline-sources", type=int, default=0,
+                    help="sources for the BiCGstab-M comparison (default: the workload's, else all)")
+    ap.add_argument("--source-batch", type=int, default=0,
+                    help="sources per multimass_solve call (default: the workload's, else all)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-baseline", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

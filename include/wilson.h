@@ -100,6 +100,14 @@ typedef struct {
     int    outer_prec;   /* WL_F64 or WL_DF: precision of the residual recomputation
                             b - M x, of the solution accumulator and of the even-odd
                             reconstruction                                           */
+    const void *shadow;  /* bicgstab_m_solve only: the shadow residual rhat of the
+                            BiCGstab recurrences, a canonical complex128 full-lattice
+                            device vector owned by the caller, or NULL for rhat = b.
+                            With rhat = b a point source, <rhat, r_1> vanishes after
+                            one iteration (closed two-hop paths are backtracks and
+                            (1 - gamma_mu)(1 + gamma_mu) = 0), so point sources need
+                            a shadow such as Gaussian noise.  <rhat, b> must not
+                            vanish (WL_ERR_ARG).                                      */
 } wl_solver_params;
 
 typedef struct {
@@ -116,7 +124,7 @@ typedef struct {
  * inner_tol 0 (1e-6 for FP32, 3e-4 for FP16, 1e-12 for FP64; never below
  * what the outer target needs), max_restarts 100,
  * WL_GUESS_POLY, WL_MODE_GRAPH, rhs_block 0, graph_iters 8, eo 1,
- * outer_prec WL_DF. */
+ * outer_prec WL_DF, shadow NULL. */
 int wl_params_default(wl_solver_params *p);
 
 /* Thread-local message describing the last failing call on this thread. */

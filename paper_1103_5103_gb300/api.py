@@ -49,7 +49,7 @@ _vp, _int, _dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
 class SolverParams(ctypes.Structure):
     _fields_ = [("tol", _dbl), ("max_iter", _int), ("inner_prec", _int), ("inner_tol", _dbl),
                 ("max_restarts", _int), ("guess", _int), ("mode", _int), ("rhs_block", _int),
-                ("graph_iters", _int), ("eo", _int), ("outer_prec", _int)]
+                ("graph_iters", _int), ("eo", _int), ("outer_prec", _int), ("shadow", _vp)]
 
 
 class SolverStats(ctypes.Structure):
@@ -137,12 +137,18 @@ def _canon(t: torch.Tensor, V: int, what: str):
 
 def params(**kw) -> SolverParams:
     """Default solver parameters (wl_params_default) with keyword overrides;
-    inner_prec accepts 'f64' | 'f32' | 'f16'."""
+    inner_prec accepts 'f64' | 'f32' | 'f16'; shadow takes a canonical
+    complex128 CUDA tensor (kept alive by the returned object)."""
     p = SolverParams()
     _check(_lib.wl_params_default(ctypes.byref(p)))
     for k, v in kw.items():
         if k in ("inner_prec", "outer_prec"):
             v = _prec(v)
+        if k == "shadow" and v is not None:
+            if v.dtype != torch.complex128:
+                raise ValueError("shadow: expected a complex128 tensor")
+            p._shadow = v
+            v = _ptr(v).value
         if not hasattr(p, k):
             raise KeyError(k)
         setattr(p, k, v)

@@ -25,6 +25,10 @@
 
 namespace wl {
 
+// BiCGstab-M breakdown threshold: |<rhat, r>| or |<rhat, v>| below 1e-12 of
+// its Cauchy-Schwarz bound (squared here).
+constexpr double kBreakdown2 = 1e-24;
+
 struct ShiftState {
     double sigma;
     double pim_re, pim_im;     // pi_{n-1}
@@ -222,7 +226,14 @@ __global__ void __launch_bounds__(kBlock) k_m_update(Geom g, int nsb, Vec x, Vec
         const double ore = S.omega_re, oim = S.omega_im;
         const double rho2 = S.rho_re * S.rho_re + S.rho_im * S.rho_im;
         const double om2 = ore * ore + oim * oim;
-        if (!isfinite(rr) || !(rho2 > 0.0) || !(om2 > 0.0)) {
+        const double r12 = r1re * r1re + r1im * r1im;
+        if (!isfinite(rr)) {
+            S.breakdown = 1;
+            S.done = 1;
+        } else if (rr <= S.target2) {
+            S.done = 1;
+        } else if (!(rho2 > 0.0) || !(om2 > 0.0) || !(r12 > S.brk2 * S.rhat2 * rr)) {
+            // the next alpha would be rho / <rhat, v> with rho lost in rounding
             S.breakdown = 1;
             S.done = 1;
         } else {
@@ -235,7 +246,6 @@ __global__ void __launch_bounds__(kBlock) k_m_update(Geom g, int nsb, Vec x, Vec
             S.beta_im = qre * wim + qim * wre;
             S.rho_re = r1re;
             S.rho_im = r1im;
-            if (rr <= S.target2) S.done = 1;
         }
     }
 }
@@ -269,12 +279,31 @@ __global__ void __launch_bounds__(kBlock) k_m_p(Geom g, int nsb, Vec r, Vec p, V
     IO::store(p.rhs(h), str, i, pv);
 }
 
-// rho = <b, b> for rhat = r = p = b (host copies the halves).
-__global__ void k_m_init(BiState *st, const double *bn2, double target2)
+// Sums over n complex entries of canonical arrays: out = {Re <a, b>, Im <a, b>, ||a||^2}.
+__global__ void k_m_dots(const double2 *a, const double2 *b, size_t n, double *partials, unsigned *ticket,
+                         double *out)
 {
-    st->rho_re = *bn2;
-    st->rho_im = 0.0;
-    st->rr = *bn2;
+    double v[3] = {0.0, 0.0, 0.0};
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+        const double2 x = a[k], y = b[k];
+        v[0] += x.x * y.x + x.y * y.y;
+        v[1] += x.x * y.y - x.y * y.x;
+        v[2] += x.x * x.x + x.y * x.y;
+    }
+    double tot[3];
+    if (grid_sum<3>(v, partials, ticket, blockIdx.x, gridDim.x, tot) && threadIdx.x == 0)
+        for (int k = 0; k < 3; ++k) out[k] = tot[k];
+}
+
+// r = p = b.  rhat = b (dots == nullptr: rho = ||b||^2) or a given shadow
+// residual (dots = {Re <rhat, b>, Im <rhat, b>, ||rhat||^2}).
+__global__ void k_m_init(BiState *st, double bn2, const double *dots, double target2, double brk2)
+{
+    st->rho_re = dots ? dots[0] : bn2;
+    st->rho_im = dots ? dots[1] : 0.0;
+    st->rhat2 = dots ? dots[2] : bn2;
+    st->brk2 = brk2;
+    st->rr = bn2;
     st->target2 = target2;
     st->done = 0;
     st->breakdown = 0;
@@ -352,16 +381,16 @@ extern "C" int bicgstab_m_solve(wl_gauge *g, const void *b, void *const *x, cons
     WL_TRY(g->ws.get("bm_partials", sizeof(double) * 2 * nsb * kRedNV, &ppart));
     double *partials = static_cast<double *>(ppart);
     void *pn;
-    WL_TRY(g->ws.get("bm_norm", sizeof(double) * 4 + sizeof(unsigned) * 4, &pn));
-    double *d_norm = static_cast<double *>(pn);
-    unsigned *d_ticket = reinterpret_cast<unsigned *>(d_norm + 2);
+    WL_TRY(g->ws.get("bm_norm", sizeof(double) * 8 + sizeof(unsigned) * 4, &pn));
+    double *d_norm = static_cast<double *>(pn);            // ||b_e||^2, ||b_o||^2, then rhat dots
+    unsigned *d_ticket = reinterpret_cast<unsigned *>(d_norm + 8);
 
     // import b; ||b||^2
     const void *bc[1] = {b};
     Vec be = half_of(bv, 0), bo = half_of(bv, 1);
     WL_TRY(import_spinors(geo, bc, be, WL_EVEN, s));
     WL_TRY(import_spinors(geo, bc, bo, WL_ODD, s));
-    WL_CUDA_TRY(cudaMemsetAsync(pn, 0, sizeof(double) * 4 + sizeof(unsigned) * 4, s));
+    WL_CUDA_TRY(cudaMemsetAsync(pn, 0, sizeof(double) * 8 + sizeof(unsigned) * 4, s));
     WL_TRY(blas_norm2(geo, be, d_norm, partials, d_ticket, s));
     WL_TRY(blas_norm2(geo, bo, d_norm + 1, partials, d_ticket + 1, s));
     double hn[2];
@@ -373,7 +402,29 @@ extern "C" int bicgstab_m_solve(wl_gauge *g, const void *b, void *const *x, cons
     const size_t vb = bv.rhs_bytes * 2;
     WL_CUDA_TRY(cudaMemsetAsync(xv.ptr, 0, vb, s));
     WL_CUDA_TRY(cudaMemcpyAsync(r.ptr, bv.ptr, vb, cudaMemcpyDeviceToDevice, s));
-    WL_CUDA_TRY(cudaMemcpyAsync(rhat.ptr, bv.ptr, vb, cudaMemcpyDeviceToDevice, s));
+    double *d_dots = nullptr;
+    if (p->shadow) {
+        // given shadow residual: rho_0 = <rhat, b> must not vanish
+        const void *sc[1] = {p->shadow};
+        WL_TRY(import_spinors(geo, sc, half_of(rhat, 0), WL_EVEN, s));
+        WL_TRY(import_spinors(geo, sc, half_of(rhat, 1), WL_ODD, s));
+        void *pd;
+        WL_TRY(g->ws.get("bm_dots_partials", sizeof(double) * 3 * 1024, &pd));
+        d_dots = d_norm + 4;
+        k_m_dots<<<1024, 256, 0, s>>>(static_cast<const double2 *>(p->shadow), static_cast<const double2 *>(b),
+                                      (size_t)geo.Vh * 2 * 12, static_cast<double *>(pd), d_ticket + 2, d_dots);
+        WL_CUDA_TRY(cudaGetLastError());
+        note_launch(s);
+        double hd[3];
+        WL_CUDA_TRY(cudaMemcpyAsync(hd, d_dots, sizeof(hd), cudaMemcpyDeviceToHost, s));
+        WL_CUDA_TRY(cudaStreamSynchronize(s));
+        if (!(hd[0] * hd[0] + hd[1] * hd[1] > kBreakdown2 * hd[2] * bn2)) {
+            set_error("bicgstab_m_solve: shadow residual (numerically) orthogonal to b");
+            return WL_ERR_ARG;
+        }
+    } else {
+        WL_CUDA_TRY(cudaMemcpyAsync(rhat.ptr, bv.ptr, vb, cudaMemcpyDeviceToDevice, s));
+    }
     WL_CUDA_TRY(cudaMemcpyAsync(pv.ptr, bv.ptr, vb, cudaMemcpyDeviceToDevice, s));
     for (int k = 0; k < ns; ++k) {
         WL_CUDA_TRY(cudaMemsetAsync(xs[k].ptr, 0, vb, s));
@@ -396,7 +447,7 @@ extern "C" int bicgstab_m_solve(wl_gauge *g, const void *b, void *const *x, cons
     WL_CUDA_TRY(cudaMemcpyAsync(mst, &hm, sizeof(MState), cudaMemcpyHostToDevice, s));
     if (ns) WL_CUDA_TRY(cudaMemcpyAsync(sh, hsh.data(), sizeof(ShiftState) * ns, cudaMemcpyHostToDevice, s));
     // iterate the unshifted system to half the tolerance (iterated/true gap)
-    k_m_init<<<1, 1, 0, s>>>(st, d_norm, 0.25 * hm.target2);
+    k_m_init<<<1, 1, 0, s>>>(st, bn2, d_dots, 0.25 * hm.target2, kBreakdown2);
     note_launch(s);
     WL_CUDA_TRY(cudaStreamSynchronize(s));
 
@@ -534,5 +585,9 @@ extern "C" int bicgstab_m_solve(wl_gauge *g, const void *b, void *const *x, cons
         const double t2 = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         for (int i = 0; i < n_mass; ++i) stats[i].seconds = t2;
     }
+    if (hs.breakdown)
+        set_error("bicgstab_m_solve: the shifted recurrences broke down after " + std::to_string(hs.iters) +
+                  " iterations (<rhat, r> or <rhat, v> vanished; with rhat = b a point source this happens at "
+                  "once: pass a shadow residual); unconverged masses were finished by single-mass BiCGstab");
     return worst;
 }

@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(kBlock) k_xr_update(Geom g, Vec x, Vec p, Vec 
         } else {
             const double rho2 = S.rho_re * S.rho_re + S.rho_im * S.rho_im;
             const double om2 = ore * ore + oim * oim;
-            if (!(rho2 > 0.0) || !(om2 > 0.0) || !(r1re * r1re + r1im * r1im > 0.0)) {
+            if (!(rho2 > 0.0) || !(om2 > 0.0) || !(r1re * r1re + r1im * r1im > S.brk2 * S.rhat2 * rr)) {
                 S.breakdown = 1;
                 S.done = 1;
             } else {

@@ -307,6 +307,18 @@ __device__ __forceinline__ float2 unpack_half2(uint32_t u)
 
 template <> struct SpinorIO<WL_F16> {
     using R = float;
+    // Per-site scale = max |component|.  A site whose largest entry is below
+    // the smallest normal float is stored as zero: 1/scale would overflow to
+    // inf there (and 0 * inf = NaN), and such a site is below 1e-38 of any
+    // unit-normalised vector.  Point-source residuals decay exponentially
+    // with distance and reach this range on large lattices.
+    static __device__ __forceinline__ float site_scale(const cx<R> (&v)[12])
+    {
+        float m = 0.f;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) m = fmaxf(m, fmaxf(fabsf(v[k].re), fabsf(v[k].im)));
+        return m >= 1.17549435e-38f ? m : 0.f;
+    }
     static __device__ __forceinline__ const float *norms(const void *base, int stride)
     {
         return reinterpret_cast<const float *>(static_cast<const uint4 *>(base) + 3 * (size_t)stride);
@@ -328,9 +340,7 @@ template <> struct SpinorIO<WL_F16> {
     }
     static __device__ __forceinline__ void store(void *base, int stride, int i, const cx<R> (&v)[12])
     {
-        float m = 0.f;
-#pragma unroll
-        for (int k = 0; k < 12; ++k) m = fmaxf(m, fmaxf(fabsf(v[k].re), fabsf(v[k].im)));
+        float m = site_scale(v);
         const float inv = m > 0.f ? 1.0f / m : 0.f;
         uint4 *p = static_cast<uint4 *>(base);
 #pragma unroll
@@ -347,9 +357,7 @@ template <> struct SpinorIO<WL_F16> {
     // Replace v by the values a store followed by a load would return.
     static __device__ __forceinline__ void roundtrip(cx<R> (&v)[12])
     {
-        float m = 0.f;
-#pragma unroll
-        for (int k = 0; k < 12; ++k) m = fmaxf(m, fmaxf(fabsf(v[k].re), fabsf(v[k].im)));
+        const float m = site_scale(v);
         const float inv = m > 0.f ? 1.0f / m : 0.f;
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
@@ -548,6 +556,10 @@ struct BiState {
     double beta_re, beta_im;
     double rr;                  // ||r||^2 of the latest residual
     double target2;             // stop when rr <= target2
+    // Breakdown test: |<rhat, r>|^2 or |<rhat, v>|^2 at or below
+    // brk2 * ||rhat||^2 * ||.||^2.  brk2 = 0 (the default) tests for exact zero.
+    double rhat2;
+    double brk2;
     int done;                   // 1: converged or broken down -> kernels skip this rhs
     int breakdown;              // 1: a denominator vanished
     int iters;                  // completed iterations

@@ -213,7 +213,7 @@ struct EpiReduce {
     size_t rhs_bytes;
     BiState *st;
     double *partials;   // [rhs][block][kRedNV]
-    static constexpr int NV = KIND == 0 ? 2 : 3;
+    static constexpr int NV = 3;
 };
 
 template <int P, bool DAG, int NB, bool CG = false>
@@ -550,10 +550,15 @@ __global__ void __launch_bounds__(128) k_hop_reduce(HopArgs a, EpiReduce<KIND> e
             cx<R> rh[12];
             SpinorIO<P>::load(static_cast<const char *>(e.rhat) + off, a.g.stride, i, rh);
             cx<R> d = {R(0), R(0)};
+            R n = R(0);
 #pragma unroll
-            for (int k = 0; k < 12; ++k) d = conjmad(rh[k], o[k], d);
+            for (int k = 0; k < 12; ++k) {
+                d = conjmad(rh[k], o[k], d);
+                n = fma(o[k].re, o[k].re, fma(o[k].im, o[k].im, n));
+            }
             red[0] = (double)d.re;
             red[1] = (double)d.im;
+            red[2] = (double)n;
         } else {
             cx<R> d = {R(0), R(0)};
             R n = R(0);
@@ -574,7 +579,7 @@ __global__ void __launch_bounds__(128) k_hop_reduce(HopArgs a, EpiReduce<KIND> e
         if constexpr (KIND == 0) {
             const double dr = tot[0], di = tot[1];
             const double den = dr * dr + di * di;
-            if (!(den > 0.0) || !isfinite(den)) {
+            if (!(den > st.brk2 * st.rhat2 * tot[2]) || !isfinite(den)) {
                 st.breakdown = 1;
                 st.done = 1;
             } else {  // alpha = rho / <rhat, v>

@@ -204,6 +204,7 @@ extern "C" int wl_params_default(wl_solver_params *p)
     p->graph_iters = 8;
     p->eo = 1;
     p->outer_prec = WL_DF;
+    p->shadow = nullptr;
     return WL_OK;
 }
 

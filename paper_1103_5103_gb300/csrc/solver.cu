@@ -373,7 +373,12 @@ static int eo_defect_correction(wl_gauge *g, const Vec &bprec, const Vec &x64, d
             const double rn = std::sqrt(h_rn2[r]);
             h_active[r] = 0;
             if (outer_done[r]) continue;
-            if (!std::isfinite(rn)) { outer_done[r] = 1; stats[r].status = WL_ERR_BREAKDOWN; continue; }
+            if (!std::isfinite(rn)) {
+                outer_done[r] = 1;
+                stats[r].status = WL_ERR_BREAKDOWN;
+                set_error("defect correction: non-finite true residual (rhs " + std::to_string(r) + ")");
+                continue;
+            }
             if (rn <= prm.tol * bnorm[r]) {
                 if (lincomb_check) continue;  // confirmed by the next, hop-based check
                 outer_done[r] = 1;
@@ -383,6 +388,10 @@ static int eo_defect_correction(wl_gauge *g, const Vec &bprec, const Vec &x64, d
             if (iters[r] >= prm.max_iter || restarts[r] >= prm.max_restarts || fails[r] >= 5) {
                 outer_done[r] = 1;
                 stats[r].status = fails[r] >= 5 ? WL_ERR_BREAKDOWN : WL_ERR_NOCONV;
+                set_error(std::string("defect correction: ") +
+                          (fails[r] >= 5 ? "five restarts without halving the residual"
+                                         : "iteration or restart cap reached") +
+                          " (rhs " + std::to_string(r) + ")");
                 continue;
             }
             // no need to iterate the inner solve below what the outer target needs

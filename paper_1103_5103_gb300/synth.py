@@ -21,6 +21,11 @@ row 2 = conj(row 0 x row 1) holds to rounding (U in SU(3)).
 """
 from __future__ import annotations
 
+import multiprocessing as mp
+import os
+from concurrent.futures import ProcessPoolExecutor
+from multiprocessing import shared_memory
+
 import numpy as np
 
 _M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
@@ -105,17 +110,52 @@ def su3_from_coeffs(c: np.ndarray, eps: float) -> np.ndarray:
     return _reunitarize(U)
 
 
-def gauge_field(dims, eps: float, seed: int, chunk: int = 1 << 20) -> np.ndarray:
-    """Random SU(3) links U_mu(n) = exp(i eps H), canonical layout (4, V, 3, 3)."""
+def _gauge_chunk(flat: np.ndarray, start: int, stop: int, eps: float, seed: int) -> None:
+    link = np.arange(start, stop, dtype=np.uint64)  # link = mu*V + site
+    ctr = link[:, None] * np.uint64(8) + np.arange(8, dtype=np.uint64)[None, :]
+    flat[start:stop] = su3_from_coeffs(normal(seed, STREAM_GAUGE, ctr), eps)
+
+
+def _gauge_worker(args) -> None:
+    name, n_links, starts, chunk, eps, seed = args
+    shm = shared_memory.SharedMemory(name=name)
+    try:
+        flat = np.ndarray((n_links, 3, 3), dtype=np.complex128, buffer=shm.buf)
+        for start in starts:
+            _gauge_chunk(flat, start, min(n_links, start + chunk), eps, seed)
+        del flat
+    finally:
+        shm.close()
+
+
+def gauge_field(dims, eps: float, seed: int, chunk: int = 1 << 20, workers: int | None = None) -> np.ndarray:
+    """Random SU(3) links U_mu(n) = exp(i eps H), canonical layout (4, V, 3, 3).
+
+    Every link is a pure function of (seed, link index), so the field is the
+    same for any chunking.  Fields of 8M links or more are generated by
+    ``workers`` spawned processes (default: one per core, at most 16) writing
+    into shared memory."""
     V = volume(dims)
-    out = np.empty((4, V, 3, 3), dtype=np.complex128)
-    flat = out.reshape(4 * V, 3, 3)
-    for start in range(0, 4 * V, chunk):
-        stop = min(4 * V, start + chunk)
-        link = np.arange(start, stop, dtype=np.uint64)  # link = mu*V + site
-        ctr = link[:, None] * np.uint64(8) + np.arange(8, dtype=np.uint64)[None, :]
-        c = normal(seed, STREAM_GAUGE, ctr)
-        flat[start:stop] = su3_from_coeffs(c, eps)
+    n_links = 4 * V
+    starts = list(range(0, n_links, chunk))
+    if workers is None:
+        workers = min(16, os.cpu_count() or 1, len(starts)) if n_links >= (1 << 23) else 1
+    if workers <= 1:
+        out = np.empty((4, V, 3, 3), dtype=np.complex128)
+        flat = out.reshape(n_links, 3, 3)
+        for start in starts:
+            _gauge_chunk(flat, start, min(n_links, start + chunk), eps, seed)
+        return out
+    shm = shared_memory.SharedMemory(create=True, size=n_links * 9 * 16)
+    try:
+        jobs = [(shm.name, n_links, starts[w::workers], chunk, eps, seed) for w in range(workers)]
+        # a worker that dies raises BrokenProcessPool here instead of being respawned
+        with ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+            list(ex.map(_gauge_worker, jobs))
+        out = np.ndarray((4, V, 3, 3), dtype=np.complex128, buffer=shm.buf).copy()
+    finally:
+        shm.close()
+        shm.unlink()
     return out
 
 

@@ -88,6 +88,37 @@ def test_internal_layout_roundtrip(api, prec):
         assert err < {"df": 1e-14, "f32": 1e-7, "f16": 1e-3}[prec], err
 
 
+def test_f16_sites_below_float_range_store_as_zero(api):
+    """FP16 storage scales each site by its largest entry.  Sites whose
+    entries are all below the smallest normal float (here 1e-40, an FP32
+    denormal) are stored as zero, not as NaN; sites at 1e-30 and at 1 keep
+    FP16 accuracy relative to themselves; the operator stays finite."""
+    dims = (6, 4, 4, 8)
+    U, lat, g = _setup(api, dims, "random")
+    psi = synth.gaussian_source(dims, seed=7)
+    n = np.arange(lat.volume)
+    scale = np.where(n % 3 == 0, 1e-40, np.where(n % 3 == 1, 1e-30, 1.0))
+    psi = psi * scale[:, None, None]
+    d = _cuda(psi)
+    back = torch.zeros_like(d)
+    for par in (0, 1):
+        buf = lat.new_internal("f16")
+        lat.spinor_import(d, buf, "f16", par)
+        lat.spinor_export(buf, back, "f16", par)
+    b = back.cpu().numpy()
+    assert np.all(np.isfinite(b))
+    assert np.all(b[n % 3 == 0] == 0)
+    for k in (1, 2):
+        s = n % 3 == k
+        err = np.linalg.norm((b[s] - psi[s]).reshape(s.sum(), -1), axis=1)
+        assert np.all(err <= 2e-3 * np.linalg.norm(psi[s].reshape(s.sum(), -1), axis=1))
+    out = torch.empty_like(d)
+    api.wilson_dslash(g, d, out, 0.12, "f16", api.OP_M)
+    o = out.cpu().numpy()
+    assert np.all(np.isfinite(o))
+    assert rel(o, O.apply(O.OP_MK, U, dims, psi, 0.12)) < TOL["f16"]
+
+
 @pytest.mark.parametrize("prec", ["f64", "f32", "f16", "df"])
 @pytest.mark.parametrize("parity", [0, 1])
 def test_wilson_hop_internal_xpay(api, prec, parity):

@@ -99,6 +99,7 @@ def test_bicgstab_m_vs_oracle(api):
     ref, _ = O.bicgstab_m(U, dims, b, masses, tol=1e-12)
     for i, m in enumerate(masses):
         assert stats[i]["true_relres"] <= 1e-10, stats[i]
+        assert stats[i]["restarts"] == 0, stats[i]   # no single-mass polish was needed
         assert rel(xs[i].cpu().numpy(), ref[i]) < 1e-8
     # the unshifted (lightest) mass needs the most iterations; heavier ones freeze earlier
     its = [stats[i]["iterations"] for i in range(len(masses))]
@@ -194,3 +195,58 @@ def test_persistent_barrier_wait_is_bounded(api):
     x = torch.zeros_like(b)
     st = api.bicgstab_solve(g, b, x, 0.2, api.params(mode=api.MODE_PERSISTENT))
     assert st["status"] == 0 and st["true_relres"] <= 1e-10
+
+
+def test_f16_inner_with_source_entries_below_float_range(api):
+    """A source with entries in the FP32 denormal range (as a point-source
+    residual far from the source on a large lattice) must not break the
+    FP16-storage inner solve."""
+    dims = (8, 8, 8, 8)
+    U = synth.gauge_field(dims, 0.3, seed=1)
+    b = synth.point_source(dims) + 1e-40 * synth.gaussian_source(dims, seed=12)
+    lat = api.Lattice(dims)
+    g = api.Gauge(lat, _cuda(U))
+    x = torch.zeros_like(_cuda(b))
+    st = api.bicgstab_solve(g, _cuda(b), x, 0.1, api.params(inner_prec="f16"))
+    assert st["status"] == api.WL_OK and st["true_relres"] <= 1e-10, st
+    assert O.true_relres(U, dims, b, x.cpu().numpy(), 0.1) <= 1.02e-10
+
+
+def test_bicgstab_m_point_source_with_gaussian_shadow(api):
+    """Point source, shadow residual = Gaussian noise (passed to both sides):
+    the shifted solutions match the oracle's, with the same iteration count,
+    and no mass needs the single-mass polish."""
+    dims = (4, 4, 4, 8)
+    U, lat, g = _gauge(api, dims, 0.5, 43, precs=("f64",))
+    b = synth.point_source(dims, 1, 2)
+    rh = synth.gaussian_source(dims, seed=44)
+    masses = [0.4, 0.2, 0.05]
+    xs = [torch.empty((lat.volume, 4, 3), dtype=torch.complex128, device="cuda") for _ in masses]
+    stats = api.bicgstab_m_solve(g, _cuda(b), xs, masses, api.params(shadow=_cuda(rh)))
+    ref, ost = O.bicgstab_m(U, dims, b, masses, tol=0.5e-10, rhat=rh)
+    assert ost["status"] == O.OK
+    for i, m in enumerate(masses):
+        assert stats[i]["true_relres"] <= 1e-10 and stats[i]["restarts"] == 0, stats[i]
+        assert rel(xs[i].cpu().numpy(), ref[i]) < 1e-8
+    assert abs(stats[2]["iterations"] - ost["iterations"][2]) <= 1, (stats, ost)
+
+
+def test_bicgstab_m_point_source_without_shadow_reports_breakdown(api):
+    """rhat = b for a point source: <rhat, r_1> = 0, the shifted recurrences
+    stop with WL_ERR_BREAKDOWN (as the oracle's do), every mass is then
+    polished by single-mass FP64 BiCGstab, and the polish is visible in
+    stats.restarts."""
+    dims = (4, 4, 4, 8)
+    U, lat, g = _gauge(api, dims, 0.5, 43, precs=("f64",))
+    b = synth.point_source(dims)
+    masses = [0.4, 0.1]
+    _, ost = O.bicgstab_m(U, dims, b, masses, tol=1e-10)
+    assert ost["status"] == O.BREAKDOWN
+    xs = [torch.empty((lat.volume, 4, 3), dtype=torch.complex128, device="cuda") for _ in masses]
+    with pytest.raises(api.WilsonError) as e:
+        api.bicgstab_m_solve(g, _cuda(b), xs, masses, api.params())
+    assert e.value.status == api.WL_ERR_BREAKDOWN
+    stats = api.bicgstab_m_solve(g, _cuda(b), xs, masses, api.params(), check=False)
+    for i, m in enumerate(masses):
+        assert stats[i]["restarts"] > 0 and stats[i]["true_relres"] <= 1e-10, stats[i]
+        assert O.true_relres(U, dims, b, xs[i].cpu().numpy(), m) <= 1.02e-10
