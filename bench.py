@@ -54,6 +54,12 @@ CONFIGS = {
 # rhs one input spinor (each read once) and one output spinor
 LINK_B = {"f64": 96, "df": 96, "f32": 48, "f16": 24}
 SPINOR_B = {"f64": 192, "df": 192, "f32": 96, "f16": 52}
+# DRAM bytes (read + write) per launch of the timed hop kernel from one ncu
+# capture, keyed by (precision, autotuner variant, rhs per launch): (half-
+# lattice sites of the captured case, bytes).  Traffic scales with sites.
+# An entry is valid only for the kernel as it was when captured; remove it
+# when that kernel changes.
+HOP_TRAFFIC = {("f32", 205, 12): (442368, 1244.7e6), ("f16", 101, 2): (1048576, 404.7e6)}
 # The reference arm cannot afford a full oracle solve; it times a sample of
 # oracle BiCGstab iterations and scales by this many inner iterations per
 # step (the paper scheme's FP32-inner count on the c3 workload, from the
@@ -299,6 +305,7 @@ def run_ours(args, cfg):
     launches = (api.launch_count() - launches0) / max(1, args.steps)
     prof = api.profile_read(g)[inner]
     api.profile_enable(g, False)
+    hop_variant = api.autotune(g, inner, nb)[0]   # the cached choice the solves used
     barrier(ws)
     t_step = max_over_ranks(float(np.mean(step_ms)) / 1e3, ws)
 
@@ -341,6 +348,10 @@ def run_ours(args, cfg):
         hop_gflops = 1320 * per_launch_site_rhs / avg_s / 1e9
     else:
         bytes_launch = avg_s = achieved = hop_gflops = None
+    traffic = None
+    if (inner, hop_variant, nb) in HOP_TRAFFIC:
+        sites_cap, bytes_cap = HOP_TRAFFIC[(inner, hop_variant, nb)]
+        traffic = bytes_cap * (V // 2) / sites_cap
     iters = sum(st["iterations"] for row in all_stats for st in row)
     worst = max(st["true_relres"] for row in all_stats for st in row)
     per_mass = {}
@@ -363,8 +374,9 @@ def run_ours(args, cfg):
         "e2e": {"value": t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(round(launches)),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": None,
-                     "kernel": f"k_hop<{inner}> (D_oe p, first hop of each BiCGstab iteration)",
+                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "kernel": f"k_hop<{inner}> (D_oe p, first hop of each BiCGstab iteration), "
+                               f"autotuned variant {hop_variant}",
                      "peak_kind": peak_kind, "bytes_per_launch": bytes_launch,
                      "avg_launch_us": avg_s * 1e6 if avg_s else None, "timed_launches": prof["launches"],
                      "gflops_1320": hop_gflops},

@@ -76,7 +76,11 @@ extern "C" {
 
 /* ------------------------------------------------------ solver parameters */
 #define WL_GUESS_ZERO 0  /* zero initial guess for every mass                     */
-#define WL_GUESS_POLY 1  /* Lagrange extrapolation through all previous masses    */
+#define WL_GUESS_POLY 1  /* Lagrange extrapolation through the previous masses
+                            (Section 6.2.1, Eq. Poly)                           */
+#define WL_GUESS_SSM  2  /* solution-space minimisation: the combination of the
+                            previous solutions with the smallest residual
+                            (Section 6.2.2)                                     */
 
 #define WL_MODE_HOST       0  /* one host round trip per iteration                      */
 #define WL_MODE_GRAPH      1  /* iterations captured in a CUDA graph, scalars on device */
@@ -108,6 +112,8 @@ typedef struct {
                             (1 - gamma_mu)(1 + gamma_mu) = 0), so point sources need
                             a shadow such as Gaussian noise.  <rhat, b> must not
                             vanish (WL_ERR_ARG).                                      */
+    int    guess_max;    /* multimass_solve: previous masses the guess uses, the most
+                            recently solved (nearest) ones; 0 = all of them         */
 } wl_solver_params;
 
 typedef struct {
@@ -124,7 +130,7 @@ typedef struct {
  * inner_tol 0 (1e-6 for FP32, 3e-4 for FP16, 1e-12 for FP64; never below
  * what the outer target needs), max_restarts 100,
  * WL_GUESS_POLY, WL_MODE_GRAPH, rhs_block 0, graph_iters 8, eo 1,
- * outer_prec WL_DF, shadow NULL. */
+ * outer_prec WL_DF, shadow NULL, guess_max 0. */
 int wl_params_default(wl_solver_params *p);
 
 /* Thread-local message describing the last failing call on this thread. */
@@ -238,7 +244,10 @@ int bicgstab_solve(wl_gauge *g, const void *b, void *x, double m0, const wl_solv
  * kappa-form solution (m0[i] + 4) psi_i as a canonical complex128 vector.
  * A shift whose FP64 true residual is still above tol afterwards is polished
  * by a single-mass FP64 BiCGstab from x[i]; its extra iterations are counted
- * in stats[i].restarts.  Masses must be distinct.  Synchronises the stream. */
+ * in stats[i].restarts.  The shadow residual is p->shadow (NULL: b).
+ * Returns WL_ERR_BREAKDOWN, with the polished solutions in x, when the
+ * shifted recurrences broke down.  Masses must be distinct.  Synchronises
+ * the stream. */
 int bicgstab_m_solve(wl_gauge *g, const void *b, void *const *x, const double *m0, int n_mass,
                      const wl_solver_params *p, wl_solver_stats *stats, void *stream);
 
@@ -246,7 +255,14 @@ int bicgstab_m_solve(wl_gauge *g, const void *b, void *const *x, const double *m
  * sorted heaviest first; each solved with even-odd preconditioned,
  * mixed-precision BiCGstab; initial guess for mass k by Lagrange
  * extrapolation through all k-1 previous solutions (Eq. Poly, extrapolating
- * the paper-normalised psi = x / (m0 + 4)).  b[r] (r < n_rhs) are canonical
+ * the paper-normalised psi = x / (m0 + 4)), or, with p->guess =
+ * WL_GUESS_SSM, by the combination of them with the smallest residual
+ * (Section 6.2.2; the Gram matrix of the solutions is formed on the
+ * canonical outputs x as they are written, and the k x k normal equations
+ * are solved on the host); p->guess_max limits either to the most recent
+ * solutions.  The first residual of each mass is the same linear
+ * combination of the stored D_eo D_oe x_j, so it costs no hop; a hop-based
+ * check confirms convergence.  b[r] (r < n_rhs) are canonical
  * sources; x[r * n_mass + i] receives the solution for source r and mass
  * m0[i]; stats[r * n_mass + i] its statistics.  All right-hand sides of one
  * mass are solved together by batched kernels.  Masses must be distinct.

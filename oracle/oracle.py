@@ -258,26 +258,38 @@ def ssm_coefficients(b, psis, m_prev, m):
     return np.linalg.solve(G, rhs)
 
 
-def multimass_solve(U, dims, b, masses, tol=1e-10, guess="poly", maxiter=10000, antiperiodic=True):
+def initial_guess(b, done_psi, done_m, m, guess="poly", guess_max=0):
+    """Full-lattice kappa-form initial guess for mass m from the previous
+    paper-normalised solutions psi_j (in solve order): Lagrange extrapolation
+    (Section 6.2.1) or solution-space minimisation (Section 6.2.2) through the
+    last guess_max of them (0: all).  None when there is nothing to use."""
+    if guess == "zero" or not done_m:
+        return None
+    k = len(done_m) if guess_max <= 0 else min(guess_max, len(done_m))
+    ms, ps = done_m[-k:], done_psi[-k:]
+    if guess == "poly":
+        c = lagrange_weights(ms, m)
+    elif guess == "ssm":
+        c = ssm_coefficients(b, ps, ms, m)
+    else:
+        raise ValueError(guess)
+    return (m + 4.0) * sum(cj * pj for cj, pj in zip(c, ps))
+
+
+def multimass_solve(U, dims, b, masses, tol=1e-10, guess="poly", maxiter=10000, antiperiodic=True, guess_max=0):
     """The paper's single-mass scheme (Section 6.2, Section 7): masses solved
     heaviest first, each by even-odd-preconditioned BiCGstab started from the
     polynomial extrapolation through all previous solutions (extrapolating the
-    paper-normalised solution psi = x / (m + 4) on even sites).  Returns
-    kappa-form solutions in the caller's mass order and per-mass stats."""
+    paper-normalised solution psi = x / (m + 4) on even sites), or from the
+    solution-space minimisation guess.  Returns kappa-form solutions in the
+    caller's mass order and per-mass stats."""
     order = sorted(range(len(masses)), key=lambda i: -masses[i])
     odd = parity_mask(dims)
     done_m, done_psi = [], []
     xs, stats = [None] * len(masses), [None] * len(masses)
     for i in order:
         m = float(masses[i])
-        x0 = None
-        if done_m and guess == "poly":
-            w = lagrange_weights(done_m, m)
-            psi = sum(wj * pj for wj, pj in zip(w, done_psi))
-            x0 = (m + 4.0) * psi
-        elif done_m and guess == "ssm":
-            c = ssm_coefficients(b, done_psi, done_m, m)
-            x0 = (m + 4.0) * sum(cj * pj for cj, pj in zip(c, done_psi))
+        x0 = initial_guess(b, done_psi, done_m, m, guess, guess_max)
         if x0 is not None:
             x0 = x0.copy()
             x0[odd] = 0

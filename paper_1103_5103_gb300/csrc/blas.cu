@@ -386,9 +386,9 @@ struct LinIn {
 };
 
 // out = sum_{j<k} c_j in_j and, optionally, out2 = sum_{j<k2} c2_j in_j
-// (k <= k2: the first k inputs are shared and read once).  Coefficients are
-// real, per rhs: c[r * k + j], c2[r * k2 + j].
-template <int PO>
+// (k <= k2: the first k inputs are shared and read once).  Coefficients per
+// rhs: c[r * k + j], c2[r * k2 + j]; real, or complex (CPLX: re, im pairs).
+template <int PO, bool CPLX>
 __global__ void __launch_bounds__(kBlock) k_lincomb(Geom g, LinIn in, int k, int k2, size_t rhs_bytes, int nrhs,
                                                     const double *c1, const double *c2, Vec out, Vec out2)
 {
@@ -402,15 +402,30 @@ __global__ void __launch_bounds__(kBlock) k_lincomb(Geom g, LinIn in, int k, int
     for (int j = 0; j < kmax; ++j) {
         cx<R> v[12];
         SpinorIO<PO>::load(static_cast<const char *>(in.p[j]) + (size_t)q.r * rhs_bytes, g.stride, q.i, v);
-        if (j < k) {
-            const R w = Conv<R>::from(c1[q.r * k + j]);
+        if constexpr (CPLX) {
+            if (j < k) {
+                const double *w = c1 + 2 * ((size_t)q.r * k + j);
+                const cx<R> z = {Conv<R>::from(w[0]), Conv<R>::from(w[1])};
 #pragma unroll
-            for (int c = 0; c < 12; ++c) acc[c] = {fma(w, v[c].re, acc[c].re), fma(w, v[c].im, acc[c].im)};
-        }
-        if (j < k2) {
-            const R w = Conv<R>::from(c2[q.r * k2 + j]);
+                for (int c = 0; c < 12; ++c) acc[c] = cmad(z, v[c], acc[c]);
+            }
+            if (j < k2) {
+                const double *w = c2 + 2 * ((size_t)q.r * k2 + j);
+                const cx<R> z = {Conv<R>::from(w[0]), Conv<R>::from(w[1])};
 #pragma unroll
-            for (int c = 0; c < 12; ++c) acc2[c] = {fma(w, v[c].re, acc2[c].re), fma(w, v[c].im, acc2[c].im)};
+                for (int c = 0; c < 12; ++c) acc2[c] = cmad(z, v[c], acc2[c]);
+            }
+        } else {
+            if (j < k) {
+                const R w = Conv<R>::from(c1[q.r * k + j]);
+#pragma unroll
+                for (int c = 0; c < 12; ++c) acc[c] = {fma(w, v[c].re, acc[c].re), fma(w, v[c].im, acc[c].im)};
+            }
+            if (j < k2) {
+                const R w = Conv<R>::from(c2[q.r * k2 + j]);
+#pragma unroll
+                for (int c = 0; c < 12; ++c) acc2[c] = {fma(w, v[c].re, acc2[c].re), fma(w, v[c].im, acc2[c].im)};
+            }
         }
     }
     if (k > 0) SpinorIO<PO>::store(out.rhs(q.r), g.stride, q.i, acc);
@@ -418,7 +433,7 @@ __global__ void __launch_bounds__(kBlock) k_lincomb(Geom g, LinIn in, int k, int
 }
 
 int blas_lincomb2(const Geom &g, const double *c1_dev, const Vec *const *in, int k, const Vec *out,
-                  const double *c2_dev, int k2, const Vec *out2, cudaStream_t s)
+                  const double *c2_dev, int k2, const Vec *out2, cudaStream_t s, bool complex_coef)
 {
     if (k < 0 || k2 < 0 || k + k2 < 1 || k > 32 || k2 > 32) { set_error("blas_lincomb: 1..32 inputs"); return WL_ERR_ARG; }
     LinIn li;
@@ -427,10 +442,15 @@ int blas_lincomb2(const Geom &g, const double *c1_dev, const Vec *const *in, int
     const Vec &o = k > 0 ? *out : *out2;
     Vec o2 = k2 > 0 ? *out2 : o;
     const Vec o1 = k > 0 ? *out : o2;
-    if (o.prec == WL_DF)
-        k_lincomb<WL_DF><<<grid_of(g, o.nrhs), kBlock, 0, s>>>(g, li, k, k2, o.rhs_bytes, o.nrhs, c1_dev, c2_dev, o1, o2);
+    const int grid = grid_of(g, o.nrhs);
+    if (o.prec == WL_DF && complex_coef)
+        k_lincomb<WL_DF, true><<<grid, kBlock, 0, s>>>(g, li, k, k2, o.rhs_bytes, o.nrhs, c1_dev, c2_dev, o1, o2);
+    else if (o.prec == WL_DF)
+        k_lincomb<WL_DF, false><<<grid, kBlock, 0, s>>>(g, li, k, k2, o.rhs_bytes, o.nrhs, c1_dev, c2_dev, o1, o2);
+    else if (o.prec == WL_F64 && complex_coef)
+        k_lincomb<WL_F64, true><<<grid, kBlock, 0, s>>>(g, li, k, k2, o.rhs_bytes, o.nrhs, c1_dev, c2_dev, o1, o2);
     else if (o.prec == WL_F64)
-        k_lincomb<WL_F64><<<grid_of(g, o.nrhs), kBlock, 0, s>>>(g, li, k, k2, o.rhs_bytes, o.nrhs, c1_dev, c2_dev, o1, o2);
+        k_lincomb<WL_F64, false><<<grid, kBlock, 0, s>>>(g, li, k, k2, o.rhs_bytes, o.nrhs, c1_dev, c2_dev, o1, o2);
     else { set_error("blas_lincomb: outer precision only"); return WL_ERR_ARG; }
     WL_CUDA_TRY(cudaGetLastError());
     note_launch(s);
@@ -441,6 +461,67 @@ int blas_lincomb(const Geom &g, const double *cre_dev, const double *, const Vec
                  const Vec &out, cudaStream_t s)
 {
     return blas_lincomb2(g, cre_dev, in, k, &out, nullptr, 0, nullptr, s);
+}
+
+// -------------------------------- inner products of canonical vectors
+// Solution-space minimisation (Section 6.2.2) needs the Gram matrix of the
+// solutions and their overlap with the source; those are formed once per
+// solved mass on the canonical complex128 outputs.
+
+struct DotIn {
+    const double2 *p[16];
+};
+
+template <int N>
+__global__ void __launch_bounds__(256) k_canon_dots(const double2 *a, DotIn in, size_t n, double *partials,
+                                                    unsigned *ticket, double *out)
+{
+    double v[2 * N];
+#pragma unroll
+    for (int j = 0; j < 2 * N; ++j) v[j] = 0.0;
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+        const double2 y = a[k];
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            const double2 x = in.p[j][k];
+            v[2 * j] += x.x * y.x + x.y * y.y;      // Re conj(x) y
+            v[2 * j + 1] += x.x * y.y - x.y * y.x;  // Im conj(x) y
+        }
+    }
+    double tot[2 * N];
+    if (grid_sum<2 * N>(v, partials, ticket, blockIdx.x, gridDim.x, tot) && threadIdx.x == 0)
+        for (int j = 0; j < 2 * N; ++j) out[j] = tot[j];
+}
+
+template <int N>
+static void launch_canon_dots(const double2 *a, const DotIn &in, size_t n, double *partials, unsigned *ticket,
+                              double *out, cudaStream_t s)
+{
+    k_canon_dots<N><<<1024, 256, 0, s>>>(a, in, n, partials, ticket, out);
+}
+
+int canon_dots(const void *const *a, const void *const *in, int n, int nrhs, size_t n_complex, double *dots_dev,
+               double *partials, unsigned *tickets, cudaStream_t s)
+{
+    if (n < 1 || n > 16 || nrhs < 1) { set_error("canon_dots: 1..16 vectors"); return WL_ERR_ARG; }
+    for (int r = 0; r < nrhs; ++r) {
+        DotIn di;
+        for (int j = 0; j < n; ++j) di.p[j] = static_cast<const double2 *>(in[r * n + j]);
+        const double2 *ar = static_cast<const double2 *>(a[r]);
+        double *o = dots_dev + 2 * (size_t)n * r;
+        // the reduction width is a template parameter: round n up to 4, 8 or 16
+        // (unused slots read input 0 and are ignored)
+        const int nn = n <= 4 ? 4 : n <= 8 ? 8 : 16;
+        for (int j = n; j < nn; ++j) di.p[j] = di.p[0];
+        double *tmp = partials + 2 * 16 * 1024;  // nn outputs before the first n are kept
+        if (nn == 4) launch_canon_dots<4>(ar, di, n_complex, partials, tickets + r, tmp, s);
+        else if (nn == 8) launch_canon_dots<8>(ar, di, n_complex, partials, tickets + r, tmp, s);
+        else launch_canon_dots<16>(ar, di, n_complex, partials, tickets + r, tmp, s);
+        WL_CUDA_TRY(cudaGetLastError());
+        note_launch(s);
+        WL_CUDA_TRY(cudaMemcpyAsync(o, tmp, sizeof(double) * 2 * n, cudaMemcpyDeviceToDevice, s));
+    }
+    return WL_OK;
 }
 
 // ------------------------------ even-odd reconstruction with its residual

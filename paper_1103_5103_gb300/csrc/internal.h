@@ -126,9 +126,15 @@ int blas_norm2(const Geom &g, const Vec &a, double *out_dev, double *partials, u
 // c[r * k + j] (cim_dev is ignored)
 int blas_lincomb(const Geom &g, const double *cre_dev, const double *cim_dev, const Vec *const *in, int k,
                  const Vec &out, cudaStream_t s);
-// out = sum_{j<k} c1_j in_j and out2 = sum_{j<k2} c2_j in_j in one pass
+// out = sum_{j<k} c1_j in_j and out2 = sum_{j<k2} c2_j in_j in one pass;
+// complex_coef: the coefficients are (re, im) pairs, c[2 * (r * k + j) + {0, 1}]
 int blas_lincomb2(const Geom &g, const double *c1_dev, const Vec *const *in, int k, const Vec *out,
-                  const double *c2_dev, int k2, const Vec *out2, cudaStream_t s);
+                  const double *c2_dev, int k2, const Vec *out2, cudaStream_t s, bool complex_coef = false);
+// For each rhs r: dots[r][j] = <in_j[r], a[r]> (j < n, n <= 16), FP64 sums
+// over n_complex entries of canonical complex128 arrays; dots_dev holds
+// 2 * n * nrhs doubles (re, im).  partials: 2 * 16 * 1024 doubles, tickets: nrhs.
+int canon_dots(const void *const *a, const void *const *in, int n, int nrhs, size_t n_complex, double *dots_dev,
+               double *partials, unsigned *tickets, cudaStream_t s);
 int blas_convert(const Geom &g, const Vec &in, const Vec &out, cudaStream_t s);
 int blas_xpay(const Geom &g, const Vec &x, double a, const Vec &y, const Vec &out, cudaStream_t s);  // out = x + a y
 // x_o = b_o + kappa Dx and ||b_o - x_o + kappa Dx||^2 per rhs into norm2_dev

@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <complex>
 #include <cstring>
 #include <numeric>
 #include <string>
@@ -517,7 +518,7 @@ static int check_params(const wl_gauge *g, const wl_solver_params *p)
 {
     if (!p || !(p->tol > 0) || p->max_iter < 1 || !valid_prec(p->inner_prec) || p->inner_prec == WL_DF ||
         p->max_restarts < 1 || (p->mode != WL_MODE_HOST && p->mode != WL_MODE_GRAPH && p->mode != WL_MODE_PERSISTENT) ||
-        p->graph_iters < 0 ||
+        p->graph_iters < 0 || p->guess < WL_GUESS_ZERO || p->guess > WL_GUESS_SSM || p->guess_max < 0 ||
         p->rhs_block < 0 || p->rhs_block > 4 || (p->outer_prec != WL_F64 && p->outer_prec != WL_DF)) {
         set_error("solver parameters out of range");
         return WL_ERR_ARG;
@@ -618,6 +619,62 @@ extern "C" int bicgstab_solve(wl_gauge *g, const void *b, void *x, double m0, co
     return st[0].status;
 }
 
+// Solution-space minimisation guess (Section 6.2.2) for mass m from the
+// solutions x_j, j = j0 .. j0+kk-1 in solve order: minimise ||b - M_p(m) psi||
+// over psi = sum_j c_j psi_j, psi_j = x_j / (m_j + 4).  With
+// M_p(m) psi_j = b + (m - m_j) psi_j = d_j, the normal equations
+// sum_j <d_i, d_j> c_j = <d_i, b> need only ||b||^2, <b, x_j> and the Gram
+// matrix <x_i, x_j>: with f_i = (m - m_i) / (m_i + 4),
+//   <d_i, d_j> = ||b||^2 + f_j <b, x_j> + f_i conj<b, x_i> + f_i f_j <x_i, x_j>,
+//   <d_i, b>   = ||b||^2 + f_i conj<b, x_i>.
+// Returns the kappa-form weights g_j = c_j (m + 4) / (m_j + 4) of the x_j.
+// Solved by Gaussian elimination with partial pivoting in long double; a
+// singular system gives the zero guess.
+static void ssm_guess(const std::vector<std::vector<std::complex<double>>> &gram,
+                      const std::vector<std::complex<double>> &bx, double bn2, double m, const double *m0,
+                      const std::vector<int> &order, int j0, int kk, std::vector<std::complex<double>> &g_out)
+{
+    using C = std::complex<long double>;
+    std::vector<std::vector<C>> A(kk, std::vector<C>(kk + 1));
+    std::vector<long double> f(kk);
+    for (int i = 0; i < kk; ++i) {
+        const double mi = m0[order[j0 + i]];
+        f[i] = (long double)(m - mi) / (long double)(mi + 4.0);
+    }
+    for (int i = 0; i < kk; ++i) {
+        const C bxi = C(bx[j0 + i]);
+        for (int j = 0; j < kk; ++j)
+            A[i][j] = (long double)bn2 + f[j] * C(bx[j0 + j]) + f[i] * std::conj(bxi) +
+                      f[i] * f[j] * C(gram[j0 + i][j0 + j]);
+        A[i][kk] = (long double)bn2 + f[i] * std::conj(bxi);
+    }
+    for (int c = 0; c < kk; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < kk; ++r)
+            if (std::abs(A[r][c]) > std::abs(A[piv][c])) piv = r;
+        if (!(std::abs(A[piv][c]) > 0.0L)) {
+            for (auto &v : g_out) v = 0.0;
+            return;
+        }
+        std::swap(A[c], A[piv]);
+        for (int r = c + 1; r < kk; ++r) {
+            const C fct = A[r][c] / A[c][c];
+            for (int q = c; q <= kk; ++q) A[r][q] -= fct * A[c][q];
+        }
+    }
+    std::vector<C> c(kk);
+    for (int i = kk - 1; i >= 0; --i) {
+        C acc = A[i][kk];
+        for (int j = i + 1; j < kk; ++j) acc -= A[i][j] * c[j];
+        c[i] = acc / A[i][i];
+    }
+    for (int j = 0; j < kk; ++j) {
+        const double mj = m0[order[j0 + j]];
+        const C gj = c[j] * (long double)((m + 4.0) / (mj + 4.0));
+        g_out[j] = std::complex<double>((double)gj.real(), (double)gj.imag());
+    }
+}
+
 extern "C" int multimass_solve(wl_gauge *g, const void *const *b, void *const *x, int n_rhs, const double *m0,
                                int n_mass, const wl_solver_params *p, wl_solver_stats *stats, void *stream)
 {
@@ -665,6 +722,25 @@ extern "C" int multimass_solve(wl_gauge *g, const void *const *b, void *const *x
     Pinned pin;
     WL_TRY(pin.reserve(sizeof(double) * 128 * n_rhs));
     double *hc = static_cast<double *>(pin.p);
+    // solution-space minimisation: Gram matrix <x_i, x_j> and <b, x_j> per rhs
+    std::vector<std::vector<std::vector<std::complex<double>>>> gram;
+    std::vector<std::vector<std::complex<double>>> bx;
+    double *ssm_dots = nullptr, *ssm_partials = nullptr;
+    unsigned *ssm_tickets = nullptr;
+    if (p->guess == WL_GUESS_SSM) {
+        gram.assign(n_rhs, std::vector<std::vector<std::complex<double>>>(n_mass,
+                                                                          std::vector<std::complex<double>>(n_mass)));
+        bx.assign(n_rhs, std::vector<std::complex<double>>(n_mass));
+        void *pp;
+        const bool fresh = g->ws.bufs["ssm_tickets"].bytes < sizeof(unsigned) * n_rhs;
+        WL_TRY(g->ws.get("ssm_tickets", sizeof(unsigned) * n_rhs, &pp));
+        ssm_tickets = static_cast<unsigned *>(pp);
+        if (fresh) WL_CUDA_TRY(cudaMemsetAsync(pp, 0, sizeof(unsigned) * n_rhs, s));
+        WL_TRY(g->ws.get("ssm_partials", sizeof(double) * (2 * 16 * 1024 + 64), &pp));
+        ssm_partials = static_cast<double *>(pp);
+        WL_TRY(g->ws.get("ssm_dots", sizeof(double) * 2 * 16 * n_rhs, &pp));
+        ssm_dots = static_cast<double *>(pp);
+    }
     int worst = WL_OK;
     for (int k = 0; k < n_mass; ++k) {
         Timer tm;
@@ -676,46 +752,94 @@ extern "C" int multimass_solve(wl_gauge *g, const void *const *b, void *const *x
         Vec r0;
         WL_TRY(make_vec(g, "dc_r64", PO, n_rhs, &r0));
         const double k2 = 1.0 / ((2.0 * m + 8.0) * (2.0 * m + 8.0));
-        const int kk = (p->guess == WL_GUESS_ZERO) ? 0 : k;
-        // Lagrange extrapolation of psi = x / (m + 4) through all previous
-        // masses (Eq. Poly): x_guess = (m + 4) sum_j w_j x_j / (m_j + 4),
-        // w_j = prod_{i != j} (m - m_i) / (m_j - m_i).  By linearity the
-        // first residual b_prec - x_guess + kappa^2 sum_j c_j y_j, with
-        // y_j = D_eo D_oe x_j kept from mass j, needs no hop.
-        std::vector<double> cj(kk);
-        for (int j = 0; j < kk; ++j) {
-            const double mj = m0[order[j]];
-            double w = 1.0;
-            for (int i = 0; i < kk; ++i)
-                if (i != j) {
-                    const double mi = m0[order[i]];
-                    w *= (m - mi) / (mj - mi);
-                }
-            cj[j] = (m + 4.0) * w / (mj + 4.0);
-        }
+        // the guess uses the kk most recently solved masses j0 .. k-1 (all
+        // of them unless guess_max limits it)
+        int kk = (p->guess == WL_GUESS_ZERO) ? 0 : k;
+        if (p->guess_max > 0) kk = std::min(kk, p->guess_max);
+        const int j0 = k - kk;
+        const bool ssm = p->guess == WL_GUESS_SSM && kk > 0;
         const int ni = 2 * kk + 1;  // inputs of the residual combination
-        for (int r = 0; r < n_rhs; ++r) {
+        // x_guess = sum_j g_j x_j (g_j real for POLY, complex for SSM); by
+        // linearity the first residual b_prec - x_guess + kappa^2 sum_j g_j y_j,
+        // with y_j = D_eo D_oe x_j kept from mass j, needs no hop.
+        if (!ssm) {
+            // Lagrange extrapolation of psi = x / (m + 4) (Eq. Poly):
+            // g_j = (m + 4) w_j / (m_j + 4), w_j = prod_{i != j} (m - m_i) / (m_j - m_i)
+            std::vector<double> cj(kk);
             for (int j = 0; j < kk; ++j) {
-                hc[r * kk + j] = cj[j];                        // x_guess
-                hc[32 * n_rhs + r * ni + j] = -cj[j];          // - x_j
-                hc[32 * n_rhs + r * ni + kk + j] = k2 * cj[j]; // + kappa^2 y_j
+                const double mj = m0[order[j0 + j]];
+                double w = 1.0;
+                for (int i = 0; i < kk; ++i)
+                    if (i != j) {
+                        const double mi = m0[order[j0 + i]];
+                        w *= (m - mi) / (mj - mi);
+                    }
+                cj[j] = (m + 4.0) * w / (mj + 4.0);
             }
-            hc[32 * n_rhs + r * ni + 2 * kk] = 1.0;            // + b_prec
+            for (int r = 0; r < n_rhs; ++r) {
+                for (int j = 0; j < kk; ++j) {
+                    hc[r * kk + j] = cj[j];                        // x_guess
+                    hc[32 * n_rhs + r * ni + j] = -cj[j];          // - x_j
+                    hc[32 * n_rhs + r * ni + kk + j] = k2 * cj[j]; // + kappa^2 y_j
+                }
+                hc[32 * n_rhs + r * ni + 2 * kk] = 1.0;            // + b_prec
+            }
+            WL_CUDA_TRY(cudaMemcpyAsync(sc.coef, hc, sizeof(double) * 64 * n_rhs, cudaMemcpyHostToDevice, s));
+        } else {
+            for (int r = 0; r < n_rhs; ++r) {
+                std::vector<std::complex<double>> gj(kk);
+                ssm_guess(gram[r], bx[r], bn2[r], m, m0, order, j0, kk, gj);
+                for (int j = 0; j < kk; ++j) {
+                    const std::complex<double> a = gj[j], c = -gj[j], d = k2 * gj[j];
+                    hc[2 * (r * kk + j)] = a.real();
+                    hc[2 * (r * kk + j) + 1] = a.imag();
+                    hc[32 * n_rhs + 2 * (r * ni + j)] = c.real();
+                    hc[32 * n_rhs + 2 * (r * ni + j) + 1] = c.imag();
+                    hc[32 * n_rhs + 2 * (r * ni + kk + j)] = d.real();
+                    hc[32 * n_rhs + 2 * (r * ni + kk + j) + 1] = d.imag();
+                }
+                hc[32 * n_rhs + 2 * (r * ni + 2 * kk)] = 1.0;
+                hc[32 * n_rhs + 2 * (r * ni + 2 * kk) + 1] = 0.0;
+            }
+            WL_CUDA_TRY(cudaMemcpyAsync(sc.coef, hc, sizeof(double) * 96 * n_rhs, cudaMemcpyHostToDevice, s));
         }
-        WL_CUDA_TRY(cudaMemcpyAsync(sc.coef, hc, sizeof(double) * 64 * n_rhs, cudaMemcpyHostToDevice, s));
         if (kk == 0) WL_CUDA_TRY(cudaMemsetAsync(sol[k].ptr, 0, sol[k].rhs_bytes * n_rhs, s));
         {
             // x_guess and the first residual in one pass over the stored x_j, y_j
             std::vector<const Vec *> ins(ni);
             for (int j = 0; j < kk; ++j) {
-                ins[j] = &sol[j];
-                ins[kk + j] = &ys[j];
+                ins[j] = &sol[j0 + j];
+                ins[kk + j] = &ys[j0 + j];
             }
             ins[2 * kk] = &bprec;
-            WL_TRY(blas_lincomb2(geo, sc.coef, ins.data(), kk, &sol[k], sc.coef + 32 * n_rhs, ni, &r0, s));
+            WL_TRY(blas_lincomb2(geo, sc.coef, ins.data(), kk, &sol[k], sc.coef + 32 * n_rhs, ni, &r0, s, ssm));
         }
         for (int r = 0; r < n_rhs; ++r) std::memset(&st[r], 0, sizeof(wl_solver_stats));
         WL_TRY(solve_one_mass(g, be, bo, bprec, sol[k], m, *p, bn2, x + im, n_mass, st, s, &ys[k], true));
+        if (p->guess == WL_GUESS_SSM && k + 1 < n_mass) {
+            // Gram data of the new solution x_k for later masses:
+            // <b, x_k> and <x_j, x_k>, j <= k, on the canonical outputs
+            const int n = k + 2;
+            std::vector<const void *> a(n_rhs), in((size_t)n_rhs * n);
+            for (int r = 0; r < n_rhs; ++r) {
+                a[r] = x[(size_t)r * n_mass + im];
+                in[(size_t)r * n] = b[r];
+                for (int j = 0; j <= k; ++j) in[(size_t)r * n + 1 + j] = x[(size_t)r * n_mass + order[j]];
+            }
+            WL_TRY(canon_dots(a.data(), in.data(), n, n_rhs, (size_t)geo.Vh * 2 * 12, ssm_dots, ssm_partials,
+                              ssm_tickets, s));
+            std::vector<double> hd(2 * (size_t)n * n_rhs);
+            WL_CUDA_TRY(cudaMemcpyAsync(hd.data(), ssm_dots, sizeof(double) * hd.size(), cudaMemcpyDeviceToHost, s));
+            WL_CUDA_TRY(cudaStreamSynchronize(s));
+            for (int r = 0; r < n_rhs; ++r) {
+                const double *d = hd.data() + 2 * (size_t)n * r;
+                bx[r][k] = {d[0], d[1]};
+                for (int j = 0; j <= k; ++j) {
+                    gram[r][j][k] = {d[2 + 2 * j], d[3 + 2 * j]};
+                    gram[r][k][j] = std::conj(gram[r][j][k]);
+                }
+            }
+        }
         WL_CUDA_TRY(cudaStreamSynchronize(s));
         const double sec = tm.sec();
         for (int r = 0; r < n_rhs; ++r) {

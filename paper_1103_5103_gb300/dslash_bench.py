@@ -22,7 +22,7 @@ LINK_B = {"f64": 96, "df": 96, "f32": 48, "f16": 24}
 SPINOR_B = {"f64": 192, "df": 192, "f32": 96, "f16": 52}
 
 
-def run(dims, precs, nrhs=1, launches=50, eps=0.5, seed=2, rhs_block=1, variants=False):
+def run(dims, precs, nrhs=1, launches=50, eps=0.5, seed=2, rhs_block=1, variants=False, tune=False):
     lat = api.Lattice(dims)
     U = torch.from_numpy(synth.gauge_field(dims, eps, seed=seed)).cuda()
     g = api.Gauge(lat, U, precs=precs)
@@ -37,6 +37,8 @@ def run(dims, precs, nrhs=1, launches=50, eps=0.5, seed=2, rhs_block=1, variants
         b = torch.empty_like(a)
         for r in range(nrhs):
             lat.spinor_import(psi, a[r * stride:(r + 1) * stride], prec, 1)
+        if tune:
+            rhs_block = -api.autotune(g, prec, nrhs)[0]
         choices = [-v for v in api.HOP_VARIANTS[prec]] if variants else [rhs_block]
         for rb in choices:
             for _ in range(5):
@@ -65,11 +67,12 @@ def main():
     ap.add_argument("--rhs-block", type=int, default=1)
     ap.add_argument("--launches", type=int, default=50)
     ap.add_argument("--variants", action="store_true", help="time every autotuner variant")
+    ap.add_argument("--tune", action="store_true", help="time the variant the autotuner picks")
     args = ap.parse_args()
     for d in args.dims:
         dims = tuple(int(v) for v in d.split("x"))
         for row in run(dims, args.prec, args.nrhs, args.launches, rhs_block=args.rhs_block,
-                       variants=args.variants):
+                       variants=args.variants, tune=args.tune):
             print(json.dumps(row), flush=True)
 
 

@@ -379,6 +379,34 @@ def test_ssm_is_least_squares_and_dk_identity():
     assert np.allclose(c, c_ls, rtol=1e-8, atol=1e-10)
 
 
+def test_initial_guesses_window_and_ssm_optimality():
+    """Guesses from previous solutions: one previous solution extrapolates to
+    psi_1 itself; two give the straight line through them; and the SSM
+    guess has the smallest full residual of any combination in the span of
+    the same solutions, so it beats the Lagrange guess from that span."""
+    dims = (2, 2, 2, 4)
+    U = synth.gauge_field(dims, 0.5, seed=43)
+    b = synth.z2_source(dims, seed=44)
+    prev = [0.5, 0.4, 0.3]
+    psis = [O.bicgstab(O.OP_MK, U, dims, b, O.kappa(mk), tol=1e-13)[0] / (mk + 4) for mk in prev]
+    m = 0.2
+    g1 = O.initial_guess(b, psis, prev, m, "poly", guess_max=1)
+    assert _rel(g1, (m + 4) * psis[-1]) < 1e-15
+    g2 = O.initial_guess(b, psis, prev, m, "poly", guess_max=2)
+    line = psis[2] + (m - prev[2]) / (prev[1] - prev[2]) * (psis[1] - psis[2])
+    assert _rel(g2, (m + 4) * line) < 1e-13
+    res = lambda x: np.linalg.norm(b - O.apply(O.OP_MK, U, dims, x, O.kappa(m)))
+    for k in (1, 2, 3):
+        gs = O.initial_guess(b, psis, prev, m, "ssm", guess_max=k)
+        gp = O.initial_guess(b, psis, prev, m, "poly", guess_max=k)
+        assert res(gs) <= res(gp) * (1 + 1e-9), k
+        # optimality: no perturbation within the span lowers the residual
+        for pk in psis[-k:]:
+            for eps in (1e-3, -1e-3, 1e-3j):
+                assert res(gs) <= res(gs + eps * (m + 4) * pk) * (1 + 1e-12)
+    assert O.initial_guess(b, psis, prev, m, "zero") is None
+
+
 def test_multimass_scheme_converges():
     dims = (4, 2, 2, 4)
     U = synth.gauge_field(dims, 0.3, seed=51)

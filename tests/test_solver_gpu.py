@@ -250,3 +250,43 @@ def test_bicgstab_m_point_source_without_shadow_reports_breakdown(api):
     for i, m in enumerate(masses):
         assert stats[i]["restarts"] > 0 and stats[i]["true_relres"] <= 1e-10, stats[i]
         assert O.true_relres(U, dims, b, xs[i].cpu().numpy(), m) <= 1.02e-10
+
+
+@pytest.mark.parametrize("guess,guess_max", [("poly", 0), ("poly", 2), ("ssm", 0), ("ssm", 2)])
+def test_multimass_guess_iterations_match_oracle(api, guess, guess_max):
+    """FP64 inner and outer: with the same initial guess (Lagrange or
+    solution-space minimisation, from all or the last two solutions) the
+    library and the oracle need the same iterations per mass, and reach the
+    same solutions.  A wrong guess coefficient would show here."""
+    dims = (8, 8, 8, 8)
+    U, lat, g = _gauge(api, dims, 0.3, 31)
+    b = synth.z2_source(dims, 33)
+    masses = [0.40, 0.35, 0.30, 0.25, 0.20]
+    code = {"poly": api.GUESS_POLY, "ssm": api.GUESS_SSM}[guess]
+    xs, st = api.multimass_solve(g, [_cuda(b)], masses,
+                                 api.params(guess=code, guess_max=guess_max, inner_prec="f64", outer_prec="f64"))
+    ref, ost = O.multimass_solve(U, dims, b, masses, tol=1e-10, guess=guess, guess_max=guess_max)
+    for i, m in enumerate(masses):
+        assert st[0][i]["true_relres"] <= 1e-10, st[0][i]
+        assert rel(xs[0][i].cpu().numpy(), ref[i]) < 1e-8
+        assert abs(st[0][i]["iterations"] - ost[i]["iterations"]) <= 2, (m, st[0][i], ost[i])
+
+
+def test_multimass_ssm_batched_fp32_inner(api):
+    """SSM guess with several sources (complex coefficients per source) and
+    the FP32 inner solve: every mass converges, fewer iterations than the
+    zero guess."""
+    dims = (4, 4, 4, 8)
+    U, lat, g = _gauge(api, dims, 0.5, 21)
+    bs = [synth.point_source(dims, 0, 0), synth.z2_source(dims, 22), synth.gaussian_source(dims, 23)]
+    masses = [0.2, 0.4, 0.05, 0.3, 0.1]
+    its = {}
+    for guess in (api.GUESS_ZERO, api.GUESS_SSM):
+        xs, stats = api.multimass_solve(g, [_cuda(b) for b in bs], masses, api.params(guess=guess))
+        its[guess] = sum(stats[r][i]["iterations"] for r in range(3) for i in range(len(masses)))
+        for r, b in enumerate(bs):
+            for i, m in enumerate(masses):
+                assert stats[r][i]["status"] == 0 and stats[r][i]["true_relres"] <= 1e-10
+                ref, _ = O.eo_solve(U, dims, b, m, tol=1e-13)
+                assert rel(xs[r][i].cpu().numpy(), ref) < 1e-8
+    assert its[api.GUESS_SSM] < its[api.GUESS_ZERO], its
