@@ -476,6 +476,174 @@ void launch_k_hop_prefetch_f32(HopArgs a, const EpiStore &e, cudaStream_t s)
     k_hop_prefetch_f32<DAG, MINB><<<nsb * a.nrhs, 128, 0, s>>>(a, e);
 }
 
+// ------------------------------------------ asynchronous-copy FP32 variant
+// The link and the NB neighbour spinors of direction d+1 are copied into
+// shared memory with cp.async while direction d is computed from shared
+// memory (two stages).  Loads in flight hold no registers, so a thread
+// keeps a whole direction outstanding while it computes.  Each thread reads
+// back only the slots it filled itself, so its own cp.async.wait_group is
+// the only ordering needed (no block barrier).
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+template <int NB>
+struct AsyncHop {
+    static constexpr int F4 = 3 + 6 * NB;  // float4 per thread and stage: link, then NB spinors
+    static constexpr int smem_bytes = 2 * F4 * 128 * 16;
+};
+
+struct AsyncCtx {
+    int i, r0, nr;      // site, first rhs, rhs in this group
+    int nb[8];          // neighbour per direction d = 2 mu + (0 forward, 1 backward)
+    bool neg_f, neg_b;  // antiperiodic sign of the forward / backward t hop
+};
+
+template <int NB>
+__device__ __forceinline__ void async_issue(const HopArgs &a, const AsyncCtx &c, float4 *stage, int d, int buf)
+{
+    const int mu = d >> 1;
+    const bool fwd = (d & 1) == 0;
+    const int j = c.nb[d];
+    const float4 *lk = reinterpret_cast<const float4 *>(static_cast<const char *>(fwd ? a.links_out : a.links_in) +
+                                                        (size_t)mu * link_dir_bytes(WL_F32, a.g.stride));
+    float4 *st = stage + (size_t)buf * AsyncHop<NB>::F4 * 128 + threadIdx.x;
+    const int li = fwd ? c.i : j;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) cp_async16(st + k * 128, lk + (size_t)k * a.g.stride + li);
+#pragma unroll
+    for (int r = 0; r < NB; ++r) {
+        if (r >= c.nr) break;
+        const float4 *sp = reinterpret_cast<const float4 *>(static_cast<const char *>(a.in) +
+                                                            (size_t)(c.r0 + r) * a.rhs_bytes);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) cp_async16(st + (3 + 6 * r + k) * 128, sp + (size_t)k * a.g.stride + j);
+    }
+}
+
+template <int D, bool DAG, int NB>
+__device__ __forceinline__ void async_step(const HopArgs &a, const AsyncCtx &c, float4 *stage,
+                                           cx<float> (&acc)[NB][12])
+{
+    if constexpr (D < 7) {
+        async_issue<NB>(a, c, stage, D + 1, (D + 1) & 1);
+        cp_async_commit();
+        cp_async_wait<1>();
+    } else {
+        cp_async_wait<0>();
+    }
+    constexpr int MU = D >> 1;
+    constexpr bool FWD = (D & 1) == 0;
+    const float4 *st = stage + (size_t)(D & 1) * AsyncHop<NB>::F4 * 128 + threadIdx.x;
+    cx<float> u[9];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float4 t = st[k * 128];
+        u[2 * k] = {t.x, t.y};
+        u[2 * k + 1] = {t.z, t.w};
+    }
+    reconstruct_row2(u);
+#pragma unroll
+    for (int r = 0; r < NB; ++r) {
+        if (r >= c.nr) break;
+        cx<float> psi[12];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const float4 t = st[(3 + 6 * r + k) * 128];
+            psi[2 * k] = {t.x, t.y};
+            psi[2 * k + 1] = {t.z, t.w};
+        }
+        if constexpr (FWD)
+            transport<MU, DAG ? 1 : 0, false>(acc[r], psi, u, MU == 3 && c.neg_f);
+        else
+            transport<MU, DAG ? 0 : 1, true>(acc[r], psi, u, MU == 3 && c.neg_b);
+    }
+}
+
+// acc[r] += D in[r0 + r] at site i (active threads only), r < nr <= NB,
+// through the two-stage shared-memory pipeline; stage holds
+// AsyncHop<NB>::smem_bytes of dynamic shared memory.
+template <bool DAG, int NB>
+__device__ __forceinline__ void hop_accumulate_async(const HopArgs &a, int i, int r0, int nr, float4 *stage,
+                                                     cx<float> (&acc)[NB][12])
+{
+    const Geom &g = a.g;
+    AsyncCtx c;
+    c.i = i;
+    c.r0 = r0;
+    c.nr = nr;
+    const Coord q = site_coord(g, i, a.out_parity);
+    const int rowbase = i - (q.x >> 1);
+    const int sy = g.Xh, sz = g.Xh * g.Y, stt = g.Xh * g.Y * g.Z;
+    c.nb[0] = rowbase + ((q.x + 1 == g.X ? 0 : q.x + 1) >> 1);
+    c.nb[1] = rowbase + ((q.x == 0 ? g.X - 1 : q.x - 1) >> 1);
+    c.nb[2] = q.y + 1 == g.Y ? i - (g.Y - 1) * sy : i + sy;
+    c.nb[3] = q.y == 0 ? i + (g.Y - 1) * sy : i - sy;
+    c.nb[4] = q.z + 1 == g.Z ? i - (g.Z - 1) * sz : i + sz;
+    c.nb[5] = q.z == 0 ? i + (g.Z - 1) * sz : i - sz;
+    c.nb[6] = q.t + 1 == g.T ? i - (g.T - 1) * stt : i + stt;
+    c.nb[7] = q.t == 0 ? i + (g.T - 1) * stt : i - stt;
+    c.neg_f = g.antiperiodic && q.t + 1 == g.T;
+    c.neg_b = g.antiperiodic && q.t == 0;
+    async_issue<NB>(a, c, stage, 0, 0);
+    cp_async_commit();
+    async_step<0, DAG, NB>(a, c, stage, acc);
+    async_step<1, DAG, NB>(a, c, stage, acc);
+    async_step<2, DAG, NB>(a, c, stage, acc);
+    async_step<3, DAG, NB>(a, c, stage, acc);
+    async_step<4, DAG, NB>(a, c, stage, acc);
+    async_step<5, DAG, NB>(a, c, stage, acc);
+    async_step<6, DAG, NB>(a, c, stage, acc);
+    async_step<7, DAG, NB>(a, c, stage, acc);
+}
+
+template <bool DAG, int NB, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_hop_async(HopArgs a, EpiStore epi)
+{
+    extern __shared__ float4 stage[];  // [2][F4][128]
+    const int grp = blockIdx.x % a.ngroups;
+    const int sb = blockIdx.x / a.ngroups;
+    const int r0 = grp * NB;
+    const int nr = a.nrhs - r0 < NB ? a.nrhs - r0 : NB;
+    if (a.skip) {
+        bool all_done = true;
+        for (int r = r0; r < r0 + nr; ++r) all_done &= rhs_done(a, r);
+        if (all_done) return;   // uniform over the block
+    }
+    const int i = sb * blockDim.x + threadIdx.x;
+    const bool active = i < a.g.Vh;
+    cx<float> acc[NB][12];
+#pragma unroll
+    for (int r = 0; r < NB; ++r)
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc[r][k] = {0.f, 0.f};
+    if (active) hop_accumulate_async<DAG, NB>(a, i, r0, nr, stage, acc);
+    epi.template operator()<WL_F32, NB>(a, i, active, r0, acc);
+}
+
+template <bool DAG, int NB, int MINB>
+void launch_k_hop_async(HopArgs a, const EpiStore &e, cudaStream_t s)
+{
+    constexpr int smem = AsyncHop<NB>::smem_bytes;
+    static bool attr = false;  // the opt-in above 48 KB, once per instantiation
+    if (!attr) {
+        cudaFuncSetAttribute(k_hop_async<DAG, NB, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        attr = true;
+    }
+    a.ngroups = (a.nrhs + NB - 1) / NB;
+    const int nsb = (a.g.Vh + 127) / 128;
+    k_hop_async<DAG, NB, MINB><<<nsb * a.ngroups, 128, smem, s>>>(a, e);
+}
+
 template <int P, bool DAG, int MINB>
 __global__ void __launch_bounds__(128, MINB) k_hop_rolled(HopArgs a, EpiStore epi)
 {
@@ -518,7 +686,7 @@ __global__ void __launch_bounds__(128, MINB) k_hop(HopArgs a, EpiStore epi)
 }
 
 template <int P, bool DAG, int KIND>
-__global__ void __launch_bounds__(128) k_hop_reduce(HopArgs a, EpiReduce<KIND> e)
+__device__ __forceinline__ void hop_reduce_body(const HopArgs &a, const EpiReduce<KIND> &e)
 {
     using R = typename PrecTraits<P>::R;
     constexpr int NV = EpiReduce<KIND>::NV;
@@ -597,6 +765,12 @@ __global__ void __launch_bounds__(128) k_hop_reduce(HopArgs a, EpiReduce<KIND> e
             }
         }
     }
+}
+
+template <int P, bool DAG, int KIND>
+__global__ void __launch_bounds__(128) k_hop_reduce(HopArgs a, EpiReduce<KIND> e)
+{
+    hop_reduce_body<P, DAG, KIND>(a, e);
 }
 
 // ------------------------------------------------------------ launchers

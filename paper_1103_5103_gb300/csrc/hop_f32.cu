@@ -17,6 +17,10 @@ int hop_launch_prec<WL_F32>(int v, int dagger, const HopArgs &a, const EpiStore 
         }
     } else {
         switch (v) {
+        case 1104: launch_k_hop_async<false, 1, 4>(a, e, s); break;
+        case 1106: launch_k_hop_async<false, 1, 6>(a, e, s); break;
+        case 1202: launch_k_hop_async<false, 2, 2>(a, e, s); break;
+        case 1203: launch_k_hop_async<false, 2, 3>(a, e, s); break;
         case 301: launch_k_hop_prefetch_f32<false, 1>(a, e, s); break;
         case 304: launch_k_hop_prefetch_f32<false, 4>(a, e, s); break;
         case 305: launch_k_hop_prefetch_f32<false, 5>(a, e, s); break;
