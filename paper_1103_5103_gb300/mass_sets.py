@@ -1,0 +1,133 @@
+"""Mass sets placed relative to the critical mass, and the single-mass versus
+multi-shift comparison of the paper's Section 7 on synthetic fields.
+
+The paper measures on a quenched ensemble whose critical mass is
+am_c = -0.8173 and uses two mass sets (Table 2): a wide one and a narrow one
+close to m_c. Our synthetic fields have their own m_c, so the sets are
+placed at the paper's distances m - m_c from it:
+
+- `critical_mass` finds the rightmost eigenvalue mu_max of the hop D by
+  implicitly restarted Arnoldi (ARPACK), with the library's FP64 dslash as
+  the operator. M_p(m) = (m + 4) - D/2 has eigenvalues (m + 4) - mu/2, so
+  its real parts reach zero first at m_c = Re(mu_max)/2 - 4, and the
+  conditioning of a solve at m grows like 1/(m - m_c). For U = 1 with an
+  antiperiodic time direction, m_c = cos(pi/T) - 1.
+- `table2_sets` shifts the paper's two sets to a given m_c.
+- `main` solves both sets with the single-mass scheme (zero guess and
+  Lagrange guess) and with FP64 BiCGstab-M, and prints one JSON line per
+  solver with its iterations, seconds and speed-up (the quantities of
+  Table 3).
+
+python -m paper_1103_5103_gb300.mass_sets [--dims 16x16x16x32] [--eps 0.5] [--sources z2|point]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+import torch
+
+from . import api, synth
+
+PAPER_MC = -0.8173
+PAPER_WIDE = [-0.7908, -0.7721, -0.7511, -0.7320, -0.7105, -0.6193, -0.5108, -0.2687]
+PAPER_NARROW = [-0.7908, -0.7887, -0.7866, -0.7846, -0.7825, -0.7804, -0.7784, -0.7763]
+
+
+def rightmost_eigenvalue(matvec, n: int, v0: np.ndarray, tol: float = 1e-6) -> complex:
+    """The eigenvalue with the largest real part of an n x n complex operator
+    given by matvec (numpy complex128 vectors), by implicitly restarted
+    Arnoldi (ARPACK, which='LR', one wanted value in a 64-vector basis: the
+    right edge of a Wilson spectrum is dense, and a wide basis converges in
+    a few hundred products where a narrow one needs thousands)."""
+    from scipy.sparse.linalg import LinearOperator, eigs
+    A = LinearOperator((n, n), matvec=matvec, dtype=np.complex128)
+    w = eigs(A, k=1, which="LR", v0=v0, ncv=min(64, n - 2), tol=tol, maxiter=100000, return_eigenvectors=False)
+    return complex(w[np.argmax(w.real)])
+
+
+def critical_mass(g: api.Gauge, seed: int = 11, tol: float = 1e-6) -> float:
+    """m_c = Re(mu_max)/2 - 4, mu_max the rightmost eigenvalue of D (FP64
+    library dslash on the GPU, vectors staged through the host)."""
+    dims = g.lat.dims
+    V = g.lat.volume
+    din = torch.empty((V, 4, 3), dtype=torch.complex128, device="cuda")
+    dout = torch.empty_like(din)
+
+    def hop(x):
+        din.copy_(torch.from_numpy(np.ascontiguousarray(x).reshape(V, 4, 3)))
+        api.wilson_dslash(g, din, dout, 0.0, "f64", api.OP_HOP)
+        return dout.cpu().numpy().reshape(-1)
+
+    mu = rightmost_eigenvalue(hop, 12 * V, synth.gaussian_source(dims, seed=seed).reshape(-1), tol)
+    return mu.real / 2.0 - 4.0
+
+
+def table2_sets(m_c: float):
+    """The paper's wide and narrow sets at the same distances from m_c."""
+    wide = [m_c + (m - PAPER_MC) for m in PAPER_WIDE]
+    narrow = [m_c + (m - PAPER_MC) for m in PAPER_NARROW]
+    return wide, narrow
+
+
+def run(dims, eps, seed, kind, inner, repeat=2):
+    lat = api.Lattice(dims)
+    U = torch.from_numpy(synth.gauge_field(dims, eps, seed=seed)).cuda()
+    g = api.Gauge(lat, U)
+    t0 = time.perf_counter()
+    m_c = critical_mass(g)
+    t_mc = time.perf_counter() - t0
+    b = synth.point_source(dims) if kind == "point" else synth.z2_source(dims, seed=seed + 1)
+    bd = torch.from_numpy(b).cuda()
+    shadow = torch.from_numpy(synth.gaussian_source(dims, seed=seed + 2)).cuda() if kind == "point" else None
+    wide, narrow = table2_sets(m_c)
+    rows = []
+    for name, masses in (("wide", wide), ("narrow", narrow)):
+        res = {}
+        for label, prm in (("single-mass, zero guess", api.params(guess=api.GUESS_ZERO, inner_prec=inner)),
+                           ("single-mass, Lagrange guess", api.params(guess=api.GUESS_POLY, inner_prec=inner))):
+            for _ in range(repeat):
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                _, st = api.multimass_solve(g, [bd], masses, prm)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t
+            res[label] = {"iterations": sum(s["iterations"] for s in st[0]), "seconds": dt,
+                          "ms_per_iteration": 1e3 * dt / max(1, sum(s["iterations"] for s in st[0])),
+                          "max_true_relres": max(s["true_relres"] for s in st[0])}
+        xs = [torch.empty_like(bd) for _ in masses]
+        for _ in range(repeat):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            stm = api.bicgstab_m_solve(g, bd, xs, masses, api.params(shadow=shadow), check=False)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t
+        it_m = max(s["iterations"] for s in stm)
+        res["multi-shift (BiCGstab-M, FP64)"] = {
+            "iterations": it_m, "seconds": dt, "ms_per_iteration": 1e3 * dt / max(1, it_m),
+            "max_true_relres": max(s["true_relres"] for s in stm),
+            "masses_polished": sum(1 for s in stm if s["restarts"] > 0)}
+        for label, r in res.items():
+            r["speed_up_vs_multi_shift"] = res["multi-shift (BiCGstab-M, FP64)"]["seconds"] / r["seconds"]
+        row = {"dims": "x".join(map(str, dims)), "eps": eps, "source": kind, "inner": inner, "m_c": m_c,
+               "m_c_seconds": t_mc, "set": name, "masses": masses, "results": res}
+        rows.append(row)
+        print(json.dumps(row), flush=True)
+    return rows
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--dims", default="16x16x16x32")
+    ap.add_argument("--eps", type=float, default=0.5)
+    ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--sources", choices=["z2", "point"], default="z2")
+    ap.add_argument("--inner", choices=["f32", "f16", "f64"], default="f32")
+    args = ap.parse_args()
+    run(tuple(int(v) for v in args.dims.split("x")), args.eps, args.seed, args.sources, args.inner)
+
+
+if __name__ == "__main__":
+    main()

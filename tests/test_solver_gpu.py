@@ -290,3 +290,18 @@ def test_multimass_ssm_batched_fp32_inner(api):
                 ref, _ = O.eo_solve(U, dims, b, m, tol=1e-13)
                 assert rel(xs[r][i].cpu().numpy(), ref) < 1e-8
     assert its[api.GUESS_SSM] < its[api.GUESS_ZERO], its
+
+
+def test_critical_mass_estimate(api):
+    """m_c from the rightmost eigenvalue of the library's FP64 hop: the free
+    field's closed form cos(pi/T) - 1, and a random field's dense spectrum."""
+    pytest.importorskip("scipy")
+    from paper_1103_5103_gb300.mass_sets import critical_mass
+    dims = (4, 4, 4, 8)
+    lat = api.Lattice(dims)
+    g = api.Gauge(lat, _cuda(synth.unit_gauge_field(dims)), precs=("f64",))
+    assert abs(critical_mass(g, tol=1e-12) - (np.cos(np.pi / 8) - 1)) < 1e-8
+    U = synth.gauge_field(dims, 0.5, seed=5)
+    g = api.Gauge(lat, _cuda(U), precs=("f64",))
+    dense = np.linalg.eigvals(O.dense_operator(O.OP_HOP, U, dims))
+    assert abs(critical_mass(g, tol=1e-12) - (dense.real.max() / 2 - 4)) < 1e-8
