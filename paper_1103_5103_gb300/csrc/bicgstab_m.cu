@@ -388,8 +388,7 @@ extern "C" int bicgstab_m_solve(wl_gauge *g, const void *b, void *const *x, cons
     // import b; ||b||^2
     const void *bc[1] = {b};
     Vec be = half_of(bv, 0), bo = half_of(bv, 1);
-    WL_TRY(import_spinors(geo, bc, be, WL_EVEN, s));
-    WL_TRY(import_spinors(geo, bc, bo, WL_ODD, s));
+    WL_TRY(import_full(geo, bc, be, bo, s));
     WL_CUDA_TRY(cudaMemsetAsync(pn, 0, sizeof(double) * 8 + sizeof(unsigned) * 4, s));
     WL_TRY(blas_norm2(geo, be, d_norm, partials, d_ticket, s));
     WL_TRY(blas_norm2(geo, bo, d_norm + 1, partials, d_ticket + 1, s));
@@ -406,8 +405,7 @@ extern "C" int bicgstab_m_solve(wl_gauge *g, const void *b, void *const *x, cons
     if (p->shadow) {
         // given shadow residual: rho_0 = <rhat, b> must not vanish
         const void *sc[1] = {p->shadow};
-        WL_TRY(import_spinors(geo, sc, half_of(rhat, 0), WL_EVEN, s));
-        WL_TRY(import_spinors(geo, sc, half_of(rhat, 1), WL_ODD, s));
+        WL_TRY(import_full(geo, sc, half_of(rhat, 0), half_of(rhat, 1), s));
         void *pd;
         WL_TRY(g->ws.get("bm_dots_partials", sizeof(double) * 3 * 1024, &pd));
         d_dots = d_norm + 4;
@@ -555,8 +553,7 @@ extern "C" int bicgstab_m_solve(wl_gauge *g, const void *b, void *const *x, cons
             WL_TRY(blas_lincomb(geo, d_coef, d_coef + 1, ins, 1, out, s));
         }
         void *xo[1] = {x[i]};
-        WL_TRY(export_spinors(geo, half_of(scaled, 0), xo, WL_EVEN, s));
-        WL_TRY(export_spinors(geo, half_of(scaled, 1), xo, WL_ODD, s));
+        WL_TRY(export_full(geo, half_of(scaled, 0), half_of(scaled, 1), xo, s));
         std::vector<double> rel;
         WL_TRY(full_relres(g, be, bo, half_of(scaled, 0), half_of(scaled, 1), 1.0 / (2.0 * m0[i] + 8.0), {bnorm}, rel, s));
         stats[i].iterations = it;

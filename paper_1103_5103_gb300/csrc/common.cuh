@@ -207,7 +207,7 @@ __host__ __device__ constexpr int spinor_site_bytes(int prec)
 }
 __host__ __device__ constexpr int link_site_bytes(int prec)
 {
-    return prec == WL_F64 ? 96 : prec == WL_F32 ? 48 : prec == WL_DF ? 96 : 24;
+    return prec == WL_F64 ? 96 : prec == WL_F32 ? 48 : prec == WL_DF ? 144 : 24;
 }
 
 // Squared magnitude accumulated per site: FP32 for FP32 and double-float
@@ -393,8 +393,8 @@ template <> struct SpinorIO<WL_DF> {
 
 // Links: per parity, per direction, the first two rows (6 complex, k = 3*row + col):
 //   F64: double2 [4][6][stride];  F32: float4 [4][3][stride];  F16: uint2 [4][3][stride]
-//   DF:  float4 [4][6][stride] (re.hi, re.lo, im.hi, im.lo)
-// Row 2 is rebuilt as conj(row0 x row1).
+//   DF:  float4 [4][9][stride] (re.hi, re.lo, im.hi, im.lo), all three rows
+// Except for DF, row 2 is rebuilt as conj(row0 x row1).
 template <int P> struct LinkIO;
 
 template <typename R>
@@ -455,18 +455,22 @@ template <> struct LinkIO<WL_F16> {
     }
 };
 
+// Double-float links keep all three rows (18 reals): rebuilding row 2 in
+// double-float arithmetic costs about 14% of the double-float hop's
+// instructions, while the extra 48 B per link are free in a hop that is
+// bound by instruction issue, not by memory.  Row 2 is formed once in FP64
+// when the links are packed.
 template <> struct LinkIO<WL_DF> {
     using R = df;
-    static constexpr int chunks = 6;
+    static constexpr int chunks = 9;
     static __device__ __forceinline__ void load(const void *dirbase, int stride, int i, cx<R> (&u)[9])
     {
         const float4 *p = static_cast<const float4 *>(dirbase);
 #pragma unroll
-        for (int k = 0; k < 6; ++k) {
+        for (int k = 0; k < 9; ++k) {
             float4 t = __ldg(p + (size_t)k * stride + i);
             u[k] = {df(t.x, t.y), df(t.z, t.w)};
         }
-        reconstruct_row2(u);
     }
 };
 

@@ -182,8 +182,7 @@ static int dslash_common(wl_gauge *g, const void *in, void *out, double kappa, i
     WL_TRY(make_vec(g, "dslash_oo", prec, 1, &oo));
     const void *cin[1] = {in};
     void *cout[1] = {out};
-    WL_TRY(import_spinors(geo, cin, ie, WL_EVEN, s));
-    WL_TRY(import_spinors(geo, cin, io, WL_ODD, s));
+    WL_TRY(import_full(geo, cin, ie, io, s));
     if (op == WL_OP_HOP) {
         WL_TRY(hop(g, io, oe, nullptr, 1.0, WL_EVEN, dagger, 1, s));
         WL_TRY(hop(g, ie, oo, nullptr, 1.0, WL_ODD, dagger, 1, s));
@@ -197,8 +196,7 @@ static int dslash_common(wl_gauge *g, const void *in, void *out, double kappa, i
         WL_TRY(hop(g, oo, oe, &ie, -kappa * kappa, WL_EVEN, dagger, 1, s));
         WL_CUDA_TRY(cudaMemsetAsync(oo.ptr, 0, spinor_bytes(geo, prec), s));
     }
-    WL_TRY(export_spinors(geo, oe, cout, WL_EVEN, s));
-    WL_TRY(export_spinors(geo, oo, cout, WL_ODD, s));
+    WL_TRY(export_full(geo, oe, oo, cout, s));
     return WL_OK;
 }
 

@@ -92,6 +92,76 @@ __global__ void k_export(Geom g, const void *in, double2 *__restrict__ canon, in
     for (int k = 0; k < 12; ++k) canon[lex * 12 + k] = make_double2(to_double(v[k].re), to_double(v[k].im));
 }
 
+// Both parities at once, through shared memory, so that the canonical side
+// is read or written in whole lines: a block takes the 128 consecutive
+// lexicographic sites 128 b .. 128 b + 127, i.e. even-odd indices 64 b ..
+// 64 b + 63 of both parities (eo index = floor(lex / 2)).  The staging
+// buffer is component-major with a stride of 129 (no bank conflicts).
+constexpr int kFullSites = 128;
+
+__device__ __forceinline__ int lex_parity(const Geom &g, size_t n)
+{
+    const int x = (int)(n % g.X);
+    size_t r = n / g.X;
+    const int y = (int)(r % g.Y);
+    r /= g.Y;
+    const int z = (int)(r % g.Z);
+    const int t = (int)(r / g.Z);
+    return (x + y + z + t) & 1;
+}
+
+template <int P>
+__global__ void __launch_bounds__(kFullSites) k_export_full(Geom g, const void *even, const void *odd,
+                                                            double2 *__restrict__ canon)
+{
+    __shared__ double2 sm[12 * (kFullSites + 1)];
+    const size_t V = (size_t)g.Vh * 2;
+    const size_t n0 = (size_t)blockIdx.x * kFullSites;
+    const size_t n = n0 + threadIdx.x;
+    if (n < V) {
+        using R = typename PrecTraits<P>::R;
+        cx<R> v[12];
+        SpinorIO<P>::load(lex_parity(g, n) ? odd : even, g.stride, (int)(n >> 1), v);
+#pragma unroll
+        for (int k = 0; k < 12; ++k)
+            sm[k * (kFullSites + 1) + threadIdx.x] = make_double2(to_double(v[k].re), to_double(v[k].im));
+    }
+    __syncthreads();
+    const size_t e0 = n0 * 12, e_end = V * 12;
+#pragma unroll
+    for (int j = 0; j < 12; ++j) {
+        const int e = j * kFullSites + threadIdx.x;
+        if (e0 + e < e_end) canon[e0 + e] = sm[(e % 12) * (kFullSites + 1) + e / 12];
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(kFullSites) k_import_full(Geom g, const double2 *__restrict__ canon, void *even,
+                                                            void *odd)
+{
+    __shared__ double2 sm[12 * (kFullSites + 1)];
+    const size_t V = (size_t)g.Vh * 2;
+    const size_t n0 = (size_t)blockIdx.x * kFullSites;
+    const size_t e0 = n0 * 12, e_end = V * 12;
+#pragma unroll
+    for (int j = 0; j < 12; ++j) {
+        const int e = j * kFullSites + threadIdx.x;
+        if (e0 + e < e_end) sm[(e % 12) * (kFullSites + 1) + e / 12] = canon[e0 + e];
+    }
+    __syncthreads();
+    const size_t n = n0 + threadIdx.x;
+    if (n < V) {
+        using R = typename PrecTraits<P>::R;
+        cx<R> v[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            const double2 t = sm[k * (kFullSites + 1) + threadIdx.x];
+            v[k] = {Conv<R>::from(t.x), Conv<R>::from(t.y)};
+        }
+        SpinorIO<P>::store(lex_parity(g, n) ? odd : even, g.stride, (int)(n >> 1), v);
+    }
+}
+
 // Pack rows 0 and 1 of U_mu at the sites of one parity.
 template <int P>
 __global__ void k_pack_links(Geom g, const double2 *__restrict__ U, void *out, int parity)
@@ -114,9 +184,19 @@ __global__ void k_pack_links(Geom g, const double2 *__restrict__ U, void *out, i
             p[(size_t)k * g.stride + i] = make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
         }
     } else if (P == WL_DF) {
+        // rows 0, 1 as given; row 2 = conj(row 0 x row 1) in FP64, the same
+        // relation the other precisions rebuild on the fly
+        double2 w[9];
+        for (int k = 0; k < 6; ++k) w[k] = u[k];
+        for (int c = 0; c < 3; ++c) {
+            const double2 a1 = w[(c + 1) % 3], a2 = w[(c + 2) % 3], b1 = w[3 + (c + 1) % 3], b2 = w[3 + (c + 2) % 3];
+            const double re = (a1.x * b2.x - a1.y * b2.y) - (a2.x * b1.x - a2.y * b1.y);
+            const double im = (a1.x * b2.y + a1.y * b2.x) - (a2.x * b1.y + a2.y * b1.x);
+            w[6 + c] = make_double2(re, -im);
+        }
         float4 *p = reinterpret_cast<float4 *>(dir);
-        for (int k = 0; k < 6; ++k) {
-            const df re(u[k].x), im(u[k].y);
+        for (int k = 0; k < 9; ++k) {
+            const df re(w[k].x), im(w[k].y);
             p[(size_t)k * g.stride + i] = make_float4(re.hi, re.lo, im.hi, im.lo);
         }
     } else {
@@ -148,6 +228,48 @@ static int launch_export(const Geom &g, const void *in, void *canon, int parity,
     k_export<P><<<bl, th, 0, s>>>(g, in, static_cast<double2 *>(canon), parity);
     WL_CUDA_TRY(cudaGetLastError());
     note_launch(s);
+    return WL_OK;
+}
+
+template <int P>
+static int launch_full(const Geom &g, const void *canon_in, void *canon_out, const void *even_in, const void *odd_in,
+                       void *even_out, void *odd_out, cudaStream_t s)
+{
+    const unsigned bl = (unsigned)(((size_t)g.Vh * 2 + kFullSites - 1) / kFullSites);
+    if (canon_out)
+        k_export_full<P><<<bl, kFullSites, 0, s>>>(g, even_in, odd_in, static_cast<double2 *>(canon_out));
+    else
+        k_import_full<P><<<bl, kFullSites, 0, s>>>(g, static_cast<const double2 *>(canon_in), even_out, odd_out);
+    WL_CUDA_TRY(cudaGetLastError());
+    note_launch(s);
+    return WL_OK;
+}
+
+int export_full(const Geom &g, const Vec &even, const Vec &odd, void *const *canon, cudaStream_t s)
+{
+    if (even.prec != odd.prec || even.nrhs != odd.nrhs) { set_error("export_full: parity mismatch"); return WL_ERR_ARG; }
+    for (int r = 0; r < even.nrhs; ++r) {
+        const void *e = even.rhs(r), *o = odd.rhs(r);
+        int st = even.prec == WL_F64   ? launch_full<WL_F64>(g, nullptr, canon[r], e, o, nullptr, nullptr, s)
+                 : even.prec == WL_F32 ? launch_full<WL_F32>(g, nullptr, canon[r], e, o, nullptr, nullptr, s)
+                 : even.prec == WL_DF  ? launch_full<WL_DF>(g, nullptr, canon[r], e, o, nullptr, nullptr, s)
+                                       : launch_full<WL_F16>(g, nullptr, canon[r], e, o, nullptr, nullptr, s);
+        WL_TRY(st);
+    }
+    return WL_OK;
+}
+
+int import_full(const Geom &g, const void *const *canon, const Vec &even, const Vec &odd, cudaStream_t s)
+{
+    if (even.prec != odd.prec || even.nrhs != odd.nrhs) { set_error("import_full: parity mismatch"); return WL_ERR_ARG; }
+    for (int r = 0; r < even.nrhs; ++r) {
+        void *e = even.rhs(r), *o = odd.rhs(r);
+        int st = even.prec == WL_F64   ? launch_full<WL_F64>(g, canon[r], nullptr, nullptr, nullptr, e, o, s)
+                 : even.prec == WL_F32 ? launch_full<WL_F32>(g, canon[r], nullptr, nullptr, nullptr, e, o, s)
+                 : even.prec == WL_DF  ? launch_full<WL_DF>(g, canon[r], nullptr, nullptr, nullptr, e, o, s)
+                                       : launch_full<WL_F16>(g, canon[r], nullptr, nullptr, nullptr, e, o, s);
+        WL_TRY(st);
+    }
     return WL_OK;
 }
 

@@ -90,8 +90,7 @@ extern "C" int wilson_dslash_noalloc(wl_gauge *g, const void *in, void *out, dou
     void *cout[1] = {out};
     // every scratch buffer is fully written below before it is read, except
     // the odd output of M_prec, which is defined as zero
-    WL_TRY(import_spinors(geo, cin, ie, WL_EVEN, s));
-    WL_TRY(import_spinors(geo, cin, io, WL_ODD, s));
+    WL_TRY(import_full(geo, cin, ie, io, s));
     if (op == WL_OP_HOP) {
         WL_TRY(hop(g, io, oe, nullptr, 1.0, WL_EVEN, dag, 1, s));
         WL_TRY(hop(g, ie, oo, nullptr, 1.0, WL_ODD, dag, 1, s));
@@ -103,7 +102,6 @@ extern "C" int wilson_dslash_noalloc(wl_gauge *g, const void *in, void *out, dou
         WL_TRY(hop(g, oo, oe, &ie, -kappa * kappa, WL_EVEN, dag, 1, s));
         WL_CUDA_TRY(cudaMemsetAsync(oo.ptr, 0, spinor_bytes(geo, prec), s));
     }
-    WL_TRY(export_spinors(geo, oe, cout, WL_EVEN, s));
-    WL_TRY(export_spinors(geo, oo, cout, WL_ODD, s));
+    WL_TRY(export_full(geo, oe, oo, cout, s));
     return WL_OK;
 }

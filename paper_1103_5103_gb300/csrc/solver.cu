@@ -509,8 +509,7 @@ static int solve_one_mass(wl_gauge *g, const Vec &be, const Vec &bo, const Vec &
         stats[r].true_relres = rel[r];
         outs[r] = x_out[(size_t)r * x_out_stride];
     }
-    WL_TRY(export_spinors(geo, xe, outs.data(), WL_EVEN, s));
-    WL_TRY(export_spinors(geo, xo, outs.data(), WL_ODD, s));
+    WL_TRY(export_full(geo, xe, xo, outs.data(), s));
     return WL_OK;
 }
 
@@ -599,8 +598,7 @@ extern "C" int bicgstab_solve(wl_gauge *g, const void *b, void *x, double m0, co
     WL_TRY(make_vec(g, "mm_bprec", PO, 1, &bprec));
     const void *bc[1] = {b};
     const void *xc[1] = {x};
-    WL_TRY(import_spinors(geo, bc, be, WL_EVEN, s));
-    WL_TRY(import_spinors(geo, bc, bo, WL_ODD, s));
+    WL_TRY(import_full(geo, bc, be, bo, s));
     WL_TRY(import_spinors(geo, xc, xe, WL_EVEN, s));
     Scratch sc;
     WL_TRY(get_scratch(g, 1, &sc, s));
@@ -701,8 +699,7 @@ extern "C" int multimass_solve(wl_gauge *g, const void *const *b, void *const *x
     WL_TRY(make_vec(g, "b_o", PO, n_rhs, &bo));
     WL_TRY(make_vec(g, "mm_Dbo", PO, n_rhs, &dbo));
     WL_TRY(make_vec(g, "mm_bprec", PO, n_rhs, &bprec));
-    WL_TRY(import_spinors(geo, b, be, WL_EVEN, s));
-    WL_TRY(import_spinors(geo, b, bo, WL_ODD, s));
+    WL_TRY(import_full(geo, b, be, bo, s));
     // D_eo b_o once for all masses; b_prec(m) = b_e + kappa(m) D_eo b_o
     WL_TRY(hop(g, bo, dbo, nullptr, 1.0, WL_EVEN, 0, 1, s));
     Scratch sc;

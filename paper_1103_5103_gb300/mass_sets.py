@@ -7,8 +7,8 @@ close to m_c. Our synthetic fields have their own m_c, so the sets are
 placed at the paper's distances m - m_c from it:
 
 - `critical_mass` finds the rightmost eigenvalue mu_max of the hop D by
-  implicitly restarted Arnoldi (ARPACK), with the library's FP64 dslash as
-  the operator. M_p(m) = (m + 4) - D/2 has eigenvalues (m + 4) - mu/2, so
+  Krylov-Schur restarted Arnoldi, with the library's FP64 dslash as the
+  operator and the basis on the GPU. M_p(m) = (m + 4) - D/2 has eigenvalues (m + 4) - mu/2, so
   its real parts reach zero first at m_c = Re(mu_max)/2 - 4, and the
   conditioning of a solve at m grows like 1/(m - m_c). For U = 1 with an
   antiperiodic time direction, m_c = cos(pi/T) - 1.
@@ -36,33 +36,71 @@ PAPER_WIDE = [-0.7908, -0.7721, -0.7511, -0.7320, -0.7105, -0.6193, -0.5108, -0.
 PAPER_NARROW = [-0.7908, -0.7887, -0.7866, -0.7846, -0.7825, -0.7804, -0.7784, -0.7763]
 
 
-def rightmost_eigenvalue(matvec, n: int, v0: np.ndarray, tol: float = 1e-6) -> complex:
-    """The eigenvalue with the largest real part of an n x n complex operator
-    given by matvec (numpy complex128 vectors), by implicitly restarted
-    Arnoldi (ARPACK, which='LR', one wanted value in a 64-vector basis: the
-    right edge of a Wilson spectrum is dense, and a wide basis converges in
-    a few hundred products where a narrow one needs thousands)."""
-    from scipy.sparse.linalg import LinearOperator, eigs
-    A = LinearOperator((n, n), matvec=matvec, dtype=np.complex128)
-    w = eigs(A, k=1, which="LR", v0=v0, ncv=min(64, n - 2), tol=tol, maxiter=100000, return_eigenvectors=False)
-    return complex(w[np.argmax(w.real)])
+def rightmost_eigenvalue(matvec, v0: torch.Tensor, tol: float = 1e-6, m: int = 64, k: int = 24,
+                         max_restarts: int = 400):
+    """The eigenvalue with the largest real part of a complex linear operator,
+    by Krylov-Schur restarted Arnoldi (Stewart, SIAM J. Matrix Anal. Appl. 23,
+    2001): expand an orthonormal basis to m vectors (classical Gram-Schmidt,
+    applied twice), take the complex Schur form of the projected matrix,
+    keep the k Schur vectors whose Ritz values lie furthest right, and
+    continue from them.  matvec maps a 1-D complex128 tensor to one of the
+    same shape (on v0's device).  Returns (eigenvalue, converged, products):
+    converged when the residual of the rightmost Ritz pair is below
+    tol * |eigenvalue|; otherwise the best Ritz value after max_restarts."""
+    from scipy.linalg import schur
+    n = v0.numel()
+    m = min(m, n - 1)
+    k = min(k, m - 2)
+    V = torch.zeros((m + 1, n), dtype=torch.complex128, device=v0.device)
+    V[0] = v0.reshape(-1) / torch.linalg.vector_norm(v0)
+    H = np.zeros((m + 1, m), dtype=np.complex128)
+    p, products, best = 0, 0, None
+    for _ in range(max_restarts):
+        for j in range(p, m):
+            w = matvec(V[j])
+            products += 1
+            h = V[:j + 1].conj() @ w
+            w = w - h @ V[:j + 1]
+            h2 = V[:j + 1].conj() @ w
+            w = w - h2 @ V[:j + 1]
+            beta = float(torch.linalg.vector_norm(w))
+            H[:j + 1, j] = (h + h2).cpu().numpy()
+            H[j + 1, j] = beta
+            V[j + 1] = w / beta
+        ev = np.linalg.eigvals(H[:m, :m])
+        thr = np.sort(ev.real)[::-1][k - 1]
+        T, Z, kk = schur(H[:m, :m], output="complex", sort=lambda x: x.real >= thr)
+        b = H[m, m - 1] * Z[m - 1, :kk]
+        theta, Y = np.linalg.eig(T[:kk, :kk])
+        i = int(np.argmax(theta.real))
+        best = complex(theta[i])
+        if abs(b @ Y[:, i]) / np.linalg.norm(Y[:, i]) <= tol * abs(best):
+            return best, True, products
+        # truncate to the kk wanted Schur vectors: A V_k = V_k T_k + v_{k+1} b^T
+        V[:kk] = torch.from_numpy(np.ascontiguousarray(Z[:, :kk].T)).to(V.device) @ V[:m]
+        V[kk] = V[m]
+        H[:] = 0
+        H[:kk, :kk] = T[:kk, :kk]
+        H[kk, :kk] = b
+        p = kk
+    return best, False, products
 
 
-def critical_mass(g: api.Gauge, seed: int = 11, tol: float = 1e-6) -> float:
-    """m_c = Re(mu_max)/2 - 4, mu_max the rightmost eigenvalue of D (FP64
-    library dslash on the GPU, vectors staged through the host)."""
+def critical_mass(g: api.Gauge, seed: int = 11, tol: float = 1e-6, max_restarts: int = 400):
+    """(m_c, converged, products): m_c = Re(mu_max)/2 - 4, mu_max the
+    rightmost eigenvalue of D, with the library's FP64 dslash as the
+    operator and the Krylov basis kept on the GPU."""
     dims = g.lat.dims
     V = g.lat.volume
-    din = torch.empty((V, 4, 3), dtype=torch.complex128, device="cuda")
-    dout = torch.empty_like(din)
+    out = torch.empty((V, 4, 3), dtype=torch.complex128, device="cuda")
 
     def hop(x):
-        din.copy_(torch.from_numpy(np.ascontiguousarray(x).reshape(V, 4, 3)))
-        api.wilson_dslash(g, din, dout, 0.0, "f64", api.OP_HOP)
-        return dout.cpu().numpy().reshape(-1)
+        api.wilson_dslash(g, x.reshape(V, 4, 3), out, 0.0, "f64", api.OP_HOP)
+        return out.reshape(-1).clone()
 
-    mu = rightmost_eigenvalue(hop, 12 * V, synth.gaussian_source(dims, seed=seed).reshape(-1), tol)
-    return mu.real / 2.0 - 4.0
+    v0 = torch.from_numpy(synth.gaussian_source(dims, seed=seed)).cuda().reshape(-1)
+    mu, ok, nprod = rightmost_eigenvalue(hop, v0, tol, max_restarts=max_restarts)
+    return mu.real / 2.0 - 4.0, ok, nprod
 
 
 def table2_sets(m_c: float):
@@ -77,7 +115,7 @@ def run(dims, eps, seed, kind, inner, repeat=2):
     U = torch.from_numpy(synth.gauge_field(dims, eps, seed=seed)).cuda()
     g = api.Gauge(lat, U)
     t0 = time.perf_counter()
-    m_c = critical_mass(g)
+    m_c, mc_converged, mc_products = critical_mass(g, tol=1e-6)
     t_mc = time.perf_counter() - t0
     b = synth.point_source(dims) if kind == "point" else synth.z2_source(dims, seed=seed + 1)
     bd = torch.from_numpy(b).cuda()
@@ -112,7 +150,7 @@ def run(dims, eps, seed, kind, inner, repeat=2):
         for label, r in res.items():
             r["speed_up_vs_multi_shift"] = res["multi-shift (BiCGstab-M, FP64)"]["seconds"] / r["seconds"]
         row = {"dims": "x".join(map(str, dims)), "eps": eps, "source": kind, "inner": inner, "m_c": m_c,
-               "m_c_seconds": t_mc, "set": name, "masses": masses, "results": res}
+               "m_c_converged": mc_converged, "m_c_products": mc_products, "m_c_seconds": t_mc, "set": name, "masses": masses, "results": res}
         rows.append(row)
         print(json.dumps(row), flush=True)
     return rows

@@ -503,16 +503,18 @@ def test_sampled_residual_helper_matches_full_residual():
 
 
 def test_rightmost_eigenvalue_of_the_hop():
-    """The critical-mass estimate's eigensolver (ARPACK, largest real part)
-    on the oracle's hop: equal to the dense spectrum's rightmost eigenvalue,
-    and for U = 1 to the free-field edge 2 (3 + cos(pi/T))."""
+    """The critical-mass estimate's eigensolver (Krylov-Schur, largest real
+    part) on the oracle's hop: equal to the dense spectrum's rightmost
+    eigenvalue, and for U = 1 to the free-field edge 2 (3 + cos(pi/T))."""
     pytest.importorskip("scipy")
+    import torch
     from paper_1103_5103_gb300.mass_sets import rightmost_eigenvalue
     for dims, U in (((4, 4, 4, 4), synth.gauge_field((4, 4, 4, 4), 0.5, seed=5)),
                     ((4, 4, 2, 6), synth.unit_gauge_field((4, 4, 2, 6)))):
-        mv = lambda x: O.hop(U, dims, x.reshape(-1, 4, 3)).reshape(-1)
-        mu = rightmost_eigenvalue(mv, 12 * synth.volume(dims), synth.gaussian_source(dims, seed=11).reshape(-1),
-                                  tol=1e-12)
+        mv = lambda x: torch.from_numpy(O.hop(U, dims, x.numpy().reshape(-1, 4, 3)).reshape(-1))
+        mu, ok, _ = rightmost_eigenvalue(mv, torch.from_numpy(synth.gaussian_source(dims, seed=11).reshape(-1)),
+                                         tol=1e-12)
+        assert ok
         dense = np.linalg.eigvals(O.dense_operator(O.OP_HOP, U, dims))
         assert abs(mu.real - dense.real.max()) < 1e-8
     assert abs(mu.real - 2 * (3 + np.cos(np.pi / 6))) < 1e-8

@@ -300,8 +300,10 @@ def test_critical_mass_estimate(api):
     dims = (4, 4, 4, 8)
     lat = api.Lattice(dims)
     g = api.Gauge(lat, _cuda(synth.unit_gauge_field(dims)), precs=("f64",))
-    assert abs(critical_mass(g, tol=1e-12) - (np.cos(np.pi / 8) - 1)) < 1e-8
+    mc, ok, _ = critical_mass(g, tol=1e-12)
+    assert ok and abs(mc - (np.cos(np.pi / 8) - 1)) < 1e-8
     U = synth.gauge_field(dims, 0.5, seed=5)
     g = api.Gauge(lat, _cuda(U), precs=("f64",))
     dense = np.linalg.eigvals(O.dense_operator(O.OP_HOP, U, dims))
-    assert abs(critical_mass(g, tol=1e-12) - (dense.real.max() / 2 - 4)) < 1e-8
+    mc, ok, _ = critical_mass(g, tol=1e-12)
+    assert ok and abs(mc - (dense.real.max() / 2 - 4)) < 1e-8
