@@ -329,8 +329,8 @@ def launch_count() -> int:
     return n.value
 
 
-HOP_VARIANTS = {"f32": [101, 106, 108, 201, 205, 401, 404, 301, 304, 305, 1104, 1106, 1202, 1203], "f16": [101, 108, 110, 201, 206, 401, 404],
-                "f64": [101, 103, 201], "df": [101, 105, 106]}
+HOP_VARIANTS = {"f32": [101, 105, 106, 108, 201, 204, 205, 401, 404, 301, 304, 305, 1104, 1106, 1202, 1203], "f16": [101, 105, 106, 108, 110, 201, 204, 206, 401, 404],
+                "f64": [101, 103, 201], "df": [101, 103, 104, 105, 106]}
 
 
 def autotune(g: Gauge, prec, nrhs: int, stream=None):

@@ -13,6 +13,8 @@ int hop_launch_prec<WL_DF>(int v, int dagger, const HopArgs &a, const EpiStore &
     } else {
         switch (v) {
         case 101: launch_k_hop_rolled<WL_DF, false, 1>(a, e, s); break;
+        case 103: launch_k_hop_rolled<WL_DF, false, 3>(a, e, s); break;
+        case 104: launch_k_hop_rolled<WL_DF, false, 4>(a, e, s); break;
         case 105: launch_k_hop_rolled<WL_DF, false, 5>(a, e, s); break;
         case 106: launch_k_hop_rolled<WL_DF, false, 6>(a, e, s); break;
         default: launch_k_hop_rolled<WL_DF, false, 1>(a, e, s); break;

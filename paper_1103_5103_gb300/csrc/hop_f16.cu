@@ -18,9 +18,12 @@ int hop_launch_prec<WL_F16>(int v, int dagger, const HopArgs &a, const EpiStore 
     } else {
         switch (v) {
         case 101: launch_k_hop<WL_F16, false, 1, 1>(a, e, s); break;
+        case 105: launch_k_hop<WL_F16, false, 1, 5>(a, e, s); break;
+        case 106: launch_k_hop<WL_F16, false, 1, 6>(a, e, s); break;
         case 108: launch_k_hop<WL_F16, false, 1, 8>(a, e, s); break;
         case 110: launch_k_hop<WL_F16, false, 1, 10>(a, e, s); break;
         case 201: launch_k_hop<WL_F16, false, 2, 1>(a, e, s); break;
+        case 204: launch_k_hop<WL_F16, false, 2, 4>(a, e, s); break;
         case 206: launch_k_hop<WL_F16, false, 2, 6>(a, e, s); break;
         case 401: launch_k_hop<WL_F16, false, 4, 1>(a, e, s); break;
         case 404: launch_k_hop<WL_F16, false, 4, 4>(a, e, s); break;

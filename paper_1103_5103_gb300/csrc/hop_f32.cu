@@ -25,9 +25,11 @@ int hop_launch_prec<WL_F32>(int v, int dagger, const HopArgs &a, const EpiStore 
         case 304: launch_k_hop_prefetch_f32<false, 4>(a, e, s); break;
         case 305: launch_k_hop_prefetch_f32<false, 5>(a, e, s); break;
         case 101: launch_k_hop<WL_F32, false, 1, 1>(a, e, s); break;
+        case 105: launch_k_hop<WL_F32, false, 1, 5>(a, e, s); break;
         case 106: launch_k_hop<WL_F32, false, 1, 6>(a, e, s); break;
         case 108: launch_k_hop<WL_F32, false, 1, 8>(a, e, s); break;
         case 201: launch_k_hop<WL_F32, false, 2, 1>(a, e, s); break;
+        case 204: launch_k_hop<WL_F32, false, 2, 4>(a, e, s); break;
         case 205: launch_k_hop<WL_F32, false, 2, 5>(a, e, s); break;
         case 401: launch_k_hop<WL_F32, false, 4, 1>(a, e, s); break;
         case 404: launch_k_hop<WL_F32, false, 4, 4>(a, e, s); break;

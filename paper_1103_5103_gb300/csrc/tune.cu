@@ -18,10 +18,10 @@ namespace wl {
 
 const std::vector<int> &hop_variants(int prec)
 {
-    static const std::vector<int> f32 = {101, 106, 108, 201, 205, 401, 404, 301, 304, 305, 1104, 1106, 1202, 1203};
-    static const std::vector<int> f16 = {101, 108, 110, 201, 206, 401, 404};
+    static const std::vector<int> f32 = {101, 105, 106, 108, 201, 204, 205, 401, 404, 301, 304, 305, 1104, 1106, 1202, 1203};
+    static const std::vector<int> f16 = {101, 105, 106, 108, 110, 201, 204, 206, 401, 404};
     static const std::vector<int> f64 = {101, 103, 201};
-    static const std::vector<int> dfv = {101, 105, 106};
+    static const std::vector<int> dfv = {101, 103, 104, 105, 106};
     static const std::vector<int> none;
     switch (prec) {
     case WL_F32: return f32;
