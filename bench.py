@@ -59,7 +59,8 @@ SPINOR_B = {"f64": 192, "df": 192, "f32": 96, "f16": 52}
 # lattice sites of the captured case, bytes).  Traffic scales with sites.
 # An entry is valid only for the kernel as it was when captured; remove it
 # when that kernel changes.
-HOP_TRAFFIC = {("f32", 205, 12): (442368, 1244.7e6), ("f16", 101, 2): (1048576, 404.7e6)}
+HOP_TRAFFIC = {("f32", 205, 12): (442368, 1244.7e6), ("f16", 101, 2): (1048576, 404.7e6),
+               ("f16", 106, 2): (1048576, 404.0e6)}
 # The reference arm cannot afford a full oracle solve; it times a sample of
 # oracle BiCGstab iterations and scales by this many inner iterations per
 # step (the paper scheme's FP32-inner count on the c3 workload, from the
