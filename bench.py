@@ -267,7 +267,7 @@ def run_ours(args, cfg):
     # solution buffers for one batch of sources, reused by every batch
     xs = [[torch.empty((V, 4, 3), dtype=torch.complex128, device=dev) for _ in masses] for _ in range(nb)]
     prm = api.params(inner_prec=inner, rhs_block=args.rhs_block, outer_prec=args.outer,
-                     inner_tol=args.inner_tol,
+                     inner_tol=args.inner_tol, reliable=int(args.reliable),
                      mode={"graph": api.MODE_GRAPH, "persistent": api.MODE_PERSISTENT, "host": api.MODE_HOST}[args.mode])
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
@@ -375,6 +375,7 @@ def run_ours(args, cfg):
         "config": {"workload": cfg["name"], "sources": nr, "source_batch": nb, "masses": masses,
                    "inner_prec": inner, "outer_prec": args.outer,
                    "inner_tol": args.inner_tol or "library default", "mode": args.mode,
+                   "outer_loop": "reliable updates" if args.reliable else "restarted defect correction",
                    "tol": 1e-10, "l2": "flushed (256 MB write) before every step; working set > L2",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "e2e": {"value": t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
@@ -454,6 +455,8 @@ def main():
     ap.add_argument("--rhs-block", type=int, default=0)
     ap.add_argument("--inner-tol", type=float, default=0.0)
     ap.add_argument("--mode", choices=["graph", "persistent", "host"], default="graph")
+    ap.add_argument("--reliable", action="store_true",
+                    help="reliable updates instead of restarted defect correction in the mixed-precision loop")
     ap.add_argument("--baseline-sources", type=int, default=0,
                     help="sources for the BiCGstab-M comparison (default: the workload's, else all)")
     ap.add_argument("--source-batch", type=int, default=0,

@@ -114,6 +114,14 @@ typedef struct {
                             vanish (WL_ERR_ARG).                                      */
     int    guess_max;    /* multimass_solve: previous masses the guess uses, the most
                             recently solved (nearest) ones; 0 = all of them         */
+    int    reliable;     /* mixed-precision outer loop: 0 = restarted defect
+                            correction (Section 6.2.4: each outer step restarts the
+                            inner BiCGstab on the FP64-class residual); 1 = reliable
+                            updates (the method the paper cites there): the inner
+                            BiCGstab keeps its shadow residual and search direction,
+                            and only r is replaced by the true residual and the
+                            correction folded into x when the inner residual has
+                            dropped by inner_tol                                      */
 } wl_solver_params;
 
 typedef struct {
@@ -130,7 +138,7 @@ typedef struct {
  * inner_tol 0 (1e-6 for FP32, 3e-4 for FP16, 1e-12 for FP64; never below
  * what the outer target needs), max_restarts 100,
  * WL_GUESS_POLY, WL_MODE_GRAPH, rhs_block 0, graph_iters 8, eo 1,
- * outer_prec WL_DF, shadow NULL, guess_max 0. */
+ * outer_prec WL_DF, shadow NULL, guess_max 0, reliable 0. */
 int wl_params_default(wl_solver_params *p);
 
 /* Thread-local message describing the last failing call on this thread. */

@@ -50,7 +50,7 @@ class SolverParams(ctypes.Structure):
     _fields_ = [("tol", _dbl), ("max_iter", _int), ("inner_prec", _int), ("inner_tol", _dbl),
                 ("max_restarts", _int), ("guess", _int), ("mode", _int), ("rhs_block", _int),
                 ("graph_iters", _int), ("eo", _int), ("outer_prec", _int), ("shadow", _vp),
-                ("guess_max", _int)]
+                ("guess_max", _int), ("reliable", _int)]
 
 
 class SolverStats(ctypes.Structure):

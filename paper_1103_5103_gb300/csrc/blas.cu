@@ -204,8 +204,15 @@ int blas_p_update(const Geom &g, const Vec &r, const Vec &p, const Vec &v, BiSta
 }
 
 // ------------------------------------------------------------ (re)start
-// r = convert(r_outer); rhat = r; p = r; x = 0; rho = ||r||^2; target2 = delta2 * rho.
-// rhs with active[r] == 0 are marked done and left untouched.
+// Per rhs, by active[r]:
+//   0: marked done, left untouched;
+//   1: restart: r = convert(r_outer); rhat = r; p = r; x = 0; rho = ||r||^2;
+//   2: reliable update: r = convert(r_outer), the true residual of the
+//      current outer solution; x = 0; rhat and p are kept, rho = <rhat, r>,
+//      and beta = (rho / rho_old)(alpha / omega) of the interrupted
+//      iteration is set so that the p update that follows continues the
+//      same Krylov recurrence (Sleijpen & van der Vorst's reliable updating).
+// In both cases target2 = delta2 * ||r||^2.
 
 template <int PO, int P, int PX>
 __global__ void __launch_bounds__(kBlock) k_restart(Geom g, Vec r64, Vec r, Vec rhat, Vec p, Vec x, BiState *state,
@@ -213,11 +220,12 @@ __global__ void __launch_bounds__(kBlock) k_restart(Geom g, Vec r64, Vec r, Vec 
 {
     const SiteIdx q = site_idx(r.nrhs);
     BiState &S = state[q.r];
-    if (!active[q.r]) {
+    const int mode = active[q.r];
+    if (!mode) {
         if (q.sb == 0 && threadIdx.x == 0) S.done = 1;
         return;
     }
-    double red[1] = {0.0};
+    double red[3] = {0.0, 0.0, 0.0};
     if (q.i < g.Vh) {
         using R = RT<P>;
         cx<RT<PO>> a[12];
@@ -227,29 +235,66 @@ __global__ void __launch_bounds__(kBlock) k_restart(Geom g, Vec r64, Vec r, Vec 
         for (int k = 0; k < 12; ++k) v[k] = cconv<R>(a[k]);
         SpinorIO<P>::roundtrip(v);
         st<P>(r, q.r, g.stride, q.i, v);
-        st<P>(rhat, q.r, g.stride, q.i, v);
-        st<P>(p, q.r, g.stride, q.i, v);
+        cx<R> h[12];
+        if (mode == 1) {
+            st<P>(rhat, q.r, g.stride, q.i, v);
+            st<P>(p, q.r, g.stride, q.i, v);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) h[k] = v[k];
+        } else {
+            ld<P>(rhat, q.r, g.stride, q.i, h);
+        }
         cx<RT<PX>> z[12];
 #pragma unroll
         for (int k = 0; k < 12; ++k) z[k] = {RT<PX>(0), RT<PX>(0)};
         SpinorIO<PX>::store(x.rhs(q.r), g.stride, q.i, z);
+        cx<R> d = {R(0), R(0)};
         R n = R(0);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) n = fma(v[k].re, v[k].re, fma(v[k].im, v[k].im, n));
-        red[0] = (double)n;
+        for (int k = 0; k < 12; ++k) {
+            d = conjmad(h[k], v[k], d);
+            n = fma(v[k].re, v[k].re, fma(v[k].im, v[k].im, n));
+        }
+        red[0] = (double)d.re;
+        red[1] = (double)d.im;
+        red[2] = (double)n;
     }
-    double tot[1];
-    if (grid_sum<1>(red, partials + (size_t)q.r * q.nsb * kRedNV, &S.ticket[3], q.sb, q.nsb, tot) &&
+    double tot[3];
+    if (grid_sum<3>(red, partials + (size_t)q.r * q.nsb * kRedNV, &S.ticket[3], q.sb, q.nsb, tot) &&
         threadIdx.x == 0) {
-        S.rho_re = tot[0];
-        S.rho_im = 0.0;
-        S.rr = tot[0];
-        S.target2 = delta2[q.r] * tot[0];
-        S.alpha_re = S.omega_re = S.beta_re = 0.0;
-        S.alpha_im = S.omega_im = S.beta_im = 0.0;
+        const double rr = tot[2];
+        double bre = 0.0, bim = 0.0, ore = 0.0, oim = 0.0;
+        if (mode == 2) {
+            // beta = (rho_new / rho_old) (alpha / omega); without a usable
+            // previous iteration the direction restarts from r (beta = 0)
+            const double rho2 = S.rho_re * S.rho_re + S.rho_im * S.rho_im;
+            const double om2 = S.omega_re * S.omega_re + S.omega_im * S.omega_im;
+            if (rho2 > 0.0 && om2 > 0.0) {
+                const double qre = (tot[0] * S.rho_re + tot[1] * S.rho_im) / rho2;
+                const double qim = (tot[1] * S.rho_re - tot[0] * S.rho_im) / rho2;
+                const double wre = (S.alpha_re * S.omega_re + S.alpha_im * S.omega_im) / om2;
+                const double wim = (S.alpha_im * S.omega_re - S.alpha_re * S.omega_im) / om2;
+                bre = qre * wre - qim * wim;
+                bim = qre * wim + qim * wre;
+                ore = S.omega_re;
+                oim = S.omega_im;
+            }
+            S.rho_re = tot[0];
+            S.rho_im = tot[1];
+        } else {
+            S.rho_re = rr;
+            S.rho_im = 0.0;
+        }
+        S.rr = rr;
+        S.target2 = delta2[q.r] * rr;
+        S.alpha_re = S.alpha_im = 0.0;
+        S.beta_re = bre;
+        S.beta_im = bim;
+        S.omega_re = ore;
+        S.omega_im = oim;
         S.iters = 0;
         S.breakdown = 0;
-        S.done = (tot[0] > 0.0 && isfinite(tot[0])) ? 0 : 1;
+        S.done = (rr > 0.0 && isfinite(rr)) ? 0 : 1;
     }
 }
 

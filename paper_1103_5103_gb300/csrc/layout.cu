@@ -328,6 +328,7 @@ extern "C" int wl_params_default(wl_solver_params *p)
     p->outer_prec = WL_DF;
     p->shadow = nullptr;
     p->guess_max = 0;
+    p->reliable = 0;
     return WL_OK;
 }
 

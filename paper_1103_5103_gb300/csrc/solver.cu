@@ -350,6 +350,8 @@ static int eo_defect_correction(wl_gauge *g, const Vec &bprec, const Vec &x64, d
     int *h_outer = h_active + nrhs;
     const double delta0 = prm.inner_tol > 0 ? prm.inner_tol : default_inner_tol(prec);
     std::vector<int> outer_done(nrhs, 0), iters(nrhs, 0), restarts(nrhs, 0), fails(nrhs, 0);
+    // reliable updates: an inner run that converged can be continued (mode 2)
+    std::vector<int> can_continue(nrhs, 0);
     std::vector<double> last_rn(nrhs, INFINITY);
     std::vector<BiState> hst;
     const double k2 = kappa * kappa;
@@ -399,7 +401,7 @@ static int eo_defect_correction(wl_gauge *g, const Vec &bprec, const Vec &x64, d
             const double need = 0.5 * prm.tol * bnorm[r] / rn;
             const double d = std::max(delta0, need);
             h_delta2[r] = d * d;
-            h_active[r] = 1;
+            h_active[r] = (prm.reliable && can_continue[r]) ? 2 : 1;
             fails[r] = rn >= 0.5 * last_rn[r] ? fails[r] + 1 : 0;  // stagnation guard
             last_rn[r] = rn;
             ++n_active;
@@ -416,6 +418,11 @@ static int eo_defect_correction(wl_gauge *g, const Vec &bprec, const Vec &x64, d
         WL_CUDA_TRY(cudaMemcpyAsync(in.sc.delta2, h_delta2, sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
         WL_TRY(blas_restart(geo, r64, in.r, in.rhat, in.p, in.e, in.sc.state, in.sc.partials, in.sc.active,
                             in.sc.delta2, s));
+        bool any_continue = false;
+        for (int r = 0; r < nrhs; ++r) any_continue |= h_active[r] == 2;
+        // continued rhs: p = r + beta (p - omega v) with the beta the update set
+        // (restarted rhs have beta = omega = 0, so p = r stays)
+        if (any_continue) WL_TRY(blas_p_update(geo, in.r, in.p, in.v, in.sc.state, s));
         int cap = 0;
         for (int r = 0; r < nrhs; ++r)
             if (h_active[r]) cap = std::max(cap, prm.max_iter - iters[r]);
@@ -425,6 +432,7 @@ static int eo_defect_correction(wl_gauge *g, const Vec &bprec, const Vec &x64, d
             if (h_active[r]) {
                 iters[r] += hst[r].iters;
                 restarts[r] += 1;
+                can_continue[r] = hst[r].done && !hst[r].breakdown && hst[r].iters > 0;
             }
         ++total_restarts;
     }
@@ -518,6 +526,7 @@ static int check_params(const wl_gauge *g, const wl_solver_params *p)
     if (!p || !(p->tol > 0) || p->max_iter < 1 || !valid_prec(p->inner_prec) || p->inner_prec == WL_DF ||
         p->max_restarts < 1 || (p->mode != WL_MODE_HOST && p->mode != WL_MODE_GRAPH && p->mode != WL_MODE_PERSISTENT) ||
         p->graph_iters < 0 || p->guess < WL_GUESS_ZERO || p->guess > WL_GUESS_SSM || p->guess_max < 0 ||
+        (p->reliable != 0 && p->reliable != 1) ||
         p->rhs_block < 0 || p->rhs_block > 4 || (p->outer_prec != WL_F64 && p->outer_prec != WL_DF)) {
         set_error("solver parameters out of range");
         return WL_ERR_ARG;

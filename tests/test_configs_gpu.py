@@ -2,10 +2,15 @@
 the benchmark times, checked against the FP64 oracle per mass.
 
 16^3x32 and 24^3x64: the oracle's full-lattice true residual ||b - M_k x|| /
-||b|| of every GPU solution it can afford (one oracle matvec each).
+||b|| of every GPU solution it can afford (one oracle matvec each); on
+24^3x64 also the solution itself against a stored oracle solve (heaviest and
+lightest mass, sampled sites).
 48^3x96: the oracle residual at 4096 random sites plus the source site and
 its neighbours (one oracle matvec takes about half a minute there).  Every
 mass must reach the 1e-10 true residual the solver promises."""
+import json
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -80,6 +85,18 @@ def test_24c64_twelve_point_sources_batched(api):
     for r in (0, 11):
         for i, m in enumerate(MASSES8):
             assert O.true_relres(U, dims, bs[r], xs[r][i].cpu().numpy(), m) <= SLACK * TOL, (r, m)
+    # solution error against the oracle's own solve (tests/golden, written by
+    # make_c3_oracle_samples.py) for source 0 at the heaviest and lightest mass
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "c3_oracle_samples.json")))
+    assert tuple(gold["dims"]) == dims and gold["gauge_seed"] == 3
+    sites = np.array(gold["sites"])
+    for key, ref in gold["x"].items():
+        i = MASSES8.index(float(key))
+        want = np.array(ref)[..., 0] + 1j * np.array(ref)[..., 1]
+        got = xs[0][i][torch.from_numpy(sites).cuda()].cpu().numpy().reshape(len(sites), 12)
+        err = rel(got, want)
+        print(f"24^3x64 source 0 m0 {key}: solution error vs oracle at {len(sites)} sites {err:.2e}")
+        assert err < 1e-8, (key, err)
     # FP64 BiCGstab-M on source 0 with a Gaussian shadow residual: every
     # shift converges without the single-mass polish and agrees with the
     # single-mass solutions

@@ -307,3 +307,38 @@ def test_critical_mass_estimate(api):
     dense = np.linalg.eigvals(O.dense_operator(O.OP_HOP, U, dims))
     mc, ok, _ = critical_mass(g, tol=1e-12)
     assert ok and abs(mc - (dense.real.max() / 2 - 4)) < 1e-8
+
+
+@pytest.mark.parametrize("inner", ["f32", "f16"])
+@pytest.mark.parametrize("mode", ["graph", "host"])
+def test_reliable_updates_vs_oracle(api, inner, mode):
+    """Reliable updates instead of restarted defect correction: the inner
+    BiCGstab keeps its shadow residual and direction across the FP64-class
+    residual replacements, and still reaches the oracle's solution."""
+    dims = (8, 8, 8, 8)
+    U, lat, g = _gauge(api, dims, 0.3, 11)
+    b = synth.z2_source(dims, seed=12)
+    for m0 in (0.3, 0.05):
+        x = torch.zeros((lat.volume, 4, 3), dtype=torch.complex128, device="cuda")
+        prm = api.params(inner_prec=inner, reliable=1,
+                         mode=api.MODE_GRAPH if mode == "graph" else api.MODE_HOST)
+        st = api.bicgstab_solve(g, _cuda(b), x, m0, prm)
+        assert st["status"] == 0 and st["true_relres"] <= 1e-10, st
+        ref, _ = O.eo_solve(U, dims, b, m0, tol=1e-13)
+        assert rel(x.cpu().numpy(), ref) < 1e-8
+        assert O.true_relres(U, dims, b, x.cpu().numpy(), m0) <= 1.1e-10
+
+
+def test_reliable_updates_multimass_batched(api):
+    """Several sources and masses with the FP16 inner solve and reliable
+    updates: every solution converges to the oracle's."""
+    dims = (4, 4, 4, 8)
+    U, lat, g = _gauge(api, dims, 0.5, 21)
+    bs = [synth.point_source(dims, 0, 0), synth.z2_source(dims, 22), synth.gaussian_source(dims, 23)]
+    masses = [0.2, 0.4, 0.05]
+    xs, stats = api.multimass_solve(g, [_cuda(b) for b in bs], masses, api.params(inner_prec="f16", reliable=1))
+    for r, b in enumerate(bs):
+        for i, m in enumerate(masses):
+            assert stats[r][i]["status"] == 0 and stats[r][i]["true_relres"] <= 1e-10, stats[r][i]
+            ref, _ = O.eo_solve(U, dims, b, m, tol=1e-13)
+            assert rel(xs[r][i].cpu().numpy(), ref) < 1e-8
