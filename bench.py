@@ -227,7 +227,8 @@ def run_reference(args, cfg):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": cfg["name"]},
+            "config": {"workload": cfg["name"], "sources": len(bs), "masses": list(cfg.get("masses", MASSES)),
+                       "tol": 1e-10},
             "cpu_baseline": {"kind": "oracle", "cores": 1, "value": v, "unit": UNIT, "host": host_cpu(),
                              "sample": f"FP64 oracle M_prec applications timed on one host core (2 per "
                                        f"BiCGstab iteration), scaled by {iters_per_step} inner iterations per step"},
