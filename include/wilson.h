@@ -23,7 +23,11 @@
  *  - "stream" is a cudaStream_t (NULL = legacy default stream).  Calls are
  *    asynchronous on that stream unless stated otherwise.
  *  - Field arrays are caller-owned DEVICE pointers; the library never frees
- *    them.  Handles (wl_lattice, wl_gauge) are library-owned: the caller
+ *    them.  The canonical sources and solutions of the solvers and of
+ *    wilson_dslash may instead be page-locked HOST memory (cudaHostAlloc or
+ *    cudaHostRegister): with unified addressing the layout kernels read and
+ *    write it directly over the host link, so no separate copy is needed.
+ *    Handles (wl_lattice, wl_gauge) are library-owned: the caller
  *    destroys them.  A wl_gauge also owns the solver workspace, allocated on
  *    first use with cudaMalloc and released by wl_gauge_destroy.
  *  - Canonical external layout (complex128, interleaved re/im):
@@ -36,7 +40,8 @@
  *  - Precisions: WL_F64, WL_F32, WL_F16 (FP16 storage with one FP32 norm
  *    per site, arithmetic in FP32) and WL_DF (double-float, see below).  Links are stored as their first two rows
  *    (12 reals) and the third row is rebuilt as conj(row0 x row1), which is
- *    exact for SU(3) links.
+ *    exact for SU(3) links; double-float links keep all three rows (row 2
+ *    formed in FP64 when the handle is created).
  */
 #ifndef WILSON_H
 #define WILSON_H

@@ -131,8 +131,16 @@ def _ptr(t: torch.Tensor):
 
 
 def _canon(t: torch.Tensor, V: int, what: str):
+    """Canonical source or solution: a CUDA tensor, or a page-locked host
+    tensor that the kernels access directly (unified addressing)."""
     if t.dtype != torch.complex128 or t.numel() != 12 * V:
         raise ValueError(f"{what}: expected complex128 with {12 * V} entries (V, 4, 3)")
+    if not t.is_cuda:
+        if not t.is_pinned():
+            raise ValueError(f"{what}: expected a CUDA tensor or pinned host memory")
+        if not t.is_contiguous():
+            raise ValueError(f"{what}: expected a contiguous tensor")
+        return ctypes.c_void_p(t.data_ptr())
     return _ptr(t)
 
 
@@ -282,7 +290,7 @@ def multimass_solve(g: Gauge, bs, masses, prm: SolverParams | None = None, xs=No
     V = g.lat.volume
     nr, nm = len(bs), len(masses)
     if xs is None:
-        xs = [[torch.empty_like(b) for _ in masses] for b in bs]
+        xs = [[torch.empty_like(b) if b.is_cuda else torch.empty_like(b).pin_memory() for _ in masses] for b in bs]
     bp = (_vp * nr)(*[_canon(b, V, "b").value for b in bs])
     xp = (_vp * (nr * nm))(*[_canon(xs[r][i], V, "x").value for r in range(nr) for i in range(nm)])
     ms = (_dbl * nm)(*[float(m) for m in masses])

@@ -342,3 +342,28 @@ def test_reliable_updates_multimass_batched(api):
             assert stats[r][i]["status"] == 0 and stats[r][i]["true_relres"] <= 1e-10, stats[r][i]
             ref, _ = O.eo_solve(U, dims, b, m, tol=1e-13)
             assert rel(xs[r][i].cpu().numpy(), ref) < 1e-8
+
+
+def test_pinned_host_sources_and_solutions(api):
+    """Canonical sources and solutions in page-locked host memory: the layout
+    kernels read and write them directly, with results identical to the
+    device-memory call."""
+    dims = (4, 4, 4, 8)
+    U, lat, g = _gauge(api, dims, 0.5, 21)
+    bs = [synth.point_source(dims, 1, 1), synth.z2_source(dims, 24)]
+    masses = [0.3, 0.1]
+    xd, sd = api.multimass_solve(g, [_cuda(b) for b in bs], masses)
+    bh = [torch.from_numpy(b).pin_memory() for b in bs]
+    xh = [[torch.empty_like(b).pin_memory() for _ in masses] for b in bh]
+    _, sh = api.multimass_solve(g, bh, masses, xs=xh)
+    torch.cuda.synchronize()
+    for r in range(len(bs)):
+        for i in range(len(masses)):
+            assert torch.equal(xh[r][i], xd[r][i].cpu()), (r, i)
+            assert sh[r][i]["iterations"] == sd[r][i]["iterations"]
+    out = torch.empty_like(bh[0]).pin_memory()
+    api.wilson_dslash(g, bh[1], out, 0.12, "f64", api.OP_M)
+    torch.cuda.synchronize()
+    assert rel(out.numpy(), O.apply(O.OP_MK, U, dims, bs[1], 0.12)) < 1e-12
+    with pytest.raises(ValueError):
+        api.multimass_solve(g, [torch.from_numpy(bs[0])], masses)   # pageable host memory is refused
