@@ -35,10 +35,14 @@ def test_host_only_calls():
     from paper_1103_5103_gb300 import api
     p = api.params()
     assert p.tol == 1e-10 and p.inner_prec == api.F32 and p.eo == 1
+    # the fields after the pointer member land where the C struct has them
+    assert p.outer_prec == api.DF and p.shadow is None and p.guess_max == 0 and p.reliable == 0
+    assert p.guess == api.GUESS_POLY and p.mode == api.MODE_GRAPH and p.graph_iters == 8
     lat = api.Lattice((4, 4, 4, 8))
     assert lat.spinor_bytes("f64") == 192 * 256 and lat.spinor_bytes("f32") == 96 * 256
     assert lat.spinor_bytes("f16") == 52 * 256
-    for bad in [(3, 4, 4, 4), (4, 4, 0, 4), (4, 4, 4, 5)]:
+    # index arithmetic is 32-bit: 12 V must stay below 2^31
+    for bad in [(3, 4, 4, 4), (4, 4, 0, 4), (4, 4, 4, 5), (512, 512, 512, 2)]:
         with pytest.raises(api.WilsonError) as e:
             api.Lattice(bad)
         assert e.value.status == api.WL_ERR_ARG
