@@ -269,6 +269,7 @@ def run_ours(args, cfg):
     xs = [[torch.empty((V, 4, 3), dtype=torch.complex128, device=dev) for _ in masses] for _ in range(nb)]
     prm = api.params(inner_prec=inner, rhs_block=args.rhs_block, outer_prec=args.outer,
                      inner_tol=args.inner_tol, reliable=int(args.reliable),
+                     inner_solver=api.SOLVER_CG if args.inner_solver == "cg" else api.SOLVER_BICGSTAB,
                      mode={"graph": api.MODE_GRAPH, "persistent": api.MODE_PERSISTENT, "host": api.MODE_HOST}[args.mode])
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
@@ -399,6 +400,7 @@ def run_ours(args, cfg):
                    "inner_prec": inner, "outer_prec": args.outer,
                    "inner_tol": args.inner_tol or "library default", "mode": args.mode,
                    "outer_loop": "reliable updates" if args.reliable else "restarted defect correction",
+                   "inner_solver": "CG on the normal equations" if args.inner_solver == "cg" else "BiCGstab",
                    "tol": 1e-10, "l2": "flushed (256 MB write) before every step; working set > L2",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "e2e": {"value": t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
@@ -482,6 +484,7 @@ def main():
     ap.add_argument("--rhs-block", type=int, default=0)
     ap.add_argument("--inner-tol", type=float, default=0.0)
     ap.add_argument("--mode", choices=["graph", "persistent", "host"], default="graph")
+    ap.add_argument("--inner-solver", choices=["bicgstab", "cg"], default="bicgstab")
     ap.add_argument("--reliable", action="store_true",
                     help="reliable updates instead of restarted defect correction in the mixed-precision loop")
     ap.add_argument("--baseline-sources", type=int, default=0,

@@ -86,6 +86,10 @@ extern "C" {
 #define WL_GUESS_SSM  2  /* solution-space minimisation: the combination of the
                             previous solutions with the smallest residual
                             (Section 6.2.2)                                     */
+#define WL_SOLVER_BICGSTAB 0  /* inner Krylov solver: BiCGstab on M_prec (the paper's)     */
+#define WL_SOLVER_CG       1  /* CG on the normal equations M_prec^dag M_prec e = M_prec^dag r
+                                 (Section 8 expects the findings to carry over to CG); the
+                                 inner stop is on the true inner residual r - M_prec e      */
 
 #define WL_MODE_HOST       0  /* one host round trip per iteration                      */
 #define WL_MODE_GRAPH      1  /* iterations captured in a CUDA graph, scalars on device */
@@ -127,6 +131,8 @@ typedef struct {
                             and only r is replaced by the true residual and the
                             correction folded into x when the inner residual has
                             dropped by inner_tol                                      */
+    int    inner_solver; /* WL_SOLVER_BICGSTAB (default) or WL_SOLVER_CG; CG works with
+                            the graph and host modes and restarted defect correction  */
 } wl_solver_params;
 
 typedef struct {
@@ -143,7 +149,8 @@ typedef struct {
  * inner_tol 0 (1e-6 for FP32, 3e-4 for FP16, 1e-12 for FP64; never below
  * what the outer target needs), max_restarts 100,
  * WL_GUESS_POLY, WL_MODE_GRAPH, rhs_block 0, graph_iters 8, eo 1,
- * outer_prec WL_DF, shadow NULL, guess_max 0, reliable 0. */
+ * outer_prec WL_DF, shadow NULL, guess_max 0, reliable 0,
+ * inner_solver WL_SOLVER_BICGSTAB. */
 int wl_params_default(wl_solver_params *p);
 
 /* Thread-local message describing the last failing call on this thread. */

@@ -24,6 +24,7 @@ F64, F32, F16, DF = 1, 2, 4, 8
 EVEN, ODD = 0, 1
 OP_HOP, OP_M, OP_MPREC = 0, 1, 2
 GUESS_ZERO, GUESS_POLY, GUESS_SSM = 0, 1, 2
+SOLVER_BICGSTAB, SOLVER_CG = 0, 1
 MODE_HOST, MODE_GRAPH, MODE_PERSISTENT = 0, 1, 2
 _PREC_NAMES = {"f64": F64, "f32": F32, "f16": F16, "df": DF}
 
@@ -50,7 +51,7 @@ class SolverParams(ctypes.Structure):
     _fields_ = [("tol", _dbl), ("max_iter", _int), ("inner_prec", _int), ("inner_tol", _dbl),
                 ("max_restarts", _int), ("guess", _int), ("mode", _int), ("rhs_block", _int),
                 ("graph_iters", _int), ("eo", _int), ("outer_prec", _int), ("shadow", _vp),
-                ("guess_max", _int), ("reliable", _int)]
+                ("guess_max", _int), ("reliable", _int), ("inner_solver", _int)]
 
 
 class SolverStats(ctypes.Structure):

@@ -172,6 +172,75 @@ int blas_xr_update(const Geom &g, const Vec &x, const Vec &p, const Vec &sv, con
     return WL_OK;
 }
 
+// ------------------- CG on the normal equations: x += alpha p, r -= alpha w
+// with ||r||^2 for the stopping test (the true inner residual r = b - M x,
+// not the normal-equation residual).
+
+template <int P, int PX>
+__global__ void __launch_bounds__(kBlock) k_cg_xr(Geom g, Vec x, Vec p, Vec w, Vec r, BiState *state,
+                                                  double *partials)
+{
+    const SiteIdx q = site_idx(r.nrhs);
+    BiState &S = state[q.r];
+    if (__ldcg(&S.done)) return;
+    using R = RT<P>;
+    using RX = RT<PX>;
+    double red[1] = {0.0};
+    if (q.i < g.Vh) {
+        const double al = __ldcg(&S.alpha_re);
+        cx<R> pv[12], wv[12], rv[12];
+        ld<P>(p, q.r, g.stride, q.i, pv);
+        ld<P>(w, q.r, g.stride, q.i, wv);
+        ld<P>(r, q.r, g.stride, q.i, rv);
+        cx<RX> xv[12];
+        SpinorIO<PX>::load(x.rhs(q.r), g.stride, q.i, xv);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            xv[k] = {fma((RX)al, (RX)pv[k].re, xv[k].re), fma((RX)al, (RX)pv[k].im, xv[k].im)};
+            rv[k] = {fma(-(R)al, wv[k].re, rv[k].re), fma(-(R)al, wv[k].im, rv[k].im)};
+        }
+        SpinorIO<PX>::store(x.rhs(q.r), g.stride, q.i, xv);
+        SpinorIO<P>::roundtrip(rv);
+        st<P>(r, q.r, g.stride, q.i, rv);
+        R n = R(0);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) n = fma(rv[k].re, rv[k].re, fma(rv[k].im, rv[k].im, n));
+        red[0] = (double)n;
+    }
+    double tot[1];
+    if (grid_sum<1>(red, partials + (size_t)q.r * q.nsb * kRedNV, &S.ticket[1], q.sb, q.nsb, tot) &&
+        threadIdx.x == 0) {
+        const double rr = tot[0];
+        S.iters += 1;
+        S.rr = rr;
+        if (!isfinite(rr)) {
+            S.breakdown = 1;
+            S.done = 1;
+        } else if (rr <= S.target2) {
+            S.done = 1;
+        }
+    }
+}
+
+int blas_cg_xr(const Geom &g, const Vec &x, const Vec &p, const Vec &w, const Vec &r, BiState *state,
+               double *partials, cudaStream_t s)
+{
+    const int gr = grid_of(g, r.nrhs);
+    if (r.prec == WL_F64 && x.prec == WL_F64)
+        k_cg_xr<WL_F64, WL_F64><<<gr, kBlock, 0, s>>>(g, x, p, w, r, state, partials);
+    else if (r.prec == WL_F32 && x.prec == WL_F32)
+        k_cg_xr<WL_F32, WL_F32><<<gr, kBlock, 0, s>>>(g, x, p, w, r, state, partials);
+    else if (r.prec == WL_F16 && x.prec == WL_F32)
+        k_cg_xr<WL_F16, WL_F32><<<gr, kBlock, 0, s>>>(g, x, p, w, r, state, partials);
+    else {
+        set_error("blas_cg_xr: unsupported precision pair");
+        return WL_ERR_ARG;
+    }
+    WL_CUDA_TRY(cudaGetLastError());
+    note_launch(s);
+    return WL_OK;
+}
+
 // ------------------------------------------------ p = r + beta (p - omega v)
 
 template <int P>

@@ -113,10 +113,17 @@ int hop_reduce(wl_gauge *g, int kind, const Vec &tmp, const Vec &xin, double a1,
                double coef, const double *coef_dev, int out_parity, int dagger, BiState *state, double *partials,
                int blk_off, int blk_total, cudaStream_t s)
 {
-    return kind == 0 ? hop_reduce_k<0>(g, tmp, xin, a1, out, rhat, coef, coef_dev, out_parity, dagger, state,
-                                       partials, blk_off, blk_total, s)
-                     : hop_reduce_k<1>(g, tmp, xin, a1, out, rhat, coef, coef_dev, out_parity, dagger, state,
-                                       partials, blk_off, blk_total, s);
+    switch (kind) {
+    case 0: return hop_reduce_k<0>(g, tmp, xin, a1, out, rhat, coef, coef_dev, out_parity, dagger, state, partials,
+                                   blk_off, blk_total, s);
+    case 1: return hop_reduce_k<1>(g, tmp, xin, a1, out, rhat, coef, coef_dev, out_parity, dagger, state, partials,
+                                   blk_off, blk_total, s);
+    case 2: return hop_reduce_k<2>(g, tmp, xin, a1, out, rhat, coef, coef_dev, out_parity, dagger, state, partials,
+                                   blk_off, blk_total, s);
+    case 3: return hop_reduce_k<3>(g, tmp, xin, a1, out, rhat, coef, coef_dev, out_parity, dagger, state, partials,
+                                   blk_off, blk_total, s);
+    default: set_error("hop_reduce: bad kind"); return WL_ERR_ARG;
+    }
 }
 
 }  // namespace wl

@@ -201,6 +201,8 @@ struct EpiStore {
 // Solver epilogues (NB = 1, one rhs per block):
 //   KIND 0: v = p + coef*acc, reduce <rhat, v>  -> alpha = rho / <rhat, v>
 //   KIND 1: t = s + coef*acc, reduce <t, s>, <t, t>  -> omega = <t,s>/<t,t>
+//   KIND 2: w = p + coef*acc, reduce ||w||^2  -> alpha = ||z||^2 / ||w||^2 (CG)
+//   KIND 3: z = r + coef*acc (dagger hop), reduce ||z||^2 -> beta (CG)
 template <int KIND>
 struct EpiReduce {
     void *out;
@@ -727,7 +729,7 @@ __device__ __forceinline__ void hop_reduce_body(const HopArgs &a, const EpiReduc
             red[0] = (double)d.re;
             red[1] = (double)d.im;
             red[2] = (double)n;
-        } else {
+        } else if constexpr (KIND == 1) {
             cx<R> d = {R(0), R(0)};
             R n = R(0);
 #pragma unroll
@@ -737,6 +739,11 @@ __device__ __forceinline__ void hop_reduce_body(const HopArgs &a, const EpiReduc
             }
             red[0] = (double)d.re;
             red[1] = (double)d.im;
+            red[2] = (double)n;
+        } else {
+            R n = R(0);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) n = fma(o[k].re, o[k].re, fma(o[k].im, o[k].im, n));
             red[2] = (double)n;
         }
     }
@@ -754,7 +761,7 @@ __device__ __forceinline__ void hop_reduce_body(const HopArgs &a, const EpiReduc
                 st.alpha_re = (st.rho_re * dr + st.rho_im * di) / den;
                 st.alpha_im = (st.rho_im * dr - st.rho_re * di) / den;
             }
-        } else {
+        } else if constexpr (KIND == 1) {
             const double tt = tot[2];
             if (tt > 0.0 && isfinite(tt)) {
                 st.omega_re = tot[0] / tt;
@@ -762,6 +769,30 @@ __device__ __forceinline__ void hop_reduce_body(const HopArgs &a, const EpiReduc
             } else {
                 st.omega_re = 0.0;
                 st.omega_im = 0.0;
+            }
+        } else if constexpr (KIND == 2) {
+            // CG on the normal equations: w = M p, alpha = ||z||^2 / ||w||^2
+            const double ww = tot[2];
+            if (!(ww > 0.0) || !isfinite(ww)) {
+                st.breakdown = 1;
+                st.done = 1;
+            } else {
+                st.alpha_re = st.rho_re / ww;
+                st.alpha_im = 0.0;
+            }
+        } else {
+            // z = M^dag r, beta = ||z||^2 / ||z_old||^2 (0 on the first z
+            // after a restart), rho = ||z||^2
+            const double zz = tot[2];
+            if (!isfinite(zz)) {
+                st.breakdown = 1;
+                st.done = 1;
+            } else {
+                st.beta_re = (st.iters == 0 || !(st.rho_re > 0.0)) ? 0.0 : zz / st.rho_re;
+                st.beta_im = 0.0;
+                st.omega_re = st.omega_im = 0.0;
+                st.rho_re = zz;
+                st.rho_im = 0.0;
             }
         }
     }
@@ -797,6 +828,16 @@ void launch_k_hop_reduce(const HopArgs &a, const EpiReduce<KIND> &e, cudaStream_
 {
     const int nsb = (a.g.Vh + 127) / 128;
     k_hop_reduce<P, DAG, KIND><<<nsb * a.nrhs, 128, 0, s>>>(a, e);
+}
+
+template <int P, int KIND>
+void launch_reduce_kind(int dagger, const HopArgs &a, const void *epi, cudaStream_t s)
+{
+    const auto &e = *static_cast<const EpiReduce<KIND> *>(epi);
+    if (dagger)
+        launch_k_hop_reduce<P, true, KIND>(a, e, s);
+    else
+        launch_k_hop_reduce<P, false, KIND>(a, e, s);
 }
 
 // Per-precision entry points (hop_<prec>.cu).  variant: see hop_variants().

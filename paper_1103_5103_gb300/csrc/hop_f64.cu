@@ -34,12 +34,11 @@ int hop_launch_prec<WL_F64>(int v, int dagger, const HopArgs &a, const EpiStore 
 template <>
 int hop_reduce_launch_prec<WL_F64>(int kind, int dagger, const HopArgs &a, const void *epi, cudaStream_t s)
 {
-    if (kind == 0) {
-        const auto &e = *static_cast<const EpiReduce<0> *>(epi);
-        dagger ? launch_k_hop_reduce<WL_F64, true, 0>(a, e, s) : launch_k_hop_reduce<WL_F64, false, 0>(a, e, s);
-    } else {
-        const auto &e = *static_cast<const EpiReduce<1> *>(epi);
-        dagger ? launch_k_hop_reduce<WL_F64, true, 1>(a, e, s) : launch_k_hop_reduce<WL_F64, false, 1>(a, e, s);
+    switch (kind) {
+    case 0: launch_reduce_kind<WL_F64, 0>(dagger, a, epi, s); break;
+    case 1: launch_reduce_kind<WL_F64, 1>(dagger, a, epi, s); break;
+    case 2: launch_reduce_kind<WL_F64, 2>(dagger, a, epi, s); break;
+    default: launch_reduce_kind<WL_F64, 3>(dagger, a, epi, s); break;
     }
     WL_CUDA_TRY(cudaGetLastError());
     return WL_OK;

@@ -118,6 +118,9 @@ int hop_reduce(wl_gauge *g, int kind, const Vec &tmp, const Vec &xin, double a1,
 
 // ---- blas.cu (all on one parity; nrhs from the vectors)
 int blas_s_update(const Geom &g, const Vec &r, const Vec &v, const Vec &s_out, BiState *st, cudaStream_t s);
+// CG on the normal equations: x += alpha p, r -= alpha w, ||r||^2 -> stop
+int blas_cg_xr(const Geom &g, const Vec &x, const Vec &p, const Vec &w, const Vec &r, BiState *state,
+               double *partials, cudaStream_t s);
 int blas_xr_update(const Geom &g, const Vec &x, const Vec &p, const Vec &sv, const Vec &t, const Vec &r,
                    const Vec &rhat, BiState *st, double *partials, cudaStream_t s);
 int blas_p_update(const Geom &g, const Vec &r, const Vec &p, const Vec &v, BiState *st, cudaStream_t s);

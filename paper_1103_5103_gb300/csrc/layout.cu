@@ -329,6 +329,7 @@ extern "C" int wl_params_default(wl_solver_params *p)
     p->shadow = nullptr;
     p->guess_max = 0;
     p->reliable = 0;
+    p->inner_solver = WL_SOLVER_BICGSTAB;
     return WL_OK;
 }
 

@@ -125,6 +125,21 @@ static int make_inner(wl_gauge *g, int prec, int nrhs, double kappa, Inner *in, 
     return get_scratch(g, nrhs, &in->sc, s);
 }
 
+// z = M^dag r with ||z||^2 and beta, then p = z + beta p (CG on the normal
+// equations; after a restart beta = 0, so p = z).
+static int cg_normal_residual(Inner &in, int rhs_block, cudaStream_t s)
+{
+    const Geom &geo = in.g->lat->geom;
+    const int *skip = &in.sc.state[0].done;
+    const int ss = sizeof(BiState) / sizeof(int);
+    WL_TRY(hop_ex(in.g, in.r, in.tmp, nullptr, 0.0, nullptr, 0.0, 1.0, WL_ODD, 1, rhs_block, skip, ss, s));
+    WL_TRY(hop_reduce(in.g, 3, in.tmp, in.r, 1.0, in.s, in.rhat, 0.0, in.sc.kappa2, WL_EVEN, 1, in.sc.state,
+                      in.sc.partials, 0, site_blocks(geo), s));
+    // omega = 0, so the BiCGstab p update reduces to p = z + beta p
+    WL_TRY(blas_p_update(geo, in.s, in.p, in.p, in.sc.state, s));
+    return WL_OK;
+}
+
 // Enqueue one BiCGstab iteration for every rhs.  ev (optional) is a pair of
 // events recorded around the first hop for live kernel timing.
 static int inner_iteration(Inner &in, int rhs_block, cudaStream_t s, cudaEvent_t *ev = nullptr)
@@ -154,6 +169,35 @@ static int inner_iteration(Inner &in, int rhs_block, cudaStream_t s, cudaEvent_t
                       0, nsb, s));
     WL_TRY(blas_xr_update(geo, in.e, in.p, in.s, in.t, in.r, in.rhat, in.sc.state, in.sc.partials, s));
     WL_TRY(blas_p_update(geo, in.r, in.p, in.v, in.sc.state, s));
+    return WL_OK;
+}
+
+// Enqueue one iteration of CG on the normal equations M^dag M e = M^dag r
+// (M = M_prec, M^dag = gamma5 M gamma5, the dagger hops):
+//   w = M p (||w||^2 -> alpha = ||z||^2 / ||w||^2);  e += alpha p;
+//   r -= alpha w (||r||^2: stop on the true inner residual);
+//   z = M^dag r (||z||^2 -> beta);  p = z + beta p.
+// Buffers: v holds w, s holds z.
+static int inner_iteration_cg(Inner &in, int rhs_block, cudaStream_t s, cudaEvent_t *ev = nullptr)
+{
+    const Geom &geo = in.g->lat->geom;
+    const int nsb = site_blocks(geo);
+    const int *skip = &in.sc.state[0].done;
+    const int ss = sizeof(BiState) / sizeof(int);
+    const double *k2 = in.sc.kappa2;
+    unsigned evflags = cudaEventRecordDefault;
+    if (ev) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        WL_CUDA_TRY(cudaStreamIsCapturing(s, &cs));
+        if (cs == cudaStreamCaptureStatusActive) evflags = cudaEventRecordExternal;
+        WL_CUDA_TRY(cudaEventRecordWithFlags(ev[0], s, evflags));
+    }
+    WL_TRY(hop_ex(in.g, in.p, in.tmp, nullptr, 0.0, nullptr, 0.0, 1.0, WL_ODD, 0, rhs_block, skip, ss, s));
+    if (ev) WL_CUDA_TRY(cudaEventRecordWithFlags(ev[1], s, evflags));
+    WL_TRY(hop_reduce(in.g, 2, in.tmp, in.p, 1.0, in.v, in.rhat, 0.0, k2, WL_EVEN, 0, in.sc.state, in.sc.partials,
+                      0, nsb, s));
+    WL_TRY(blas_cg_xr(geo, in.e, in.p, in.v, in.r, in.sc.state, in.sc.partials, s));
+    WL_TRY(cg_normal_residual(in, rhs_block, s));
     return WL_OK;
 }
 
@@ -194,6 +238,7 @@ static int run_inner(Inner &in, const wl_solver_params &prm, int max_iter, std::
             (uintptr_t)in.rhat.ptr, (uintptr_t)in.s.ptr, (uintptr_t)in.t.ptr, (uintptr_t)in.e.ptr,
             (uintptr_t)in.sc.state, (uintptr_t)in.sc.partials, (uintptr_t)in.sc.kappa2, (uintptr_t)nrhs,
             (uintptr_t)in.prec, (uintptr_t)in.xprec, (uintptr_t)K, (uintptr_t)rb, (uintptr_t)prof,
+            (uintptr_t)prm.inner_solver,
             (uintptr_t)in.g->lat->geom.Vh};
         if (gc.exec == nullptr || gc.key != key) {
             gc.release();
@@ -205,7 +250,9 @@ static int run_inner(Inner &in, const wl_solver_params &prm, int max_iter, std::
             cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
             if (e == cudaSuccess) {
                 for (int k = 0; k < K && status == WL_OK; ++k)
-                    status = inner_iteration(in, rb, cap, prof ? &gc.events[2 * k] : nullptr);
+                    status = prm.inner_solver == WL_SOLVER_CG
+                                 ? inner_iteration_cg(in, rb, cap, prof ? &gc.events[2 * k] : nullptr)
+                                 : inner_iteration(in, rb, cap, prof ? &gc.events[2 * k] : nullptr);
                 e = cudaStreamEndCapture(cap, &graph);
             }
             if (e == cudaSuccess && status == WL_OK) e = cudaGraphInstantiate(&gc.exec, graph, 0);
@@ -257,7 +304,7 @@ static int run_inner(Inner &in, const wl_solver_params &prm, int max_iter, std::
             add_launches(graph_kernels);
             done_iters += K;
         } else {
-            status = inner_iteration(in, rb, s, ev);
+            status = prm.inner_solver == WL_SOLVER_CG ? inner_iteration_cg(in, rb, s, ev) : inner_iteration(in, rb, s, ev);
             if (status != WL_OK) break;
             done_iters += 1;
         }
@@ -418,6 +465,7 @@ static int eo_defect_correction(wl_gauge *g, const Vec &bprec, const Vec &x64, d
         WL_CUDA_TRY(cudaMemcpyAsync(in.sc.delta2, h_delta2, sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
         WL_TRY(blas_restart(geo, r64, in.r, in.rhat, in.p, in.e, in.sc.state, in.sc.partials, in.sc.active,
                             in.sc.delta2, s));
+        if (prm.inner_solver == WL_SOLVER_CG) WL_TRY(cg_normal_residual(in, 0, s));  // z = M^dag r, p = z
         bool any_continue = false;
         for (int r = 0; r < nrhs; ++r) any_continue |= h_active[r] == 2;
         // continued rhs: p = r + beta (p - omega v) with the beta the update set
@@ -527,6 +575,8 @@ static int check_params(const wl_gauge *g, const wl_solver_params *p)
         p->max_restarts < 1 || (p->mode != WL_MODE_HOST && p->mode != WL_MODE_GRAPH && p->mode != WL_MODE_PERSISTENT) ||
         p->graph_iters < 0 || p->guess < WL_GUESS_ZERO || p->guess > WL_GUESS_SSM || p->guess_max < 0 ||
         (p->reliable != 0 && p->reliable != 1) ||
+        (p->inner_solver != WL_SOLVER_BICGSTAB && p->inner_solver != WL_SOLVER_CG) ||
+        (p->inner_solver == WL_SOLVER_CG && (p->reliable || p->mode == WL_MODE_PERSISTENT)) ||
         p->rhs_block < 0 || p->rhs_block > 4 || (p->outer_prec != WL_F64 && p->outer_prec != WL_DF)) {
         set_error("solver parameters out of range");
         return WL_ERR_ARG;

@@ -367,3 +367,39 @@ def test_pinned_host_sources_and_solutions(api):
     assert rel(out.numpy(), O.apply(O.OP_MK, U, dims, bs[1], 0.12)) < 1e-12
     with pytest.raises(ValueError):
         api.multimass_solve(g, [torch.from_numpy(bs[0])], masses)   # pageable host memory is refused
+
+
+@pytest.mark.parametrize("inner", ["f64", "f32", "f16"])
+@pytest.mark.parametrize("mode", ["graph", "host"])
+def test_cg_normal_equations_inner_solver(api, inner, mode):
+    """CG on the normal equations M^dag M e = M^dag r as the inner solver of
+    the defect correction (the dagger hops are gamma5-conjugated): the same
+    solution as the oracle's BiCGstab solve."""
+    dims = (4, 4, 4, 8)
+    U, lat, g = _gauge(api, dims, 0.3, 11)
+    b = synth.z2_source(dims, seed=12)
+    for m0 in (0.3, 0.05):
+        x = torch.zeros((lat.volume, 4, 3), dtype=torch.complex128, device="cuda")
+        prm = api.params(inner_prec=inner, inner_solver=api.SOLVER_CG,
+                         mode=api.MODE_GRAPH if mode == "graph" else api.MODE_HOST)
+        st = api.bicgstab_solve(g, _cuda(b), x, m0, prm)
+        assert st["status"] == 0 and st["true_relres"] <= 1e-10, st
+        ref, _ = O.eo_solve(U, dims, b, m0, tol=1e-13)
+        assert rel(x.cpu().numpy(), ref) < 1e-8
+
+
+def test_cg_multimass_batched_and_rejected_combinations(api):
+    dims = (4, 4, 4, 8)
+    U, lat, g = _gauge(api, dims, 0.5, 21)
+    bs = [synth.point_source(dims, 0, 0), synth.z2_source(dims, 22)]
+    masses = [0.2, 0.4, 0.05]
+    xs, stats = api.multimass_solve(g, [_cuda(b) for b in bs], masses, api.params(inner_solver=api.SOLVER_CG))
+    for r, b in enumerate(bs):
+        for i, m in enumerate(masses):
+            assert stats[r][i]["status"] == 0 and stats[r][i]["true_relres"] <= 1e-10, stats[r][i]
+            ref, _ = O.eo_solve(U, dims, b, m, tol=1e-13)
+            assert rel(xs[r][i].cpu().numpy(), ref) < 1e-8
+    for bad in (dict(reliable=1), dict(mode=api.MODE_PERSISTENT)):
+        with pytest.raises(api.WilsonError) as e:
+            api.multimass_solve(g, [_cuda(bs[0])], masses, api.params(inner_solver=api.SOLVER_CG, **bad))
+        assert e.value.status == api.WL_ERR_ARG
