@@ -403,3 +403,25 @@ def test_cg_multimass_batched_and_rejected_combinations(api):
         with pytest.raises(api.WilsonError) as e:
             api.multimass_solve(g, [_cuda(bs[0])], masses, api.params(inner_solver=api.SOLVER_CG, **bad))
         assert e.value.status == api.WL_ERR_ARG
+
+
+def test_multimass_mass_count_edges(api):
+    """One mass (no guess to build), the maximum of sixteen (a Lagrange guess
+    through fifteen solutions, 31 inputs to one combination), and seventeen,
+    which is refused."""
+    dims = (4, 4, 2, 4)
+    U, lat, g = _gauge(api, dims, 0.4, 61)
+    b = synth.gaussian_source(dims, seed=62)
+    xs, st = api.multimass_solve(g, [_cuda(b)], [0.25])
+    assert st[0][0]["true_relres"] <= 1e-10
+    assert rel(xs[0][0].cpu().numpy(), O.eo_solve(U, dims, b, 0.25, tol=1e-13)[0]) < 1e-8
+    masses = [0.5 * 0.04 ** (i / 15.0) for i in range(16)]
+    for guess in (api.GUESS_POLY, api.GUESS_SSM):
+        xs, st = api.multimass_solve(g, [_cuda(b)], masses, api.params(guess=guess))
+        for i, m in enumerate(masses):
+            assert st[0][i]["true_relres"] <= 1e-10, (m, st[0][i])
+        for i in (0, 7, 15):
+            assert rel(xs[0][i].cpu().numpy(), O.eo_solve(U, dims, b, masses[i], tol=1e-13)[0]) < 1e-8
+    with pytest.raises(api.WilsonError) as e:
+        api.multimass_solve(g, [_cuda(b)], masses + [0.9])
+    assert e.value.status == api.WL_ERR_ARG
