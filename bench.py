@@ -378,6 +378,8 @@ def run_ours(args, cfg):
         hop_gflops = 1320 * per_launch_site_rhs / avg_s / 1e9
     else:
         bytes_launch = avg_s = achieved = hop_gflops = None
+    # the timed hop's operands: links of one parity and nb input/output spinors
+    l2_resident = bytes_launch is not None and bytes_launch < 129e6
     traffic = None
     if (inner, hop_variant, nb) in HOP_TRAFFIC:
         sites_cap, bytes_cap = HOP_TRAFFIC[(inner, hop_variant, nb)]
@@ -410,7 +412,10 @@ def run_ours(args, cfg):
                 "explicit_copies_value": t_e2e_copy},
         "gpu_launches": int(round(launches)),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     # a hop whose operands fit in the 129 MB L2 is latency-bound:
+                     # no HBM fraction is quoted for it
+                     "frac": (achieved / peak) if achieved and not l2_resident else None,
+                     "l2_resident": l2_resident, "traffic": traffic,
                      "kernel": f"k_hop<{inner}> (D_oe p, first hop of each BiCGstab iteration), "
                                f"autotuned variant {hop_variant}",
                      "peak_kind": peak_kind, "bytes_per_launch": bytes_launch,
