@@ -490,6 +490,8 @@ def main():
     ap.add_argument("--inner-tol", type=float, default=0.0)
     ap.add_argument("--mode", choices=["graph", "persistent", "host"], default="graph")
     ap.add_argument("--inner-solver", choices=["bicgstab", "cg"], default="bicgstab")
+    ap.add_argument("--dims", default="",
+                    help="run the workload on another lattice, e.g. 32x32x32x64 (profiling of a smaller case)")
     ap.add_argument("--reliable", action="store_true",
                     help="reliable updates instead of restarted defect correction in the mixed-precision loop")
     ap.add_argument("--baseline-sources", type=int, default=0,
@@ -504,7 +506,12 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    cfg = CONFIGS[args.config]
+    cfg = dict(CONFIGS[args.config])
+    if args.dims:
+        # profiling aid: the workload's sources, masses and precisions on a
+        # smaller lattice (the line's workload name says so)
+        cfg["dims"] = tuple(int(v) for v in args.dims.split("x"))
+        cfg["name"] = cfg["name"] + f", run on {args.dims}"
     if args.impl == "reference":
         run_reference(args, cfg)
     else:
