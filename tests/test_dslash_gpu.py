@@ -88,6 +88,39 @@ def test_internal_layout_roundtrip(api, prec):
         assert err < {"df": 1e-14, "f32": 1e-7, "f16": 1e-3}[prec], err
 
 
+def test_double_float_and_fp32_export_is_exact(api):
+    """Import splits a double into hi = fl32(d), lo = fl32(d - hi) and
+    renormalises; export returns hi + lo in FP64, which is exact.  The round
+    trip equals the same float arithmetic done in numpy, bit for bit, for
+    normal, zero, negative-zero, subnormal-float and extreme values."""
+    dims = (2, 2, 2, 2)
+    lat = api.Lattice(dims)
+    V = lat.volume
+    rng = np.random.default_rng(3)
+    special = np.array([0.0, -0.0, 1.0, -2.5, 1.0 / 3.0, 1e-40, -3e-42, 1e-38, 3.0e38, -1.17549435e-38,
+                        np.pi * 1e20, np.e * 1e-20])
+    vals = np.concatenate([special, rng.standard_normal(12 * V * 2 - len(special)) * 10.0 ** rng.integers(-30, 30, 12 * V * 2 - len(special))])
+    psi = (vals[0::2] + 1j * vals[1::2]).reshape(V, 4, 3)
+    d = _cuda(psi)
+    for prec in ("df", "f32"):
+        back = torch.zeros_like(d)
+        for par in (0, 1):
+            buf = lat.new_internal(prec)
+            lat.spinor_import(d, buf, prec, par)
+            lat.spinor_export(buf, back, prec, par)
+        got = back.cpu().numpy().view(np.float64).reshape(-1)
+        x = psi.view(np.float64).reshape(-1)
+        hi = x.astype(np.float32)
+        if prec == "df":
+            lo = (x - hi.astype(np.float64)).astype(np.float32)
+            s = (hi + lo).astype(np.float32)
+            lo = (lo - (s - hi)).astype(np.float32)
+            want = s.astype(np.float64) + lo.astype(np.float64)
+        else:
+            want = hi.astype(np.float64)
+        assert np.array_equal(got.view(np.uint64), want.view(np.uint64)), prec
+
+
 def test_f16_sites_below_float_range_store_as_zero(api):
     """FP16 storage scales each site by its largest entry.  Sites whose
     entries are all below the smallest normal float (here 1e-40, an FP32
