@@ -427,44 +427,48 @@ def run_ours(args, cfg):
         "gauge_generation_s": gen_s,
     }
     if rank == 0 and ws == 1 and not args.no_baseline:
-        # FP64 BiCGstab-M on the same GPU, same sources and masses (context for
-        # the paper's comparison; not part of the timed step).  A fresh handle
-        # with FP64 links only, so its footprint is its own.
+        # BiCGstab-M on the same GPU, same sources and masses (context for the
+        # paper's comparison; not part of the timed step), with its vectors
+        # and hops in double-float and in FP64.  Each on a fresh handle with
+        # only the links it uses, so its footprint is its own.
         g.close()
         del g, xs
-        torch.cuda.synchronize()
-        torch.cuda.empty_cache()
-        mem1 = _used_bytes(torch)
-        g64 = api.Gauge(lat, U_dev, precs=("f64",))
-        t_m, it_m, worst_m, mem_m, polished = 0.0, 0, 0.0, 0, 0
-        per_shift = None
         # with rhat = b a point source breaks the recurrences down at once
         # (<b, r_1> = 0): such sources get a Gaussian shadow residual
         point = cfg["sources"].startswith("point")
         shadow = torch.from_numpy(synth.gaussian_source(dims, seed=cfg["seed"] + 1000)).to(dev) if point else None
-        prm_m = api.params(shadow=shadow)
         nsrc = min(nr, args.baseline_sources or cfg.get("baseline_sources", nr))
-        for r in range(nsrc):
-            xm = [torch.empty((V, 4, 3), dtype=torch.complex128, device=dev) for _ in masses]
+        for key, outer, precs in (("bicgstab_m_df", "df", ("df", "f32")), ("bicgstab_m_fp64", "f64", ("f64",))):
             torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            stm = api.bicgstab_m_solve(g64, bs[r], xm, masses, prm_m, check=False)
-            torch.cuda.synchronize()
-            t_m += time.perf_counter() - t0
-            mem_m = max(mem_m, _used_bytes(torch) - mem1)
-            it_m += max(s["iterations"] for s in stm)
-            worst_m = max(worst_m, max(s["true_relres"] for s in stm))
-            per_shift = [int(s["iterations"]) for s in stm]
-            polished += sum(1 for s in stm if s["restarts"] > 0)
-            del xm
-        g64.close()
-        line["bicgstab_m_fp64"] = {"seconds_per_step": t_m * nr / nsrc, "sources_run": nsrc,
-                                   "iterations_per_source": it_m / nsrc, "max_true_relres": worst_m,
-                                   "iterations_per_mass_last_source": per_shift,
-                                   "shadow_residual": "Gaussian noise" if point else "b",
-                                   "masses_polished_by_single_mass": polished,
-                                   "device_memory_gb": mem_m / 1e9,
-                                   "speedup_of_single_mass_scheme": (t_m * nr / nsrc) / t_step}
+            torch.cuda.empty_cache()
+            mem1 = _used_bytes(torch)
+            gm = api.Gauge(lat, U_dev, precs=precs)
+            prm_m = api.params(shadow=shadow, outer_prec=outer)
+            t_m, it_m, worst_m, mem_m, polished = 0.0, 0, 0.0, 0, 0
+            per_shift = None
+            for r in range(nsrc):
+                xm = [torch.empty((V, 4, 3), dtype=torch.complex128, device=dev) for _ in masses]
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                stm = api.bicgstab_m_solve(gm, bs[r], xm, masses, prm_m, check=False)
+                torch.cuda.synchronize()
+                t_m += time.perf_counter() - t0
+                mem_m = max(mem_m, _used_bytes(torch) - mem1)
+                it_m += max(s["iterations"] for s in stm)
+                worst_m = max(worst_m, max(s["true_relres"] for s in stm))
+                per_shift = [int(s["iterations"]) for s in stm]
+                polished += sum(1 for s in stm if s["restarts"] > 0)
+                del xm
+            gm.close()
+            del gm
+            line[key] = {"seconds_per_step": t_m * nr / nsrc, "sources_run": nsrc,
+                         "vectors_and_hops": "double-float" if outer == "df" else "FP64",
+                         "iterations_per_source": it_m / nsrc, "max_true_relres": worst_m,
+                         "iterations_per_mass_last_source": per_shift,
+                         "shadow_residual": "Gaussian noise" if point else "b",
+                         "masses_polished_by_single_mass": polished,
+                         "device_memory_gb": mem_m / 1e9,
+                         "speedup_of_single_mass_scheme": (t_m * nr / nsrc) / t_step}
     if rank == 0 and ws == 1 and not args.no_cpu:
         s_it, n_it, dt = oracle_sample(cfg, U, bs_h, target_s=args.cpu_seconds)
         line["cpu_baseline"] = {"value": s_it * iters, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),

@@ -259,12 +259,16 @@ int bicgstab_solve(wl_gauge *g, const void *b, void *x, double m0, const wl_solv
 /* Multi-shift BiCGstab-M baseline (Section 6.1): one Krylov space built on
  * the full-lattice unshifted system M_p(m_s), m_s = min m0[i], shifts
  * sigma_i = m0[i] - m_s, converged shifts frozen, loop ends when the
- * unshifted residual is below tol * ||b||.  Always FP64, no even-odd
- * preconditioning (the paper: multi-shift cannot use it).  x[i] receives the
+ * unshifted residual is below tol * ||b||.  No even-odd preconditioning
+ * (the paper: multi-shift cannot use it) and no reduced precision (the
+ * shifted recurrences need the full Krylov space): the vectors and hops run
+ * in p->outer_prec, WL_F64 (needs FP64 links) or WL_DF (double-float, needs
+ * double-float links); inner_prec is not used.  x[i] receives the
  * kappa-form solution (m0[i] + 4) psi_i as a canonical complex128 vector.
- * A shift whose FP64 true residual is still above tol afterwards is polished
- * by a single-mass FP64 BiCGstab from x[i]; its extra iterations are counted
- * in stats[i].restarts.  The shadow residual is p->shadow (NULL: b).
+ * A shift whose true residual is still above tol afterwards is polished by
+ * a single-mass BiCGstab from x[i] (FP64 inner where the handle has FP64
+ * links, else FP32 inner and outer_prec outer); its extra iterations are
+ * counted in stats[i].restarts.  The shadow residual is p->shadow (NULL: b).
  * Returns WL_ERR_BREAKDOWN, with the polished solutions in x, when the
  * shifted recurrences broke down.  Masses must be distinct.  Synchronises
  * the stream. */

@@ -12,7 +12,9 @@
 //     beta^s = beta_n (pi_n / pi_{n+1})^2
 //     p^s = r_{n+1} / (pi_{n+1} lambda_{n+1}) + beta^s q^s
 // The shifted residual is r_{n+1} / (pi_{n+1} lambda_{n+1}); a shift whose
-// residual is below tol ||b|| is frozen (Section 6.1).  All vectors FP64,
+// residual is below tol ||b|| is frozen (Section 6.1).  The vectors and hops
+// are FP64 or double-float (48-bit significands on the FP32 pipes); the
+// scalar recurrences are FP64 either way;
 // each full-lattice vector stored as its even and odd halves.
 #include <algorithm>
 #include <chrono>
@@ -147,14 +149,19 @@ __device__ __forceinline__ FullIdx full_idx(int nsb)
     return f;
 }
 
-using IO = SpinorIO<WL_F64>;
+// complex scalar of the vector arithmetic type
+template <typename R>
+__device__ __forceinline__ cx<R> cs(double re, double im) { return {Conv<R>::from(re), Conv<R>::from(im)}; }
 
+template <int P>
 __global__ void __launch_bounds__(kBlock) k_m_s(Geom g, int nsb, Vec r, Vec v, Vec s, const BiState *st)
 {
+    using IO = SpinorIO<P>;
+    using R = typename PrecTraits<P>::R;
     const FullIdx f = full_idx(nsb);
     if (__ldcg(&st->done) || f.i >= g.Vh) return;
-    const cx<double> al = {__ldcg(&st->alpha_re), __ldcg(&st->alpha_im)};
-    cx<double> a[12], b[12];
+    const cx<R> al = cs<R>(__ldcg(&st->alpha_re), __ldcg(&st->alpha_im));
+    cx<R> a[12], b[12];
     IO::load(r.rhs(f.half), g.stride, f.i, a);
     IO::load(v.rhs(f.half), g.stride, f.i, b);
 #pragma unroll
@@ -164,27 +171,30 @@ __global__ void __launch_bounds__(kBlock) k_m_s(Geom g, int nsb, Vec r, Vec v, V
 
 // Shift x/q updates, unshifted x += alpha p + omega s, r = s - omega t with
 // <rhat, r> and ||r||^2 -> beta (last block).
+template <int P>
 __global__ void __launch_bounds__(kBlock) k_m_update(Geom g, int nsb, Vec x, Vec p, Vec s, Vec t, Vec r, Vec rhat,
                                                      ShiftVecs sv, const ShiftState *sh, int ns, BiState *st,
                                                      double *partials)
 {
+    using IO = SpinorIO<P>;
+    using R = typename PrecTraits<P>::R;
     const FullIdx f = full_idx(nsb);
     BiState &S = *st;
     if (__ldcg(&S.done)) return;
     double red[3] = {0.0, 0.0, 0.0};
     if (f.i < g.Vh) {
         const int h = f.half, i = f.i, str = g.stride;
-        const cx<double> al = {__ldcg(&S.alpha_re), __ldcg(&S.alpha_im)};
-        const cx<double> om = {__ldcg(&S.omega_re), __ldcg(&S.omega_im)};
-        cx<double> sv_[12], rv[12];
+        const cx<R> al = cs<R>(__ldcg(&S.alpha_re), __ldcg(&S.alpha_im));
+        const cx<R> om = cs<R>(__ldcg(&S.omega_re), __ldcg(&S.omega_im));
+        cx<R> sv_[12], rv[12];
         IO::load(s.rhs(h), str, i, sv_);
         IO::load(r.rhs(h), str, i, rv);
         for (int k = 0; k < ns; ++k) {
             const ShiftState &Q = sh[k];
             if (!Q.active) continue;
-            const cx<double> cxp = {Q.cxp_re, Q.cxp_im}, cxs = {Q.cxs_re, Q.cxs_im};
-            const cx<double> cqr = {Q.cqr_re, Q.cqr_im}, cqs = {Q.cqs_re, Q.cqs_im};
-            cx<double> xs[12], ps[12];
+            const cx<R> cxp = cs<R>(Q.cxp_re, Q.cxp_im), cxs = cs<R>(Q.cxs_re, Q.cxs_im);
+            const cx<R> cqr = cs<R>(Q.cqr_re, Q.cqr_im), cqs = cs<R>(Q.cqs_re, Q.cqs_im);
+            cx<R> xs[12], ps[12];
             IO::load(sv.x[h][k], str, i, xs);
             IO::load(sv.p[h][k], str, i, ps);
 #pragma unroll
@@ -195,7 +205,7 @@ __global__ void __launch_bounds__(kBlock) k_m_update(Geom g, int nsb, Vec x, Vec
             IO::store(sv.x[h][k], str, i, xs);
             IO::store(sv.p[h][k], str, i, ps);
         }
-        cx<double> xv[12], pv[12], tv[12];
+        cx<R> xv[12], pv[12], tv[12];
         IO::load(x.rhs(h), str, i, xv);
         IO::load(p.rhs(h), str, i, pv);
 #pragma unroll
@@ -205,18 +215,18 @@ __global__ void __launch_bounds__(kBlock) k_m_update(Geom g, int nsb, Vec x, Vec
 #pragma unroll
         for (int c = 0; c < 12; ++c) rv[c] = sv_[c] - om * tv[c];
         IO::store(r.rhs(h), str, i, rv);
-        cx<double> rh[12];
+        cx<R> rh[12];
         IO::load(rhat.rhs(h), str, i, rh);
-        cx<double> d = {0.0, 0.0};
-        double n = 0.0;
+        cx<R> d = {R(0), R(0)};
+        R n = R(0);
 #pragma unroll
         for (int c = 0; c < 12; ++c) {
             d = conjmad(rh[c], rv[c], d);
             n = fma(rv[c].re, rv[c].re, fma(rv[c].im, rv[c].im, n));
         }
-        red[0] = d.re;
-        red[1] = d.im;
-        red[2] = n;
+        red[0] = to_double(d.re);
+        red[1] = to_double(d.im);
+        red[2] = to_double(n);
     }
     double tot[3];
     if (grid_sum<3>(red, partials, &S.ticket[2], blockIdx.x, 2 * nsb, tot) && threadIdx.x == 0) {
@@ -251,27 +261,30 @@ __global__ void __launch_bounds__(kBlock) k_m_update(Geom g, int nsb, Vec x, Vec
 }
 
 // p = r + beta (p - omega v);  p^s = r / (pi lambda) + beta^s q^s.
+template <int P>
 __global__ void __launch_bounds__(kBlock) k_m_p(Geom g, int nsb, Vec r, Vec p, Vec v, ShiftVecs sv,
                                                 const ShiftState *sh, int ns, const BiState *st)
 {
+    using IO = SpinorIO<P>;
+    using R = typename PrecTraits<P>::R;
     const FullIdx f = full_idx(nsb);
     if (f.i >= g.Vh || __ldcg(&st->done)) return;
     const int h = f.half, i = f.i, str = g.stride;
-    cx<double> rv[12];
+    cx<R> rv[12];
     IO::load(r.rhs(h), str, i, rv);
     for (int k = 0; k < ns; ++k) {
         const ShiftState &Q = sh[k];
         if (!Q.active) continue;
-        const cx<double> cpr = {Q.cpr_re, Q.cpr_im}, bsg = {Q.bs_re, Q.bs_im};
-        cx<double> ps[12];
+        const cx<R> cpr = cs<R>(Q.cpr_re, Q.cpr_im), bsg = cs<R>(Q.bs_re, Q.bs_im);
+        cx<R> ps[12];
         IO::load(sv.p[h][k], str, i, ps);
 #pragma unroll
         for (int c = 0; c < 12; ++c) ps[c] = cmad(cpr, rv[c], bsg * ps[c]);
         IO::store(sv.p[h][k], str, i, ps);
     }
-    const cx<double> be = {__ldcg(&st->beta_re), __ldcg(&st->beta_im)};
-    const cx<double> om = {__ldcg(&st->omega_re), __ldcg(&st->omega_im)};
-    cx<double> pv[12], vv[12];
+    const cx<R> be = cs<R>(__ldcg(&st->beta_re), __ldcg(&st->beta_im));
+    const cx<R> om = cs<R>(__ldcg(&st->omega_re), __ldcg(&st->omega_im));
+    cx<R> pv[12], vv[12];
     IO::load(p.rhs(h), str, i, pv);
     IO::load(v.rhs(h), str, i, vv);
 #pragma unroll
@@ -330,7 +343,13 @@ extern "C" int bicgstab_m_solve(wl_gauge *g, const void *b, void *const *x, cons
         return WL_ERR_ARG;
     }
     if (!(p->tol > 0) || p->max_iter < 1) { set_error("bicgstab_m_solve: bad parameters"); return WL_ERR_ARG; }
-    if (!(g->prec_mask & WL_F64)) { set_error("bicgstab_m_solve: needs FP64 links"); return WL_ERR_ARG; }
+    // vectors and hops in FP64 or double-float (outer_prec)
+    const int P = p->outer_prec;
+    if (P != WL_F64 && P != WL_DF) { set_error("bicgstab_m_solve: outer_prec must be FP64 or double-float"); return WL_ERR_ARG; }
+    if (!(g->prec_mask & P)) {
+        set_error(P == WL_DF ? "bicgstab_m_solve: needs double-float links" : "bicgstab_m_solve: needs FP64 links");
+        return WL_ERR_ARG;
+    }
     for (int i = 0; i < n_mass; ++i) {
         if (!x[i]) { set_error("bicgstab_m_solve: NULL solution"); return WL_ERR_ARG; }
         if (!(2.0 * m0[i] + 8.0 > 0.0)) { set_error("bicgstab_m_solve: need 2 m0 + 8 > 0"); return WL_ERR_ARG; }
@@ -348,23 +367,23 @@ extern "C" int bicgstab_m_solve(wl_gauge *g, const void *b, void *const *x, cons
     const double ms = m0[is];
     const int ns = n_mass - 1;
 
-    // full-lattice FP64 vectors: 2 halves each
+    // full-lattice vectors: 2 halves each
     Vec bv, xv, r, rhat, pv, v, sv, t;
-    WL_TRY(make_vec(g, "bm_b", WL_F64, 2, &bv));
-    WL_TRY(make_vec(g, "bm_x", WL_F64, 2, &xv));
-    WL_TRY(make_vec(g, "bm_r", WL_F64, 2, &r));
-    WL_TRY(make_vec(g, "bm_rhat", WL_F64, 2, &rhat));
-    WL_TRY(make_vec(g, "bm_p", WL_F64, 2, &pv));
-    WL_TRY(make_vec(g, "bm_v", WL_F64, 2, &v));
-    WL_TRY(make_vec(g, "bm_s", WL_F64, 2, &sv));
-    WL_TRY(make_vec(g, "bm_t", WL_F64, 2, &t));
+    WL_TRY(make_vec(g, "bm_b", P, 2, &bv));
+    WL_TRY(make_vec(g, "bm_x", P, 2, &xv));
+    WL_TRY(make_vec(g, "bm_r", P, 2, &r));
+    WL_TRY(make_vec(g, "bm_rhat", P, 2, &rhat));
+    WL_TRY(make_vec(g, "bm_p", P, 2, &pv));
+    WL_TRY(make_vec(g, "bm_v", P, 2, &v));
+    WL_TRY(make_vec(g, "bm_s", P, 2, &sv));
+    WL_TRY(make_vec(g, "bm_t", P, 2, &t));
     std::vector<Vec> xs(ns), ps(ns);
     ShiftVecs shv;
     std::vector<int> shift_mass(ns);
     for (int k = 0, i = 0; i < n_mass; ++i) {
         if (i == is) continue;
-        WL_TRY(make_vec(g, "bm_xs" + std::to_string(k), WL_F64, 2, &xs[k]));
-        WL_TRY(make_vec(g, "bm_ps" + std::to_string(k), WL_F64, 2, &ps[k]));
+        WL_TRY(make_vec(g, "bm_xs" + std::to_string(k), P, 2, &xs[k]));
+        WL_TRY(make_vec(g, "bm_ps" + std::to_string(k), P, 2, &ps[k]));
         for (int h = 0; h < 2; ++h) {
             shv.x[h][k] = xs[k].rhs(h);
             shv.p[h][k] = ps[k].rhs(h);
@@ -457,7 +476,8 @@ extern "C" int bicgstab_m_solve(wl_gauge *g, const void *b, void *const *x, cons
         // v = A p, <rhat, v> -> alpha
         WL_TRY(hop_reduce(g, 0, po, pe, a1, ve, rhe, -0.5, nullptr, WL_EVEN, 0, st, partials, 0, 2 * nsb, q));
         WL_TRY(hop_reduce(g, 0, pe, po, a1, vo, rho, -0.5, nullptr, WL_ODD, 0, st, partials, nsb, 2 * nsb, q));
-        k_m_s<<<2 * nsb, kBlock, 0, q>>>(geo, nsb, r, v, sv, st);
+        if (P == WL_DF) k_m_s<WL_DF><<<2 * nsb, kBlock, 0, q>>>(geo, nsb, r, v, sv, st);
+        else k_m_s<WL_F64><<<2 * nsb, kBlock, 0, q>>>(geo, nsb, r, v, sv, st);
         note_launch(q);
         // t = A s, <t,s>, <t,t> -> omega
         WL_TRY(hop_reduce(g, 1, so, se, a1, te, rhe, -0.5, nullptr, WL_EVEN, 0, st, partials, 0, 2 * nsb, q));
@@ -466,9 +486,13 @@ extern "C" int bicgstab_m_solve(wl_gauge *g, const void *b, void *const *x, cons
             k_shift_a<<<1, 32, 0, q>>>(sh, ns, st, mst);
             note_launch(q);
         }
-        k_m_update<<<2 * nsb, kBlock, 0, q>>>(geo, nsb, xv, pv, sv, t, r, rhat, shv, sh, ns, st, partials);
+        if (P == WL_DF)
+            k_m_update<WL_DF><<<2 * nsb, kBlock, 0, q>>>(geo, nsb, xv, pv, sv, t, r, rhat, shv, sh, ns, st, partials);
+        else
+            k_m_update<WL_F64><<<2 * nsb, kBlock, 0, q>>>(geo, nsb, xv, pv, sv, t, r, rhat, shv, sh, ns, st, partials);
         k_shift_b<<<1, 32, 0, q>>>(sh, ns, st, mst);
-        k_m_p<<<2 * nsb, kBlock, 0, q>>>(geo, nsb, r, pv, v, shv, sh, ns, st);
+        if (P == WL_DF) k_m_p<WL_DF><<<2 * nsb, kBlock, 0, q>>>(geo, nsb, r, pv, v, shv, sh, ns, st);
+        else k_m_p<WL_F64><<<2 * nsb, kBlock, 0, q>>>(geo, nsb, r, pv, v, shv, sh, ns, st);
         note_launch(q);
         note_launch(q);
         note_launch(q);
@@ -525,10 +549,11 @@ extern "C" int bicgstab_m_solve(wl_gauge *g, const void *b, void *const *x, cons
     if (ns) WL_CUDA_TRY(cudaMemcpy(hsh.data(), sh, sizeof(ShiftState) * ns, cudaMemcpyDeviceToHost));
     const double unshifted_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
 
-    // outputs in kappa form x_i = (m_i + 4) psi_i, FP64 true residuals; a
-    // mass still above tol is polished by single-mass FP64 BiCGstab.
+    // outputs in kappa form x_i = (m_i + 4) psi_i, true residuals in the
+    // vector precision; a mass still above tol is polished by single-mass
+    // BiCGstab.
     Vec scaled;
-    WL_TRY(make_vec(g, "bm_out", WL_F64, 2, &scaled));
+    WL_TRY(make_vec(g, "bm_out", P, 2, &scaled));
     void *pc;
     WL_TRY(g->ws.get("bm_coef", sizeof(double) * 2, &pc));
     double *d_coef = static_cast<double *>(pc);
@@ -568,8 +593,10 @@ extern "C" int bicgstab_m_solve(wl_gauge *g, const void *b, void *const *x, cons
     for (int i = 0; i < n_mass; ++i) stats[i].seconds = total;
     for (int i : polish) {
         wl_solver_params pp = *p;
-        pp.inner_prec = WL_F64;
-        pp.outer_prec = WL_F64;
+        // FP64 polish where the handle has FP64 links, else FP32 inside
+        // double-float defect correction
+        pp.inner_prec = (g->prec_mask & WL_F64) ? WL_F64 : WL_F32;
+        pp.outer_prec = P;
         pp.eo = 1;
         wl_solver_stats pol;
         const int ps_ = bicgstab_solve(g, b, x[i], m0[i], &pp, &pol, stream);

@@ -101,6 +101,7 @@ static int hop_reduce_k(wl_gauge *g, const Vec &tmp, const Vec &xin, double a1, 
     case WL_F64: st = hop_reduce_launch_prec<WL_F64>(KIND, dagger, a, &e, s); break;
     case WL_F32: st = hop_reduce_launch_prec<WL_F32>(KIND, dagger, a, &e, s); break;
     case WL_F16: st = hop_reduce_launch_prec<WL_F16>(KIND, dagger, a, &e, s); break;
+    case WL_DF: st = hop_reduce_launch_prec<WL_DF>(KIND, dagger, a, &e, s); break;
     default: set_error("hop_reduce: bad precision"); return WL_ERR_ARG;
     }
     WL_TRY(st);

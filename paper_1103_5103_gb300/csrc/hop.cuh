@@ -706,7 +706,15 @@ __device__ __forceinline__ void hop_reduce_body(const HopArgs &a, const EpiReduc
         cx<R> acc[1][12];
 #pragma unroll
         for (int k = 0; k < 12; ++k) acc[0][k] = {R(0), R(0)};
-        hop_accumulate<P, DAG, 1>(a, i, r, acc);
+        if constexpr (P == WL_DF) {
+            // double-float: the rolled transporter loop (the unrolled one
+            // overflows the instruction cache)
+            HopArgs b = a;
+            b.in = static_cast<const char *>(a.in) + (size_t)r * a.rhs_bytes;
+            hop_accumulate_rolled<P, DAG>(b, i, acc[0]);
+        } else {
+            hop_accumulate<P, DAG, 1>(a, i, r, acc);
+        }
         const size_t off = (size_t)r * e.rhs_bytes;
         cx<R> xv[12], o[12];
         SpinorIO<P>::load(static_cast<const char *>(e.xin) + off, a.g.stride, i, xv);
@@ -726,9 +734,9 @@ __device__ __forceinline__ void hop_reduce_body(const HopArgs &a, const EpiReduc
                 d = conjmad(rh[k], o[k], d);
                 n = fma(o[k].re, o[k].re, fma(o[k].im, o[k].im, n));
             }
-            red[0] = (double)d.re;
-            red[1] = (double)d.im;
-            red[2] = (double)n;
+            red[0] = to_double(d.re);
+            red[1] = to_double(d.im);
+            red[2] = to_double(n);
         } else if constexpr (KIND == 1) {
             cx<R> d = {R(0), R(0)};
             R n = R(0);
@@ -737,14 +745,14 @@ __device__ __forceinline__ void hop_reduce_body(const HopArgs &a, const EpiReduc
                 d = conjmad(o[k], xv[k], d);
                 n = fma(o[k].re, o[k].re, fma(o[k].im, o[k].im, n));
             }
-            red[0] = (double)d.re;
-            red[1] = (double)d.im;
-            red[2] = (double)n;
+            red[0] = to_double(d.re);
+            red[1] = to_double(d.im);
+            red[2] = to_double(n);
         } else {
             R n = R(0);
 #pragma unroll
             for (int k = 0; k < 12; ++k) n = fma(o[k].re, o[k].re, fma(o[k].im, o[k].im, n));
-            red[2] = (double)n;
+            red[2] = to_double(n);
         }
     }
     double tot[NV];

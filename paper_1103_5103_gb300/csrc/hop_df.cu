@@ -27,9 +27,14 @@ int hop_launch_prec<WL_DF>(int v, int dagger, const HopArgs &a, const EpiStore &
 template <>
 int hop_reduce_launch_prec<WL_DF>(int kind, int dagger, const HopArgs &a, const void *epi, cudaStream_t s)
 {
-    (void)kind; (void)dagger; (void)a; (void)epi; (void)s;
-    set_error("hop_reduce: no double-float solver loop");
-    return WL_ERR_ARG;
+    // double-float BiCGstab-M (kinds 0 and 1 only)
+    switch (kind) {
+    case 0: launch_reduce_kind<WL_DF, 0>(dagger, a, epi, s); break;
+    case 1: launch_reduce_kind<WL_DF, 1>(dagger, a, epi, s); break;
+    default: set_error("hop_reduce: double-float supports kinds 0 and 1"); return WL_ERR_ARG;
+    }
+    WL_CUDA_TRY(cudaGetLastError());
+    return WL_OK;
 }
 
 }  // namespace wl

@@ -14,9 +14,10 @@ placed at the paper's distances m - m_c from it:
   antiperiodic time direction, m_c = cos(pi/T) - 1.
 - `table2_sets` shifts the paper's two sets to a given m_c.
 - `main` solves both sets with the single-mass scheme (zero guess and
-  Lagrange guess) and with FP64 BiCGstab-M, and prints one JSON line per
-  solver with its iterations, seconds and speed-up (the quantities of
-  Table 3).
+  Lagrange guess) and with BiCGstab-M (vectors and hops in double-float
+  and in FP64), and prints one JSON line per set with each solver's
+  iterations, seconds and speed-up over the faster BiCGstab-M (the
+  quantities of Table 3).
 
 python -m paper_1103_5103_gb300.mass_sets [--dims 16x16x16x32] [--eps 0.5] [--sources z2|point]
 """
@@ -136,19 +137,23 @@ def run(dims, eps, seed, kind, inner, repeat=2):
                           "ms_per_iteration": 1e3 * dt / max(1, sum(s["iterations"] for s in st[0])),
                           "max_true_relres": max(s["true_relres"] for s in st[0])}
         xs = [torch.empty_like(bd) for _ in masses]
-        for _ in range(repeat):
-            torch.cuda.synchronize()
-            t = time.perf_counter()
-            stm = api.bicgstab_m_solve(g, bd, xs, masses, api.params(shadow=shadow), check=False)
-            torch.cuda.synchronize()
-            dt = time.perf_counter() - t
-        it_m = max(s["iterations"] for s in stm)
-        res["multi-shift (BiCGstab-M, FP64)"] = {
-            "iterations": it_m, "seconds": dt, "ms_per_iteration": 1e3 * dt / max(1, it_m),
-            "max_true_relres": max(s["true_relres"] for s in stm),
-            "masses_polished": sum(1 for s in stm if s["restarts"] > 0)}
+        t_ms = []
+        for label, outer in (("multi-shift (BiCGstab-M, double-float)", "df"),
+                             ("multi-shift (BiCGstab-M, FP64)", "f64")):
+            for _ in range(repeat):
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                stm = api.bicgstab_m_solve(g, bd, xs, masses, api.params(shadow=shadow, outer_prec=outer),
+                                           check=False)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t
+            it_m = max(s["iterations"] for s in stm)
+            res[label] = {"iterations": it_m, "seconds": dt, "ms_per_iteration": 1e3 * dt / max(1, it_m),
+                          "max_true_relres": max(s["true_relres"] for s in stm),
+                          "masses_polished": sum(1 for s in stm if s["restarts"] > 0)}
+            t_ms.append(dt)
         for label, r in res.items():
-            r["speed_up_vs_multi_shift"] = res["multi-shift (BiCGstab-M, FP64)"]["seconds"] / r["seconds"]
+            r["speed_up_vs_multi_shift"] = min(t_ms) / r["seconds"]
         row = {"dims": "x".join(map(str, dims)), "eps": eps, "source": kind, "inner": inner, "m_c": m_c,
                "m_c_converged": mc_converged, "m_c_products": mc_products, "m_c_seconds": t_mc, "set": name, "masses": masses, "results": res}
         rows.append(row)

@@ -89,13 +89,16 @@ def test_multimass_guess_reduces_iterations(api):
     assert it1 < it0, (it0, it1)
 
 
-def test_bicgstab_m_vs_oracle(api):
+@pytest.mark.parametrize("outer", ["f64", "df"])
+def test_bicgstab_m_vs_oracle(api, outer):
+    """BiCGstab-M with FP64 or double-float vectors and hops against the
+    oracle's FP64 recursion."""
     dims = (4, 4, 4, 8)
-    U, lat, g = _gauge(api, dims, 0.5, 41, precs=("f64",))
+    U, lat, g = _gauge(api, dims, 0.5, 41, precs=(outer,))
     b = synth.z2_source(dims, 42)
     masses = [0.4, 0.25, 0.1, 0.05]
     xs = [torch.empty((lat.volume, 4, 3), dtype=torch.complex128, device="cuda") for _ in masses]
-    stats = api.bicgstab_m_solve(g, _cuda(b), xs, masses, api.params(inner_prec="f64"))
+    stats = api.bicgstab_m_solve(g, _cuda(b), xs, masses, api.params(outer_prec=outer))
     ref, _ = O.bicgstab_m(U, dims, b, masses, tol=1e-12)
     for i, m in enumerate(masses):
         assert stats[i]["true_relres"] <= 1e-10, stats[i]
@@ -212,17 +215,18 @@ def test_f16_inner_with_source_entries_below_float_range(api):
     assert O.true_relres(U, dims, b, x.cpu().numpy(), 0.1) <= 1.02e-10
 
 
-def test_bicgstab_m_point_source_with_gaussian_shadow(api):
+@pytest.mark.parametrize("outer", ["f64", "df"])
+def test_bicgstab_m_point_source_with_gaussian_shadow(api, outer):
     """Point source, shadow residual = Gaussian noise (passed to both sides):
     the shifted solutions match the oracle's, with the same iteration count,
     and no mass needs the single-mass polish."""
     dims = (4, 4, 4, 8)
-    U, lat, g = _gauge(api, dims, 0.5, 43, precs=("f64",))
+    U, lat, g = _gauge(api, dims, 0.5, 43, precs=(outer,))
     b = synth.point_source(dims, 1, 2)
     rh = synth.gaussian_source(dims, seed=44)
     masses = [0.4, 0.2, 0.05]
     xs = [torch.empty((lat.volume, 4, 3), dtype=torch.complex128, device="cuda") for _ in masses]
-    stats = api.bicgstab_m_solve(g, _cuda(b), xs, masses, api.params(shadow=_cuda(rh)))
+    stats = api.bicgstab_m_solve(g, _cuda(b), xs, masses, api.params(shadow=_cuda(rh), outer_prec=outer))
     ref, ost = O.bicgstab_m(U, dims, b, masses, tol=0.5e-10, rhat=rh)
     assert ost["status"] == O.OK
     for i, m in enumerate(masses):
@@ -244,12 +248,26 @@ def test_bicgstab_m_point_source_without_shadow_reports_breakdown(api):
     assert ost["status"] == O.BREAKDOWN
     xs = [torch.empty((lat.volume, 4, 3), dtype=torch.complex128, device="cuda") for _ in masses]
     with pytest.raises(api.WilsonError) as e:
-        api.bicgstab_m_solve(g, _cuda(b), xs, masses, api.params())
+        api.bicgstab_m_solve(g, _cuda(b), xs, masses, api.params(outer_prec="f64"))
     assert e.value.status == api.WL_ERR_BREAKDOWN
-    stats = api.bicgstab_m_solve(g, _cuda(b), xs, masses, api.params(), check=False)
+    stats = api.bicgstab_m_solve(g, _cuda(b), xs, masses, api.params(outer_prec="f64"), check=False)
     for i, m in enumerate(masses):
         assert stats[i]["restarts"] > 0 and stats[i]["true_relres"] <= 1e-10, stats[i]
         assert O.true_relres(U, dims, b, xs[i].cpu().numpy(), m) <= 1.02e-10
+
+
+def test_bicgstab_m_needs_links_of_its_precision(api):
+    """Double-float BiCGstab-M (the default outer_prec) on a handle with
+    FP64 links only, and an inner precision as outer_prec, are argument
+    errors."""
+    dims = (4, 4, 4, 4)
+    U, lat, g = _gauge(api, dims, 0.3, 1, precs=("f64",))
+    b = _cuda(synth.z2_source(dims, 2))
+    xs = [torch.empty_like(b) for _ in range(2)]
+    for prm in (api.params(), api.params(outer_prec="f32")):
+        with pytest.raises(api.WilsonError) as e:
+            api.bicgstab_m_solve(g, b, xs, [0.3, 0.1], prm)
+        assert e.value.status == api.WL_ERR_ARG
 
 
 @pytest.mark.parametrize("guess,guess_max", [("poly", 0), ("poly", 2), ("ssm", 0), ("ssm", 2)])
