@@ -11,6 +11,9 @@
 //   after r_{n+1}, beta_n:   lambda_{n+1} = lambda_n (1 + omega_n sigma)
 //     beta^s = beta_n (pi_n / pi_{n+1})^2
 //     p^s = r_{n+1} / (pi_{n+1} lambda_{n+1}) + beta^s q^s
+// The p^s update is applied lazily: each shift stores q^s, and the next
+// iteration's x/q kernel forms p^s from it and r on the fly (one read and
+// one write of the shift vectors per iteration fewer).
 // The shifted residual is r_{n+1} / (pi_{n+1} lambda_{n+1}); a shift whose
 // residual is below tol ||b|| is frozen (Section 6.1).  The vectors and hops
 // are FP64 or double-float (48-bit significands on the FP32 pipes); the
@@ -153,76 +156,112 @@ __device__ __forceinline__ FullIdx full_idx(int nsb)
 template <typename R>
 __device__ __forceinline__ cx<R> cs(double re, double im) { return {Conv<R>::from(re), Conv<R>::from(im)}; }
 
+// One spin-colour component c of site i (layouts as SpinorIO: FP64 double2
+// [12][stride], double-float float4 [12][stride]).  The vector kernels below
+// stream component by component, so a thread holds a few complex numbers
+// instead of whole spinors per shift, and the kernels run at full occupancy.
+template <int P> struct CompIO;
+template <> struct CompIO<WL_F64> {
+    using R = double;
+    static __device__ __forceinline__ cx<R> ld(const void *base, int stride, int c, int i)
+    {
+        const double2 t = static_cast<const double2 *>(base)[(size_t)c * stride + i];
+        return {t.x, t.y};
+    }
+    static __device__ __forceinline__ void st(void *base, int stride, int c, int i, cx<R> v)
+    {
+        static_cast<double2 *>(base)[(size_t)c * stride + i] = make_double2(v.re, v.im);
+    }
+};
+template <> struct CompIO<WL_DF> {
+    using R = df;
+    static __device__ __forceinline__ cx<R> ld(const void *base, int stride, int c, int i)
+    {
+        const float4 t = static_cast<const float4 *>(base)[(size_t)c * stride + i];
+        return {df(t.x, t.y), df(t.z, t.w)};
+    }
+    static __device__ __forceinline__ void st(void *base, int stride, int c, int i, cx<R> v)
+    {
+        const df re = df_normalize(v.re), im = df_normalize(v.im);
+        static_cast<float4 *>(base)[(size_t)c * stride + i] = make_float4(re.hi, re.lo, im.hi, im.lo);
+    }
+};
+
 template <int P>
 __global__ void __launch_bounds__(kBlock) k_m_s(Geom g, int nsb, Vec r, Vec v, Vec s, const BiState *st)
 {
-    using IO = SpinorIO<P>;
+    using C = CompIO<P>;
     using R = typename PrecTraits<P>::R;
     const FullIdx f = full_idx(nsb);
     if (__ldcg(&st->done) || f.i >= g.Vh) return;
     const cx<R> al = cs<R>(__ldcg(&st->alpha_re), __ldcg(&st->alpha_im));
-    cx<R> a[12], b[12];
-    IO::load(r.rhs(f.half), g.stride, f.i, a);
-    IO::load(v.rhs(f.half), g.stride, f.i, b);
-#pragma unroll
-    for (int k = 0; k < 12; ++k) a[k] = a[k] - al * b[k];
-    IO::store(s.rhs(f.half), g.stride, f.i, a);
+    const int h = f.half, i = f.i, str = g.stride;
+#pragma unroll 4
+    for (int c = 0; c < 12; ++c) C::st(s.rhs(h), str, c, i, C::ld(r.rhs(h), str, c, i) - al * C::ld(v.rhs(h), str, c, i));
 }
 
-// Shift x/q updates, unshifted x += alpha p + omega s, r = s - omega t with
-// <rhat, r> and ||r||^2 -> beta (last block).
+// Shift updates, p^s = cpr r + beta^s q^s (previous iteration's
+// coefficients; cpr = 1, beta^s = 0 at the start), then x^s and q^s;
+// unshifted x += alpha p + omega s, r = s - omega t with <rhat, r> and
+// ||r||^2 -> beta (last block).
 template <int P>
 __global__ void __launch_bounds__(kBlock) k_m_update(Geom g, int nsb, Vec x, Vec p, Vec s, Vec t, Vec r, Vec rhat,
                                                      ShiftVecs sv, const ShiftState *sh, int ns, BiState *st,
                                                      double *partials)
 {
-    using IO = SpinorIO<P>;
+    using C = CompIO<P>;
     using R = typename PrecTraits<P>::R;
+    static_assert(sizeof(cx<R>) == 16, "coefficient staging assumes 16-byte complex scalars");
     const FullIdx f = full_idx(nsb);
     BiState &S = *st;
     if (__ldcg(&S.done)) return;
+    // the active shifts and their six coefficients, staged once per block
+    __shared__ alignas(16) unsigned char sraw[32 * 6 * 16];
+    __shared__ int sact[32];
+    __shared__ int snact;
+    cx<R> *sc = reinterpret_cast<cx<R> *>(sraw);
+    if (threadIdx.x < ns) {
+        const ShiftState &Q = sh[threadIdx.x];
+        cx<R> *q = sc + 6 * threadIdx.x;
+        q[0] = cs<R>(Q.cxp_re, Q.cxp_im);
+        q[1] = cs<R>(Q.cxs_re, Q.cxs_im);
+        q[2] = cs<R>(Q.cqr_re, Q.cqr_im);
+        q[3] = cs<R>(Q.cqs_re, Q.cqs_im);
+        q[4] = cs<R>(Q.cpr_re, Q.cpr_im);
+        q[5] = cs<R>(Q.bs_re, Q.bs_im);
+    }
+    if (threadIdx.x == 0) {
+        int n = 0;
+        for (int k = 0; k < ns; ++k)
+            if (sh[k].active) sact[n++] = k;
+        snact = n;
+    }
+    __syncthreads();
     double red[3] = {0.0, 0.0, 0.0};
     if (f.i < g.Vh) {
-        const int h = f.half, i = f.i, str = g.stride;
+        const int h = f.half, i = f.i, str = g.stride, nact = snact;
         const cx<R> al = cs<R>(__ldcg(&S.alpha_re), __ldcg(&S.alpha_im));
         const cx<R> om = cs<R>(__ldcg(&S.omega_re), __ldcg(&S.omega_im));
-        cx<R> sv_[12], rv[12];
-        IO::load(s.rhs(h), str, i, sv_);
-        IO::load(r.rhs(h), str, i, rv);
-        for (int k = 0; k < ns; ++k) {
-            const ShiftState &Q = sh[k];
-            if (!Q.active) continue;
-            const cx<R> cxp = cs<R>(Q.cxp_re, Q.cxp_im), cxs = cs<R>(Q.cxs_re, Q.cxs_im);
-            const cx<R> cqr = cs<R>(Q.cqr_re, Q.cqr_im), cqs = cs<R>(Q.cqs_re, Q.cqs_im);
-            cx<R> xs[12], ps[12];
-            IO::load(sv.x[h][k], str, i, xs);
-            IO::load(sv.p[h][k], str, i, ps);
-#pragma unroll
-            for (int c = 0; c < 12; ++c) {
-                xs[c] = cmad(cxp, ps[c], cmad(cxs, sv_[c], xs[c]));
-                ps[c] = cmad(cqr, rv[c], cmad(cqs, sv_[c], ps[c]));
-            }
-            IO::store(sv.x[h][k], str, i, xs);
-            IO::store(sv.p[h][k], str, i, ps);
-        }
-        cx<R> xv[12], pv[12], tv[12];
-        IO::load(x.rhs(h), str, i, xv);
-        IO::load(p.rhs(h), str, i, pv);
-#pragma unroll
-        for (int c = 0; c < 12; ++c) xv[c] = cmad(al, pv[c], cmad(om, sv_[c], xv[c]));
-        IO::store(x.rhs(h), str, i, xv);
-        IO::load(t.rhs(h), str, i, tv);
-#pragma unroll
-        for (int c = 0; c < 12; ++c) rv[c] = sv_[c] - om * tv[c];
-        IO::store(r.rhs(h), str, i, rv);
-        cx<R> rh[12];
-        IO::load(rhat.rhs(h), str, i, rh);
         cx<R> d = {R(0), R(0)};
         R n = R(0);
-#pragma unroll
+#pragma unroll 2
         for (int c = 0; c < 12; ++c) {
-            d = conjmad(rh[c], rv[c], d);
-            n = fma(rv[c].re, rv[c].re, fma(rv[c].im, rv[c].im, n));
+            const cx<R> sc_ = C::ld(s.rhs(h), str, c, i), rc = C::ld(r.rhs(h), str, c, i);
+            for (int j = 0; j < nact; ++j) {
+                const int k = sact[j];
+                const cx<R> *q = sc + 6 * k;
+                cx<R> xs = C::ld(sv.x[h][k], str, c, i);
+                const cx<R> ps = C::ld(sv.p[h][k], str, c, i);
+                const cx<R> pc = cmad(q[4], rc, q[5] * ps);
+                xs = cmad(q[0], pc, cmad(q[1], sc_, xs));
+                C::st(sv.x[h][k], str, c, i, xs);
+                C::st(sv.p[h][k], str, c, i, cmad(q[2], rc, cmad(q[3], sc_, pc)));
+            }
+            C::st(x.rhs(h), str, c, i, cmad(al, C::ld(p.rhs(h), str, c, i), cmad(om, sc_, C::ld(x.rhs(h), str, c, i))));
+            const cx<R> rn = sc_ - om * C::ld(t.rhs(h), str, c, i);
+            C::st(r.rhs(h), str, c, i, rn);
+            d = conjmad(C::ld(rhat.rhs(h), str, c, i), rn, d);
+            n = fma(rn.re, rn.re, fma(rn.im, rn.im, n));
         }
         red[0] = to_double(d.re);
         red[1] = to_double(d.im);
@@ -260,36 +299,22 @@ __global__ void __launch_bounds__(kBlock) k_m_update(Geom g, int nsb, Vec x, Vec
     }
 }
 
-// p = r + beta (p - omega v);  p^s = r / (pi lambda) + beta^s q^s.
+// p = r + beta (p - omega v)  (the shifted p^s follow in k_m_update).
 template <int P>
-__global__ void __launch_bounds__(kBlock) k_m_p(Geom g, int nsb, Vec r, Vec p, Vec v, ShiftVecs sv,
-                                                const ShiftState *sh, int ns, const BiState *st)
+__global__ void __launch_bounds__(kBlock) k_m_p(Geom g, int nsb, Vec r, Vec p, Vec v, const BiState *st)
 {
-    using IO = SpinorIO<P>;
+    using C = CompIO<P>;
     using R = typename PrecTraits<P>::R;
     const FullIdx f = full_idx(nsb);
     if (f.i >= g.Vh || __ldcg(&st->done)) return;
     const int h = f.half, i = f.i, str = g.stride;
-    cx<R> rv[12];
-    IO::load(r.rhs(h), str, i, rv);
-    for (int k = 0; k < ns; ++k) {
-        const ShiftState &Q = sh[k];
-        if (!Q.active) continue;
-        const cx<R> cpr = cs<R>(Q.cpr_re, Q.cpr_im), bsg = cs<R>(Q.bs_re, Q.bs_im);
-        cx<R> ps[12];
-        IO::load(sv.p[h][k], str, i, ps);
-#pragma unroll
-        for (int c = 0; c < 12; ++c) ps[c] = cmad(cpr, rv[c], bsg * ps[c]);
-        IO::store(sv.p[h][k], str, i, ps);
-    }
     const cx<R> be = cs<R>(__ldcg(&st->beta_re), __ldcg(&st->beta_im));
     const cx<R> om = cs<R>(__ldcg(&st->omega_re), __ldcg(&st->omega_im));
-    cx<R> pv[12], vv[12];
-    IO::load(p.rhs(h), str, i, pv);
-    IO::load(v.rhs(h), str, i, vv);
-#pragma unroll
-    for (int c = 0; c < 12; ++c) pv[c] = rv[c] + be * (pv[c] - om * vv[c]);
-    IO::store(p.rhs(h), str, i, pv);
+#pragma unroll 4
+    for (int c = 0; c < 12; ++c) {
+        const cx<R> pv = C::ld(p.rhs(h), str, c, i), vv = C::ld(v.rhs(h), str, c, i);
+        C::st(p.rhs(h), str, c, i, C::ld(r.rhs(h), str, c, i) + be * (pv - om * vv));
+    }
 }
 
 // Sums over n complex entries of canonical arrays: out = {Re <a, b>, Im <a, b>, ||a||^2}.
@@ -452,6 +477,7 @@ extern "C" int bicgstab_m_solve(wl_gauge *g, const void *b, void *const *x, cons
         std::memset(&hsh[k], 0, sizeof(ShiftState));
         hsh[k].sigma = m0[shift_mass[k]] - ms;
         hsh[k].pim_re = hsh[k].pi_re = hsh[k].lam_re = 1.0;
+        hsh[k].cpr_re = 1.0;   // p^s_0 = r_0 = b (with beta^s = 0 and q^s = b stored)
         hsh[k].active = 1;
         hsh[k].frozen_at = -1;
     }
@@ -491,8 +517,8 @@ extern "C" int bicgstab_m_solve(wl_gauge *g, const void *b, void *const *x, cons
         else
             k_m_update<WL_F64><<<2 * nsb, kBlock, 0, q>>>(geo, nsb, xv, pv, sv, t, r, rhat, shv, sh, ns, st, partials);
         k_shift_b<<<1, 32, 0, q>>>(sh, ns, st, mst);
-        if (P == WL_DF) k_m_p<WL_DF><<<2 * nsb, kBlock, 0, q>>>(geo, nsb, r, pv, v, shv, sh, ns, st);
-        else k_m_p<WL_F64><<<2 * nsb, kBlock, 0, q>>>(geo, nsb, r, pv, v, shv, sh, ns, st);
+        if (P == WL_DF) k_m_p<WL_DF><<<2 * nsb, kBlock, 0, q>>>(geo, nsb, r, pv, v, st);
+        else k_m_p<WL_F64><<<2 * nsb, kBlock, 0, q>>>(geo, nsb, r, pv, v, st);
         note_launch(q);
         note_launch(q);
         note_launch(q);
