@@ -289,8 +289,10 @@ int bicgstab_m_solve(wl_gauge *g, const void *b, void *const *x, const double *m
  * check confirms convergence.  b[r] (r < n_rhs) are canonical
  * sources; x[r * n_mass + i] receives the solution for source r and mass
  * m0[i]; stats[r * n_mass + i] its statistics.  All right-hand sides of one
- * mass are solved together by batched kernels.  Masses must be distinct.
- * Synchronises the stream. */
+ * mass are solved together by batched kernels.  The solutions of a
+ * finished mass are written to x on an internal stream while the next mass
+ * is solved; every write is complete when the call returns.  Masses must be
+ * distinct.  Synchronises the stream. */
 int multimass_solve(wl_gauge *g, const void *const *b, void *const *x, int n_rhs, const double *m0,
                     int n_mass, const wl_solver_params *p, wl_solver_stats *stats, void *stream);
 

@@ -94,7 +94,9 @@ int import_spinors(const Geom &g, const void *const *canon, const Vec &out, int 
 int export_spinors(const Geom &g, const Vec &in, void *const *canon, int parity, cudaStream_t s);
 // Both parities in one pass, with whole-line canonical accesses.
 int import_full(const Geom &g, const void *const *canon, const Vec &even, const Vec &odd, cudaStream_t s);
-int export_full(const Geom &g, const Vec &even, const Vec &odd, void *const *canon, cudaStream_t s);
+// max_blocks > 0: at most that many blocks, each looping over tiles.
+int export_full(const Geom &g, const Vec &even, const Vec &odd, void *const *canon, cudaStream_t s,
+                int max_blocks = 0);
 
 // ---- dslash.cu
 // out[r] = a1 * x1[r] + a2 * x2[r] + coef * D_{p,1-p} in[r] for r < nrhs (x1, x2

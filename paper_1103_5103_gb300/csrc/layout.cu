@@ -116,22 +116,28 @@ __global__ void __launch_bounds__(kFullSites) k_export_full(Geom g, const void *
 {
     __shared__ double2 sm[12 * (kFullSites + 1)];
     const size_t V = (size_t)g.Vh * 2;
-    const size_t n0 = (size_t)blockIdx.x * kFullSites;
-    const size_t n = n0 + threadIdx.x;
-    if (n < V) {
-        using R = typename PrecTraits<P>::R;
-        cx<R> v[12];
-        SpinorIO<P>::load(lex_parity(g, n) ? odd : even, g.stride, (int)(n >> 1), v);
+    const size_t ntiles = (V + kFullSites - 1) / kFullSites;
+    // tiles strided by the grid: a reduced grid (the overlapped export of
+    // the multi-mass solver) occupies a few SMs while other work runs
+    for (size_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const size_t n0 = tile * kFullSites;
+        const size_t n = n0 + threadIdx.x;
+        if (n < V) {
+            using R = typename PrecTraits<P>::R;
+            cx<R> v[12];
+            SpinorIO<P>::load(lex_parity(g, n) ? odd : even, g.stride, (int)(n >> 1), v);
 #pragma unroll
-        for (int k = 0; k < 12; ++k)
-            sm[k * (kFullSites + 1) + threadIdx.x] = make_double2(to_double(v[k].re), to_double(v[k].im));
-    }
-    __syncthreads();
-    const size_t e0 = n0 * 12, e_end = V * 12;
+            for (int k = 0; k < 12; ++k)
+                sm[k * (kFullSites + 1) + threadIdx.x] = make_double2(to_double(v[k].re), to_double(v[k].im));
+        }
+        __syncthreads();
+        const size_t e0 = n0 * 12, e_end = V * 12;
 #pragma unroll
-    for (int j = 0; j < 12; ++j) {
-        const int e = j * kFullSites + threadIdx.x;
-        if (e0 + e < e_end) canon[e0 + e] = sm[(e % 12) * (kFullSites + 1) + e / 12];
+        for (int j = 0; j < 12; ++j) {
+            const int e = j * kFullSites + threadIdx.x;
+            if (e0 + e < e_end) canon[e0 + e] = sm[(e % 12) * (kFullSites + 1) + e / 12];
+        }
+        __syncthreads();   // sm is refilled by the next tile
     }
 }
 
@@ -233,9 +239,10 @@ static int launch_export(const Geom &g, const void *in, void *canon, int parity,
 
 template <int P>
 static int launch_full(const Geom &g, const void *canon_in, void *canon_out, const void *even_in, const void *odd_in,
-                       void *even_out, void *odd_out, cudaStream_t s)
+                       void *even_out, void *odd_out, cudaStream_t s, int max_blocks = 0)
 {
-    const unsigned bl = (unsigned)(((size_t)g.Vh * 2 + kFullSites - 1) / kFullSites);
+    unsigned bl = (unsigned)(((size_t)g.Vh * 2 + kFullSites - 1) / kFullSites);
+    if (max_blocks > 0 && canon_out && bl > (unsigned)max_blocks) bl = (unsigned)max_blocks;
     if (canon_out)
         k_export_full<P><<<bl, kFullSites, 0, s>>>(g, even_in, odd_in, static_cast<double2 *>(canon_out));
     else
@@ -245,15 +252,16 @@ static int launch_full(const Geom &g, const void *canon_in, void *canon_out, con
     return WL_OK;
 }
 
-int export_full(const Geom &g, const Vec &even, const Vec &odd, void *const *canon, cudaStream_t s)
+int export_full(const Geom &g, const Vec &even, const Vec &odd, void *const *canon, cudaStream_t s, int max_blocks)
 {
     if (even.prec != odd.prec || even.nrhs != odd.nrhs) { set_error("export_full: parity mismatch"); return WL_ERR_ARG; }
     for (int r = 0; r < even.nrhs; ++r) {
         const void *e = even.rhs(r), *o = odd.rhs(r);
-        int st = even.prec == WL_F64   ? launch_full<WL_F64>(g, nullptr, canon[r], e, o, nullptr, nullptr, s)
-                 : even.prec == WL_F32 ? launch_full<WL_F32>(g, nullptr, canon[r], e, o, nullptr, nullptr, s)
-                 : even.prec == WL_DF  ? launch_full<WL_DF>(g, nullptr, canon[r], e, o, nullptr, nullptr, s)
-                                       : launch_full<WL_F16>(g, nullptr, canon[r], e, o, nullptr, nullptr, s);
+        const int mb = max_blocks;
+        int st = even.prec == WL_F64   ? launch_full<WL_F64>(g, nullptr, canon[r], e, o, nullptr, nullptr, s, mb)
+                 : even.prec == WL_F32 ? launch_full<WL_F32>(g, nullptr, canon[r], e, o, nullptr, nullptr, s, mb)
+                 : even.prec == WL_DF  ? launch_full<WL_DF>(g, nullptr, canon[r], e, o, nullptr, nullptr, s, mb)
+                                       : launch_full<WL_F16>(g, nullptr, canon[r], e, o, nullptr, nullptr, s, mb);
         WL_TRY(st);
     }
     return WL_OK;

@@ -531,19 +531,64 @@ int full_relres(wl_gauge *g, const Vec &be, const Vec &bo, const Vec &xe, const 
     return WL_OK;
 }
 
+// Exports of finished masses on a side stream, overlapped with the solve of
+// the next mass (the canonical solutions may be page-locked host memory,
+// written at the host link's rate).  The side stream has the highest
+// priority and the export a grid of kExportBlocks looping blocks, so it
+// starts as soon as a few SM slots free up and then streams on them while
+// the solver's kernels fill the rest.  The odd halves x_o alternate between
+// two buffers; a mass waits for the export of the mass two before it ahead
+// of overwriting one.  Destruction waits for every export.
+constexpr int kExportBlocks = 152;
+struct AsyncExport {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ready[2] = {nullptr, nullptr}, done[2] = {nullptr, nullptr};
+    bool pending[2] = {false, false};
+    int slot = 0;
+    int init()
+    {
+        int lo = 0, hi = 0;
+        WL_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+        WL_CUDA_TRY(cudaStreamCreateWithPriority(&stream, cudaStreamNonBlocking, hi));
+        for (int k = 0; k < 2; ++k) {
+            WL_CUDA_TRY(cudaEventCreateWithFlags(&ready[k], cudaEventDisableTiming));
+            WL_CUDA_TRY(cudaEventCreateWithFlags(&done[k], cudaEventDisableTiming));
+        }
+        return WL_OK;
+    }
+    // order everything after the last export on s
+    int join(cudaStream_t s)
+    {
+        for (int k = 0; k < 2; ++k)
+            if (pending[k]) WL_CUDA_TRY(cudaStreamWaitEvent(s, done[k], 0));
+        return WL_OK;
+    }
+    ~AsyncExport()
+    {
+        if (stream) cudaStreamSynchronize(stream);
+        for (int k = 0; k < 2; ++k) {
+            if (ready[k]) cudaEventDestroy(ready[k]);
+            if (done[k]) cudaEventDestroy(done[k]);
+        }
+        if (stream) cudaStreamDestroy(stream);
+    }
+};
+
 // One mass for nrhs sources already imported as be, bo (outer precision),
 // with bprec = b_e + kappa D_eo b_o prepared by the caller: solve, rebuild
-// x_o = b_o + kappa D_oe x_e, compute the full-lattice residual, export x.
+// x_o = b_o + kappa D_oe x_e, compute the full-lattice residual, export x
+// (on s, or on the side stream of ax).
 static int solve_one_mass(wl_gauge *g, const Vec &be, const Vec &bo, const Vec &bprec, const Vec &xe, double m0,
                           const wl_solver_params &prm, const std::vector<double> &bnorm2, void *const *x_out,
                           int x_out_stride, std::vector<wl_solver_stats> &stats, cudaStream_t s,
-                          const Vec *y_out = nullptr, bool r0_given = false)
+                          const Vec *y_out = nullptr, bool r0_given = false, AsyncExport *ax = nullptr)
 {
     const Geom &geo = g->lat->geom;
     const int nrhs = be.nrhs;
     const double kappa = 1.0 / (2.0 * m0 + 8.0);
+    const int slot = ax ? ax->slot : 0;
     Vec xo;
-    WL_TRY(make_vec(g, "mm_xo", xe.prec, nrhs, &xo));
+    WL_TRY(make_vec(g, ax ? (slot ? "mm_xo1" : "mm_xo0") : "mm_xo", xe.prec, nrhs, &xo));
     std::vector<double> bnorm(nrhs);
     for (int r = 0; r < nrhs; ++r) bnorm[r] = std::sqrt(bnorm2[r]);
     WL_TRY(eo_defect_correction(g, bprec, xe, kappa, prm, bnorm, stats, s, y_out, r0_given));
@@ -553,6 +598,7 @@ static int solve_one_mass(wl_gauge *g, const Vec &be, const Vec &bo, const Vec &
     WL_TRY(make_vec(g, "dc_tmp64", xe.prec, nrhs, &dx));
     Scratch sc;
     WL_TRY(get_scratch(g, nrhs, &sc, s));
+    if (ax && ax->pending[slot]) WL_CUDA_TRY(cudaStreamWaitEvent(s, ax->done[slot], 0));
     WL_TRY(blas_recon(geo, bo, dx, kappa, xo, sc.norms, sc.partials, sc.tickets, s));
     std::vector<double> ro2(nrhs);
     WL_CUDA_TRY(cudaMemcpyAsync(ro2.data(), sc.norms, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
@@ -565,7 +611,13 @@ static int solve_one_mass(wl_gauge *g, const Vec &be, const Vec &bo, const Vec &
         stats[r].true_relres = rel[r];
         outs[r] = x_out[(size_t)r * x_out_stride];
     }
-    WL_TRY(export_full(geo, xe, xo, outs.data(), s));
+    if (!ax) return export_full(geo, xe, xo, outs.data(), s);
+    WL_CUDA_TRY(cudaEventRecord(ax->ready[slot], s));
+    WL_CUDA_TRY(cudaStreamWaitEvent(ax->stream, ax->ready[slot], 0));
+    WL_TRY(export_full(geo, xe, xo, outs.data(), ax->stream, kExportBlocks));
+    WL_CUDA_TRY(cudaEventRecord(ax->done[slot], ax->stream));
+    ax->pending[slot] = true;
+    ax->slot ^= 1;
     return WL_OK;
 }
 
@@ -797,6 +849,8 @@ extern "C" int multimass_solve(wl_gauge *g, const void *const *b, void *const *x
         WL_TRY(g->ws.get("ssm_dots", sizeof(double) * 2 * 16 * n_rhs, &pp));
         ssm_dots = static_cast<double *>(pp);
     }
+    AsyncExport ax;
+    WL_TRY(ax.init());
     int worst = WL_OK;
     for (int k = 0; k < n_mass; ++k) {
         Timer tm;
@@ -871,8 +925,10 @@ extern "C" int multimass_solve(wl_gauge *g, const void *const *b, void *const *x
             WL_TRY(blas_lincomb2(geo, sc.coef, ins.data(), kk, &sol[k], sc.coef + 32 * n_rhs, ni, &r0, s, ssm));
         }
         for (int r = 0; r < n_rhs; ++r) std::memset(&st[r], 0, sizeof(wl_solver_stats));
-        WL_TRY(solve_one_mass(g, be, bo, bprec, sol[k], m, *p, bn2, x + im, n_mass, st, s, &ys[k], true));
+        WL_TRY(solve_one_mass(g, be, bo, bprec, sol[k], m, *p, bn2, x + im, n_mass, st, s, &ys[k], true, &ax));
         if (p->guess == WL_GUESS_SSM && k + 1 < n_mass) {
+            // the Gram products read the canonical solutions: wait for their export
+            WL_TRY(ax.join(s));
             // Gram data of the new solution x_k for later masses:
             // <b, x_k> and <x_j, x_k>, j <= k, on the canonical outputs
             const int n = k + 2;
@@ -904,5 +960,7 @@ extern "C" int multimass_solve(wl_gauge *g, const void *const *b, void *const *x
             if (st[r].status != WL_OK) worst = st[r].status;
         }
     }
+    WL_TRY(ax.join(s));
+    WL_CUDA_TRY(cudaStreamSynchronize(s));
     return worst;
 }
