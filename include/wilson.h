@@ -181,8 +181,11 @@ int wl_spinor_export(const wl_lattice *lat, const void *internal, void *canon_c1
 /* Pack canonical complex128 links (device, [4][V][3][3]) into the internal
  * 12-real per-parity layout (Section 4, Eq. 8, compressed to two rows) for
  * every precision set in prec_mask (WL_F64 | WL_F32 | WL_F16).  The links
- * must be SU(3) to rounding.  The gauge handle keeps a reference to lat,
- * which must outlive it.  Synchronises the stream before returning. */
+ * must be SU(3): the 12-real formats rebuild the third row from the first
+ * two.  Links whose U U^dag - 1 or det U - 1 has an entry (real or
+ * imaginary part) above 1e-6 in magnitude, or a NaN, are rejected with
+ * WL_ERR_ARG.  The gauge handle keeps a reference to lat, which must
+ * outlive it.  Synchronises the stream before returning. */
 int wl_gauge_create(wl_lattice *lat, const void *U_canon_c128, unsigned prec_mask, void *stream,
                     wl_gauge **out);
 int wl_gauge_destroy(wl_gauge *g);

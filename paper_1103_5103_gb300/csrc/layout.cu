@@ -410,6 +410,73 @@ extern "C" int wl_spinor_export(const wl_lattice *lat, const void *internal, voi
     return export_spinors(lat->geom, v, c, parity, as_stream(stream));
 }
 
+// Largest deviation of the canonical links from SU(3): max over links of
+// the entries of |U U^dag - 1| and of |det U - 1| (each as max(|re|, |im|)).
+// A NaN counts as +inf.  Blocks combine with an atomic max on the bit
+// pattern, which orders non-negative doubles (and +inf) like their values.
+static __device__ __forceinline__ void dev_max(double &m, double v)
+{
+    if (!(v <= m)) m = (v != v) ? INFINITY : v;
+}
+
+static __global__ void k_su3_deviation(const double2 *__restrict__ U, size_t nlinks, unsigned long long *out)
+{
+    double m = 0.0;
+    for (size_t l = (size_t)blockIdx.x * blockDim.x + threadIdx.x; l < nlinks; l += (size_t)gridDim.x * blockDim.x) {
+        cx<double> u[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const double2 t = U[l * 9 + k];
+            u[k] = {t.x, t.y};
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = a; b < 3; ++b) {
+                cx<double> s = {a == b ? -1.0 : 0.0, 0.0};
+#pragma unroll
+                for (int c = 0; c < 3; ++c) s = conjmad(u[3 * b + c], u[3 * a + c], s);  // (U U^dag)_ab - delta_ab
+                dev_max(m, fabs(s.re));
+                dev_max(m, fabs(s.im));
+            }
+        const cx<double> det = u[0] * (u[4] * u[8] - u[5] * u[7]) - u[1] * (u[3] * u[8] - u[5] * u[6]) +
+                               u[2] * (u[3] * u[7] - u[4] * u[6]);
+        dev_max(m, fabs(det.re - 1.0));
+        dev_max(m, fabs(det.im));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dev_max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+// Links further than this from SU(3) are rejected: the 12-real formats
+// rebuild the third row as conj(row 0 x row 1), which is the link only for
+// SU(3) matrices.
+constexpr double kSU3Tol = 1e-6;
+
+static int su3_deviation(const Geom &geo, const void *U, double *dev, cudaStream_t s)
+{
+    unsigned long long *d = nullptr, h = 0;
+    WL_CUDA_TRY(cudaMalloc(&d, sizeof(unsigned long long)));
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) {
+        const size_t nlinks = (size_t)4 * geo.Vh * 2;
+        const unsigned grid = (unsigned)std::min<size_t>((nlinks + 255) / 256, 152 * 8);
+        k_su3_deviation<<<grid, 256, 0, s>>>(static_cast<const double2 *>(U), nlinks, d);
+        note_launch(s);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d);
+    if (e != cudaSuccess) {
+        set_error(std::string("wl_gauge_create: ") + cudaGetErrorString(e));
+        return WL_ERR_CUDA;
+    }
+    std::memcpy(dev, &h, sizeof(double));
+    return WL_OK;
+}
+
 extern "C" int wl_gauge_create(wl_lattice *lat, const void *U, unsigned prec_mask, void *stream, wl_gauge **out)
 {
     if (!lat || !U || !out || !(prec_mask & (WL_F64 | WL_F32 | WL_F16 | WL_DF)) || (prec_mask & ~15u)) {
@@ -417,6 +484,17 @@ extern "C" int wl_gauge_create(wl_lattice *lat, const void *U, unsigned prec_mas
         return WL_ERR_ARG;
     }
     cudaStream_t s = as_stream(stream);
+    {
+        double dev = 0.0;
+        WL_TRY(su3_deviation(lat->geom, U, &dev, s));
+        if (!(dev <= kSU3Tol)) {
+            char msg[160];
+            std::snprintf(msg, sizeof(msg), "wl_gauge_create: links are not SU(3) (largest deviation %.3g > %.0e)",
+                          dev, kSU3Tol);
+            set_error(msg);
+            return WL_ERR_ARG;
+        }
+    }
     wl_gauge *g = new wl_gauge;
     g->lat = lat;
     g->prec_mask = prec_mask;

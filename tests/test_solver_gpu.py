@@ -443,3 +443,51 @@ def test_multimass_mass_count_edges(api):
     with pytest.raises(api.WilsonError) as e:
         api.multimass_solve(g, [_cuda(b)], masses + [0.9])
     assert e.value.status == api.WL_ERR_ARG
+
+
+def test_gauge_create_rejects_links_off_su3(api):
+    """The 12-real formats rebuild the third row of a link from the first
+    two, so links off SU(3) are refused: a link scaled by 1.001 (not
+    unitary), a U(3) link (det = e^{0.3 i}) and a NaN entry each give
+    WL_ERR_ARG; a perturbation at 1e-9 (rounding of stored links) is
+    accepted."""
+    dims = (4, 4, 4, 4)
+    U = synth.gauge_field(dims, 0.5, seed=5)
+    lat = api.Lattice(dims)
+    bad = []
+    for k in range(3):
+        B = U.copy()
+        if k == 0:
+            B[1, 17] *= 1.001
+        elif k == 1:
+            B[2, 40] *= np.exp(0.1j)
+        else:
+            B[3, 9, 1, 2] = complex(float("nan"), 0.0)
+        bad.append(B)
+    for B in bad:
+        with pytest.raises(api.WilsonError) as e:
+            api.Gauge(lat, _cuda(B), precs=("f32",))
+        assert e.value.status == api.WL_ERR_ARG
+    ok = U + 1e-9 * synth.gauge_field(dims, 0.5, seed=6)
+    g = api.Gauge(lat, _cuda(ok), precs=("f32",))
+    g.close()
+
+
+def test_nan_source_breaks_down_alone(api):
+    """A source with a NaN entry, batched with a good one: its masses report
+    WL_ERR_BREAKDOWN (non-finite residual) while the good source converges
+    to 1e-10 at every mass, the same as solved alone."""
+    dims = (4, 4, 4, 8)
+    U, lat, g = _gauge(api, dims, 0.5, 7, precs=("f64", "f32", "df"))
+    good = synth.z2_source(dims, 8)
+    nan = synth.z2_source(dims, 9)
+    nan[5, 2, 1] = complex(float("nan"), 1.0)
+    masses = [0.4, 0.2, 0.1]
+    xs, st = api.multimass_solve(g, [_cuda(good), _cuda(nan)], masses, api.params(), check=False)
+    for i, m in enumerate(masses):
+        assert st[1][i]["status"] == api.WL_ERR_BREAKDOWN, st[1][i]
+        assert st[0][i]["status"] == api.WL_OK and st[0][i]["true_relres"] <= 1e-10, st[0][i]
+        assert O.true_relres(U, dims, good, xs[0][i].cpu().numpy(), m) <= 1.02e-10
+    with pytest.raises(api.WilsonError) as e:
+        api.multimass_solve(g, [_cuda(nan)], masses, api.params())
+    assert e.value.status == api.WL_ERR_BREAKDOWN
