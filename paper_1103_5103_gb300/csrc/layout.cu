@@ -457,11 +457,14 @@ constexpr double kSU3Tol = 1e-6;
 static int su3_deviation(const Geom &geo, const void *U, double *dev, cudaStream_t s)
 {
     unsigned long long *d = nullptr, h = 0;
+    int dev_id = 0, nsm = 0;
+    WL_CUDA_TRY(cudaGetDevice(&dev_id));
+    WL_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev_id));
     WL_CUDA_TRY(cudaMalloc(&d, sizeof(unsigned long long)));
     cudaError_t e = cudaMemsetAsync(d, 0, sizeof(unsigned long long), s);
     if (e == cudaSuccess) {
         const size_t nlinks = (size_t)4 * geo.Vh * 2;
-        const unsigned grid = (unsigned)std::min<size_t>((nlinks + 255) / 256, 152 * 8);
+        const unsigned grid = (unsigned)std::min<size_t>((nlinks + 255) / 256, (size_t)nsm * 8);
         k_su3_deviation<<<grid, 256, 0, s>>>(static_cast<const double2 *>(U), nlinks, d);
         note_launch(s);
         e = cudaGetLastError();

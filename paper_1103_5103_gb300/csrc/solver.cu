@@ -534,19 +534,22 @@ int full_relres(wl_gauge *g, const Vec &be, const Vec &bo, const Vec &xe, const 
 // Exports of finished masses on a side stream, overlapped with the solve of
 // the next mass (the canonical solutions may be page-locked host memory,
 // written at the host link's rate).  The side stream has the highest
-// priority and the export a grid of kExportBlocks looping blocks, so it
-// starts as soon as a few SM slots free up and then streams on them while
-// the solver's kernels fill the rest.  The odd halves x_o alternate between
+// priority and the export a grid of one looping block per SM, so it starts
+// as soon as a few SM slots free up and then streams on them while the
+// solver's kernels fill the rest.  The odd halves x_o alternate between
 // two buffers; a mass waits for the export of the mass two before it ahead
 // of overwriting one.  Destruction waits for every export.
-constexpr int kExportBlocks = 152;
 struct AsyncExport {
     cudaStream_t stream = nullptr;
     cudaEvent_t ready[2] = {nullptr, nullptr}, done[2] = {nullptr, nullptr};
     bool pending[2] = {false, false};
     int slot = 0;
+    int blocks = 0;   // export grid: the SM count
     int init()
     {
+        int dev = 0;
+        WL_CUDA_TRY(cudaGetDevice(&dev));
+        WL_CUDA_TRY(cudaDeviceGetAttribute(&blocks, cudaDevAttrMultiProcessorCount, dev));
         int lo = 0, hi = 0;
         WL_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
         WL_CUDA_TRY(cudaStreamCreateWithPriority(&stream, cudaStreamNonBlocking, hi));
@@ -614,7 +617,7 @@ static int solve_one_mass(wl_gauge *g, const Vec &be, const Vec &bo, const Vec &
     if (!ax) return export_full(geo, xe, xo, outs.data(), s);
     WL_CUDA_TRY(cudaEventRecord(ax->ready[slot], s));
     WL_CUDA_TRY(cudaStreamWaitEvent(ax->stream, ax->ready[slot], 0));
-    WL_TRY(export_full(geo, xe, xo, outs.data(), ax->stream, kExportBlocks));
+    WL_TRY(export_full(geo, xe, xo, outs.data(), ax->stream, ax->blocks));
     WL_CUDA_TRY(cudaEventRecord(ax->done[slot], ax->stream));
     ax->pending[slot] = true;
     ax->slot ^= 1;
