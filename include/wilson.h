@@ -270,8 +270,9 @@ int bicgstab_solve(wl_gauge *g, const void *b, void *x, double m0, const wl_solv
  * kappa-form solution (m0[i] + 4) psi_i as a canonical complex128 vector.
  * A shift whose true residual is still above tol afterwards is polished by
  * a single-mass BiCGstab from x[i] (FP64 inner where the handle has FP64
- * links, else FP32 inner and outer_prec outer); its extra iterations are
- * counted in stats[i].restarts.  The shadow residual is p->shadow (NULL: b).
+ * links, else FP32 inner and outer_prec outer, which needs FP32 links: a
+ * polish that finds neither returns WL_ERR_ARG in stats[i].status); its
+ * extra iterations are counted in stats[i].restarts.  The shadow residual is p->shadow (NULL: b).
  * Returns WL_ERR_BREAKDOWN, with the polished solutions in x, when the
  * shifted recurrences broke down.  Masses must be distinct.  Synchronises
  * the stream. */
