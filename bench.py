@@ -3,14 +3,20 @@
 hop (dslash) kernel's HBM bandwidth against the measured GB300 copy peak.
 
 One step = the paper's single-mass multi-mass scheme (even-odd
-preconditioning, FP64 defect correction around a reduced-precision
-BiCGstab, Lagrange initial guesses, masses heaviest first) for every source
-of the workload, all sources batched in one multimass_solve call.
+preconditioning, double-float (FP64-class) defect correction around a
+reduced-precision BiCGstab, Lagrange initial guesses, masses heaviest
+first) for every source of the workload, all sources batched in one
+multimass_solve call.  The line also carries the end-to-end time through
+the public API with host inputs and outputs, the hop roofline, the FP64
+oracle's time on one host core, and the multi-shift BiCGstab-M baseline
+(double-float and FP64) on the same sources and masses.
 
 Default workload (--config c3): 24^3 x 64 lattice, synthetic SU(3) links
 exp(i 0.5 H), antiperiodic in time, 12 spin-colour point sources at site 0,
 8 masses m0 = 0.40 .. 0.05.  --config c2 selects 16^3 x 32, eps 0.5, one Z2
-source, the same 8 masses (its working set fits in the 129 MB L2).
+source, the same 8 masses (its working set fits in the 129 MB L2);
+--config c5 selects 48^3 x 96, eps 0.7, 12 point sources, 16 masses
+0.5 * 0.04^(i/15), FP16 inner.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 For N > 1 launch with torch.distributed.run; every rank solves its own
