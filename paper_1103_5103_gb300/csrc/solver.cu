@@ -852,8 +852,11 @@ extern "C" int multimass_solve(wl_gauge *g, const void *const *b, void *const *x
         WL_TRY(g->ws.get("ssm_dots", sizeof(double) * 2 * 16 * n_rhs, &pp));
         ssm_dots = static_cast<double *>(pp);
     }
+    // overlapped exports, except next to the persistent solver's cooperative
+    // launch (all its blocks must be resident; nothing else shares the GPU)
     AsyncExport ax;
-    WL_TRY(ax.init());
+    AsyncExport *axp = p->mode == WL_MODE_PERSISTENT ? nullptr : &ax;
+    if (axp) WL_TRY(ax.init());
     int worst = WL_OK;
     for (int k = 0; k < n_mass; ++k) {
         Timer tm;
@@ -928,7 +931,7 @@ extern "C" int multimass_solve(wl_gauge *g, const void *const *b, void *const *x
             WL_TRY(blas_lincomb2(geo, sc.coef, ins.data(), kk, &sol[k], sc.coef + 32 * n_rhs, ni, &r0, s, ssm));
         }
         for (int r = 0; r < n_rhs; ++r) std::memset(&st[r], 0, sizeof(wl_solver_stats));
-        WL_TRY(solve_one_mass(g, be, bo, bprec, sol[k], m, *p, bn2, x + im, n_mass, st, s, &ys[k], true, &ax));
+        WL_TRY(solve_one_mass(g, be, bo, bprec, sol[k], m, *p, bn2, x + im, n_mass, st, s, &ys[k], true, axp));
         if (p->guess == WL_GUESS_SSM && k + 1 < n_mass) {
             // the Gram products read the canonical solutions: wait for their export
             WL_TRY(ax.join(s));
