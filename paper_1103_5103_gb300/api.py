@@ -147,8 +147,10 @@ def _canon(t: torch.Tensor, V: int, what: str):
 
 def params(**kw) -> SolverParams:
     """Default solver parameters (wl_params_default) with keyword overrides;
-    inner_prec accepts 'f64' | 'f32' | 'f16'; shadow takes a canonical
-    complex128 CUDA tensor (kept alive by the returned object)."""
+    inner_prec accepts 'f64' | 'f32' | 'f16', outer_prec 'df' | 'f64' (the
+    defect correction's outer loop, and the vectors and hops of
+    bicgstab_m_solve); shadow takes a canonical complex128 CUDA tensor (kept
+    alive by the returned object)."""
     p = SolverParams()
     _check(_lib.wl_params_default(ctypes.byref(p)))
     for k, v in kw.items():
