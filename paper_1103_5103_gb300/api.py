@@ -30,7 +30,7 @@ _PREC_NAMES = {"f64": F64, "f32": F32, "f16": F16, "df": DF}
 
 
 def _prec(p) -> int:
-    """'f64' | 'f32' | 'f16' or the raw WL_F* value (validated by the library)."""
+    """'f64' | 'f32' | 'f16' | 'df' or the raw WL_F* value (validated by the library)."""
     return _PREC_NAMES[p] if isinstance(p, str) else int(p)
 
 
