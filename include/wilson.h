@@ -60,7 +60,8 @@ extern "C" {
 #define WL_ERR_NOCONV    4  /* iteration cap reached; outputs hold the last iterate           */
 #define WL_ERR_BREAKDOWN 5  /* Krylov breakdown that restarts could not cure                  */
 #define WL_ERR_TIMEOUT   6  /* a bounded device wait ran out                                  */
-#define WL_ERR_CHECKED   7  /* a bounds check of a checked build recorded a violation         */
+#define WL_ERR_CHECKED   7  /* reserved for a bounds-checked build (a recorded index
+                               violation); no call of this library returns it            */
 
 /* ------------------------------------------------------------- precisions */
 #define WL_F64 1
