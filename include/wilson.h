@@ -239,9 +239,12 @@ int wilson_dslash_dag(wl_gauge *g, const void *in, void *out, double kappa, int 
  * half-lattice spinors of precision prec exceed 64 MiB are rejected with
  * WL_ERR_ARG.  The first call on a device looks up the array's device
  * address (with lazy module loading this also makes the driver load the
- * library's module); make that first call before any stream capture.  All
- * calls share the array: calls whose work overlaps on the GPU (different
- * streams or threads) race on it -- order them on one stream. */
+ * library's module); make that first call before any stream capture.  The
+ * address is cached per device and is stale after cudaDeviceReset: do not
+ * call it after a device reset.  All calls share the array: calls whose work
+ * overlaps on the GPU (different streams or threads) race on it -- order
+ * them on one stream.  The call holds the handle's lock, like every other
+ * call on a wl_gauge. */
 int wilson_dslash_noalloc(wl_gauge *g, const void *in, void *out, double kappa, int prec, int op, int dagger,
                           void *stream);
 

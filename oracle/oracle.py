@@ -33,13 +33,24 @@ OK, NOCONV = 0, 1
 
 
 def build(force: bool = False) -> str:
-    """Compile the C oracle (plain gcc, no contraction so x86 and Arm agree)."""
+    """Compile the C oracle (plain gcc, no contraction so x86 and Arm agree),
+    with OpenMP for the per-site loops where the compiler has it."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-                               "-fcx-limited-range", "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fcx-limited-range",
+                "-o", tmp, _SRC, "-lm"]
+        try:
+            subprocess.check_call(base + ["-fopenmp"], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB)
     return _LIB
+
+
+def set_threads(n: int = 0) -> int:
+    """Threads for the oracle's per-site loops (n > 0 sets them); returns the
+    count in use.  Results do not depend on it."""
+    return int(lib().or_threads(int(n)))
 
 
 class _Op(ctypes.Structure):
@@ -72,6 +83,8 @@ def lib():
         _lib.or_link_force.argtypes = [vp, ctypes.c_int, vp, vp, vp, ctypes.c_double, vp, vp]
         _lib.or_gamma_matrices.argtypes = [vp]
         _lib.or_apply_mk_sites.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_double, vp, ctypes.c_long, vp]
+        _lib.or_threads.argtypes = [ctypes.c_int]
+        _lib.or_threads.restype = ctypes.c_int
     return _lib
 
 

@@ -7,7 +7,11 @@
  * smoke check and the benchmark's CPU-baseline leg may load it; the library
  * never calls it and shares no code with it.
  *
- * Everything is FP64, scalar loops, C99 complex arithmetic, single thread.
+ * Everything is FP64, scalar loops, C99 complex arithmetic.  The per-site
+ * loops of the hop and of the sampled-site operator may run on several
+ * threads (an OpenMP parallel-for when built with -fopenmp): every output
+ * site is computed by the same code from the same inputs, so the result is
+ * bit-identical for any thread count.  Reductions stay sequential.
  * Fields use the canonical layouts:
  *   spinor psi[n][s][c]      (site n lexicographic, spin s = 0..3, colour c = 0..2)
  *   links  U[mu][n][a][b]    (mu = 0..3 <-> x, y, z, t = the paper's gamma_1..gamma_4)
@@ -33,6 +37,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef double complex cplx;
 
@@ -55,6 +62,19 @@ typedef struct {
     int restarts;        /* restarts after an iterated/true residual gap or breakdown */
     double true_relres;  /* ||b - A x|| / bref at exit */
 } or_stats;
+
+/* Threads for the per-site loops: n > 0 sets the count; returns the count
+ * in use (1 when built without OpenMP). */
+int or_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 /* ---------------------------------------------------------------- gamma -- */
 
@@ -159,6 +179,7 @@ void or_hop(const int d[4], int ap, const cplx *U, const cplx *in, cplx *out)
                 Pp[mu][a][b] = id + g[mu][a][b];
             }
     const long V = or_volume(d);
+#pragma omp parallel for schedule(static)
     for (long n = 0; n < V; ++n) {
         cplx acc[3][4] = {{0}};
         for (int mu = 0; mu < 4; ++mu) {
@@ -203,6 +224,7 @@ void or_apply_mk_sites(const int d[4], int ap, const cplx *U, const cplx *in, do
     cplx g[4][4][4];
     or_gammas(g);
     const long V = or_volume(d);
+#pragma omp parallel for schedule(static)
     for (long j = 0; j < nsites; ++j) {
         const long n = sites[j];
         cplx acc[3][4] = {{0}};

@@ -33,7 +33,10 @@ void *g_scratch_ptr[kMaxDevices] = {};
 
 // Device address of the scratch array on the current device.  The host-side
 // symbol is only a stand-in, so the address is looked up once per device,
-// with that device current.
+// with that device current, and cached.  cudaDeviceReset (or anything else
+// that destroys the primary context) unloads the module, so the cached
+// address is stale afterwards; the library does not support calls after a
+// device reset.
 int scratch_address(void **out)
 {
     int dev = 0;
@@ -76,6 +79,9 @@ extern "C" int wilson_dslash_noalloc(wl_gauge *g, const void *in, void *out, dou
     }
     void *base = nullptr;
     WL_TRY(scratch_address(&base));
+    // the hop variant lookup reads the handle's tuning table, which
+    // wl_autotune may be filling from another thread
+    std::lock_guard<std::mutex> lock(g->mu);
     cudaStream_t s = as_stream(stream);
     Vec ie, io, oe, oo;
     Vec *v[4] = {&ie, &io, &oe, &oo};

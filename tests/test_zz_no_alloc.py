@@ -51,3 +51,32 @@ def test_noalloc_rejects_oversized_lattice(api):
     with pytest.raises(api.WilsonError) as e:
         api.wilson_dslash_noalloc(g, psi, out, 0.12, "f64", api.OP_M)
     assert e.value.status == api.WL_ERR_ARG and "64 MiB" in str(e.value)
+
+
+def test_noalloc_allocates_nothing(api):
+    """The property the entry point exists for: on a handle whose workspace
+    is empty, the call leaves the device's free memory unchanged.  A first
+    call on another handle comes before the measurement, because the first
+    launch of a kernel may make the driver load its code.  The same
+    measurement then sees wilson_dslash allocate the handle's workspace."""
+    dims = (16, 16, 16, 16)  # four FP32 half-lattice spinors of 3.1 MB each
+    U = torch.from_numpy(synth.gauge_field(dims, 0.5, seed=18)).cuda()
+    lat = api.Lattice(dims)
+    psi = torch.from_numpy(synth.gaussian_source(dims, seed=50)).cuda()
+    got = torch.empty_like(psi)
+    want = torch.empty_like(psi)
+    warm = api.Gauge(lat, U, precs=("f32",))
+    api.wilson_dslash_noalloc(warm, psi, got, 0.121, "f32", api.OP_MPREC)
+    torch.cuda.synchronize()
+    g = api.Gauge(lat, U, precs=("f32",))
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(2):
+        api.wilson_dslash_noalloc(g, psi, got, 0.121, "f32", api.OP_MPREC)
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    assert free1 == free0, free0 - free1
+    api.wilson_dslash(g, psi, want, 0.121, "f32", api.OP_MPREC)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] < free1
+    assert rel(got.cpu().numpy(), want.cpu().numpy()) <= TOL["f32"]
