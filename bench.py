@@ -1,22 +1,25 @@
 #!/usr/bin/env python3
 """Benchmark: multi-mass Wilson solve time to a 1e-10 true residual, and the
-hop (dslash) kernel's HBM bandwidth against the measured GB300 copy peak.
+hop (dslash) kernels' throughput against the measured GB300 peaks.
 
 One step = the paper's single-mass multi-mass scheme (even-odd
-preconditioning, double-float (FP64-class) defect correction around a
-reduced-precision BiCGstab, Lagrange initial guesses, masses heaviest
-first) for every source of the workload, all sources batched in one
-multimass_solve call.  The line also carries the end-to-end time through
-the public API with host inputs and outputs, the hop roofline, the FP64
-oracle's time on one host core, and the multi-shift BiCGstab-M baseline
-(double-float and FP64) on the same sources and masses.
+preconditioning, FP64 defect correction around a reduced-precision
+BiCGstab, Lagrange initial guesses, masses heaviest first) for every source
+of the workload, the sources batched into multimass_solve calls.  The line
+also carries the end-to-end time through the public API with host inputs
+and outputs, a roofline entry for each hop class that takes a large share
+of the step (the inner hop against HBM, the FP64 residual hop against the
+FP64 pipe), the FP64 oracle's time on the host cores, the solution error
+against stored oracle solutions per mass, and the multi-shift BiCGstab-M
+baseline (FP64 and double-float) on the same GPU.
 
-Default workload (--config c3): 24^3 x 64 lattice, synthetic SU(3) links
-exp(i 0.5 H), antiperiodic in time, 12 spin-colour point sources at site 0,
-8 masses m0 = 0.40 .. 0.05.  --config c2 selects 16^3 x 32, eps 0.5, one Z2
-source, the same 8 masses (its working set fits in the 129 MB L2);
---config c5 selects 48^3 x 96, eps 0.7, 12 point sources, 16 masses
-0.5 * 0.04^(i/15), FP16 inner.
+Default workload (--config c5): 48^3 x 96 lattice, synthetic SU(3) links
+exp(i 0.7 H), antiperiodic in time, 12 spin-colour point sources at site 0,
+16 masses m0 = 0.5 * 0.04^(i/15), FP16-storage inner solves (FP32
+arithmetic), FP64 residual recomputation, accumulator and reductions.
+--config c3 selects 24^3 x 64, eps 0.5, 12 point sources, 8 masses
+m0 = 0.40 .. 0.05, FP32 inner; --config c2 16^3 x 32, one Z2 source (its
+working set fits in the 129 MB L2); --outer df the double-float outer loop.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 For N > 1 launch with torch.distributed.run; every rank solves its own
@@ -54,24 +57,25 @@ CONFIGS = {
     "c5": dict(name="48^3x96, 12 spin-colour point sources x 16 masses (m0 0.5*0.04^(i/15)), eps 0.7",
                dims=(48, 48, 48, 96), eps=0.7, seed=5, sources="points12",
                masses=[0.5 * 0.04 ** (i / 15.0) for i in range(16)], inner="f16", source_batch=2,
-               baseline_sources=1),
+               baseline_sources=1, e2e_steps=3),
 }
-# algorithmic bytes of one hop: per output site 8 links, per output site and
-# rhs one input spinor (each read once) and one output spinor
+# algorithmic bytes of one hop: per output site 8 links (12 reals: the
+# minimum the method must read), per output site and rhs one input spinor
+# (each read once) and one output spinor
 LINK_B = {"f64": 96, "df": 96, "f32": 48, "f16": 24}
 SPINOR_B = {"f64": 192, "df": 192, "f32": 96, "f16": 52}
+FLOP_SITE = 1320   # per hop output site and rhs
 # DRAM bytes (read + write) per launch of the timed hop kernel from one ncu
 # capture, keyed by (precision, autotuner variant, rhs per launch): (half-
 # lattice sites of the captured case, bytes).  Traffic scales with sites.
 # An entry is valid only for the kernel as it was when captured; remove it
 # when that kernel changes.
-HOP_TRAFFIC = {("f32", 205, 12): (442368, 1244.7e6), ("f16", 101, 2): (1048576, 404.7e6),
-               ("f16", 106, 2): (1048576, 404.0e6)}
-# The reference arm cannot afford a full oracle solve; it times a sample of
-# oracle BiCGstab iterations and scales by this many inner iterations per
-# step (the paper scheme's FP32-inner count on the c3 workload, from the
-# optimised arm's own JSON line `iterations_per_step`).
-REF_ITERS_PER_STEP = {"c3": 963, "c2": None}
+HOP_TRAFFIC = {}
+# FP64 FMA rate of one GB300 (TFLOP/s, 2 flops per FMA): 152 SMs x 2 FP64
+# FMA per clock x 2.07 GHz, the unit count and clock of the part; a probe
+# kernel of independent FMA chains measured 1.26 TFLOP/s
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+GOLDEN = os.path.join(ROOT, "tests", "golden")
 
 
 def sources(cfg):
@@ -191,53 +195,95 @@ def max_over_ranks(v, ws):
     return float(t.item())
 
 
-def oracle_sample(cfg, U, bs, target_s=15.0):
-    """Time FP64 oracle applications of M_prec (lightest mass, first source)
-    for about target_s seconds (at least one application).  One BiCGstab
-    iteration applies the operator twice; its six vector updates are not
-    timed (under 2% of an oracle iteration).  Returns (seconds per
-    iteration, applications, seconds)."""
+def oracle_counts(config):
+    """The FP64 oracle's own per-mass BiCGstab iterations and restarts for
+    this workload, from tests/golden/<config>_oracle_multimass.json (written
+    by tests/golden/make_oracle_multimass.py, which calls only the oracle),
+    averaged over the point sources it recorded.  None if there is no such
+    file."""
+    path = os.path.join(GOLDEN, f"{config}_oracle_multimass.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        gold = json.load(f)
+    recs = [r for r in gold["sources"].values() if None not in r["iterations"]]
+    if not recs:
+        return None
+    n = len(gold["masses"])
+    iters = [float(np.mean([r["iterations"][i] for r in recs])) for i in range(n)]
+    rest = [float(np.mean([r["restarts"][i] for r in recs])) for i in range(n)]
+    return {"iterations": iters, "restarts": rest, "sources": sorted(int(k) for k in gold["sources"]),
+            "file": os.path.relpath(path, ROOT)}
+
+
+def oracle_sample(cfg, U, b):
+    """Time the FP64 oracle as it stands on this workload's field: one
+    application of M_prec, and one call of its even-odd BiCGstab limited to
+    one iteration (initial residual, the iteration -- two M_prec and the
+    vector updates --, the restart check and the final residual: five
+    applications).  Returns (seconds per M_prec, seconds per BiCGstab
+    iteration, seconds spent)."""
     from oracle import oracle as O
     dims = cfg["dims"]
     m = cfg.get("masses", MASSES)[-1]
-    # the cost of an application does not depend on the vector: start from
-    # the even part of the source
-    bp = np.where(O.parity_mask(dims)[:, None, None], 0, bs[0])
-    n, t = 0, 0.0
-    while t < target_s or n < 1:
-        t0 = time.perf_counter()
-        bp = O.apply(O.OP_MPREC, U, dims, bp, O.kappa(m))
-        t += time.perf_counter() - t0
-        n += 1
-    return 2.0 * t / n, n, t
+    bp = O.eo_source(U, dims, b, m)
+    t0 = time.perf_counter()
+    O.apply(O.OP_MPREC, U, dims, bp, O.kappa(m))
+    t1 = time.perf_counter()
+    _, st = O.bicgstab(O.OP_MPREC, U, dims, bp, O.kappa(m), tol=1e-30, maxiter=1)
+    t2 = time.perf_counter()
+    assert st["iterations"] == 1
+    t_mprec = t1 - t0
+    return t_mprec, max((t2 - t1) - 3.0 * t_mprec, 0.0), t2 - t0
+
+
+def oracle_workload_seconds(counts, n_src, t_mprec, t_iter):
+    """Oracle time for the whole workload: per source and mass, its
+    iterations x t_iter plus the applications around them (initial and final
+    residual, one per restart, and the even-odd source, reconstruction and
+    full residual, three half-cost full-lattice hops)."""
+    per_src = sum(it * t_iter + (4.5 + r) * t_mprec for it, r in zip(counts["iterations"], counts["restarts"]))
+    return n_src * per_src
+
+
+def oracle_threads():
+    from oracle import oracle as O
+    return O.set_threads(os.cpu_count() or 1)
 
 
 def run_reference(args, cfg):
-    ws, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
+    ws, rank = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     from paper_1103_5103_gb300 import synth
+    counts = oracle_counts(args.config) if not getattr(args, "dims", "") else None
+    if counts is None:
+        print(json.dumps({"impl": "reference", "unavailable":
+                          "no oracle iteration count stored for this workload (tests/golden); the oracle "
+                          "cannot run a full step in the time a bench run has"}))
+        return
     U = synth.gauge_field(cfg["dims"], cfg["eps"], seed=cfg["seed"])
     bs = sources(cfg)
-    iters_per_step = REF_ITERS_PER_STEP.get(args.config)
-    if not iters_per_step:
-        print(json.dumps({"impl": "reference", "unavailable":
-                          "no iteration count recorded for this workload; the oracle cannot run a full step"}))
-        return
-    times = []
+    threads = oracle_threads()
+    times, last = [], None
     for k in range(args.warmup + args.steps):
-        s_it, n, dt = oracle_sample(cfg, U, bs, target_s=max(5.0, 90.0 / (args.warmup + args.steps)))
+        last = oracle_sample(cfg, U, bs[0])
         if k >= args.warmup:
-            times.append(s_it * iters_per_step)
+            times.append(oracle_workload_seconds(counts, len(bs), last[0], last[1]))
     v = float(np.mean(times))
+    its = int(round(len(bs) * sum(counts["iterations"])))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": cfg["name"], "sources": len(bs), "masses": list(cfg.get("masses", MASSES)),
                        "tol": 1e-10},
-            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": v, "unit": UNIT, "host": host_cpu(),
-                             "sample": f"FP64 oracle M_prec applications timed on one host core (2 per "
-                                       f"BiCGstab iteration), scaled by {iters_per_step} inner iterations per step"},
+            "cpu_baseline": {"kind": "oracle", "cores": threads, "value": v, "unit": UNIT, "host": host_cpu(),
+                             "sample": f"per step, one FP64 oracle M_prec application and one oracle BiCGstab "
+                                       f"iteration (two M_prec and its vector updates) timed on {threads} host "
+                                       f"threads ({last[0]:.2f} s and {last[1]:.2f} s in the last step), scaled "
+                                       f"by the oracle's own {its} iterations for the workload (mean over the "
+                                       f"sources {counts['sources']} in {counts['file']}, times {len(bs)} "
+                                       f"sources) plus its per-mass operator applications"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -245,6 +291,87 @@ def run_reference(args, cfg):
 def _used_bytes(torch):
     free, total = torch.cuda.mem_get_info()
     return total - free
+
+
+def roofline_entries(prof, inner, outer, V, peak, peak_kind, nb, hop_variant, outer_variant):
+    """One entry per hop class from the solve's live CUDA-event timings: the
+    inner hop (D_oe p, the first hop of every inner BiCGstab iteration) is
+    bound by HBM bandwidth; the FP64 residual hop (D_oe x, the first hop of
+    every outer check) by the FP64 pipe, whose FMA rate GB300 cuts to 1/57
+    of FP32.  Each entry also gives the class's estimated share of the step:
+    its mean launch time times its launches per step (four hops per inner
+    iteration, two per outer check)."""
+    out = {}
+    pi = prof[inner]
+    if pi["launches"]:
+        sites = pi["sites"] / pi["launches"]
+        site_rhs = pi["site_rhs"] / pi["launches"]
+        byts = sites * 8 * LINK_B[inner] + site_rhs * 2 * SPINOR_B[inner]
+        avg = pi["ms"] / pi["launches"] / 1e3
+        ach = byts / avg / 1e9
+        l2 = byts < 129e6
+        traffic = None
+        if (inner, hop_variant, nb) in HOP_TRAFFIC:
+            sites_cap, bytes_cap = HOP_TRAFFIC[(inner, hop_variant, nb)]
+            traffic = bytes_cap * (V // 2) / sites_cap
+        out["inner"] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                        # a hop whose operands fit in the 129 MB L2 is latency-bound:
+                        # no HBM fraction is quoted for it
+                        "frac": None if l2 else ach / peak, "l2_resident": l2, "traffic": traffic,
+                        "kernel": f"k_hop<{inner}> (D_oe p, first hop of each inner BiCGstab iteration), "
+                                  f"autotuned variant {hop_variant}, {site_rhs / sites:.0f} rhs per launch",
+                        "peak_kind": peak_kind, "bytes_per_launch": byts, "avg_launch_us": avg * 1e6,
+                        "timed_launches": pi["launches"], "gflops_1320": FLOP_SITE * site_rhs / avg / 1e9}
+    po = prof["outer"]
+    if po["launches"]:
+        site_rhs = po["site_rhs"] / po["launches"]
+        avg = po["ms"] / po["launches"] / 1e3
+        tf = FLOP_SITE * site_rhs / avg / 1e12
+        if outer == "f64":
+            out["outer"] = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                            "frac": tf / FP64_PEAK_TFLOPS, "traffic": None,
+                            "kernel": f"k_hop<f64> (D_oe x, first hop of each outer FP64 residual check), "
+                                      f"variant {outer_variant}, {site_rhs / (po['sites'] / po['launches']):.2f} "
+                                      f"rhs per launch on average",
+                            "peak_kind": "FP64 FMA rate from the unit count and clock (152 SMs x 2 FMA/clk "
+                                         "x 2.07 GHz; a probe measured 1.26)",
+                            "flops_per_site": FLOP_SITE, "avg_launch_us": avg * 1e6,
+                            "timed_launches": po["launches"]}
+        else:
+            out["outer"] = {"bound": "alu", "achieved": tf, "peak": None, "unit": "TFLOP/s", "frac": None,
+                            "traffic": None, "kernel": "k_hop_rolled<df> (double-float residual hop; FP32-issue "
+                                                       "bound)", "avg_launch_us": avg * 1e6,
+                            "timed_launches": po["launches"]}
+    return out
+
+
+def golden_errors(config, xs_by_source, masses, dev):
+    """Relative l2 error of GPU solutions against the oracle's solutions
+    (polished to 1e-13) stored at sampled sites in tests/golden, per mass:
+    {source: [error per mass]} for the sources given and recorded."""
+    import torch
+    path = os.path.join(GOLDEN, f"{config}_oracle_multimass.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        gold = json.load(f)
+    sites = torch.tensor(gold["sites"], dtype=torch.long, device=dev)
+    out = {}
+    for k, xs in xs_by_source.items():
+        rec = gold["sources"].get(str(k))
+        if rec is None:
+            continue
+        errs = []
+        for i, m in enumerate(masses):
+            ref = rec["x"][i]
+            if ref is None:
+                errs.append(None)
+                continue
+            want = np.array(ref)[..., 0] + 1j * np.array(ref)[..., 1]
+            got = xs[i][sites].cpu().numpy().reshape(len(gold["sites"]), 12)
+            errs.append(float(np.linalg.norm(got - want) / np.linalg.norm(want)))
+        out[str(k)] = errs
+    return out
 
 
 def run_ours(args, cfg):
@@ -257,6 +384,7 @@ def run_ours(args, cfg):
     dims = cfg["dims"]
     masses = list(cfg.get("masses", MASSES))
     inner = args.inner or cfg.get("inner", "f32")
+    outer = args.outer
     t0 = time.time()
     U = synth.gauge_field(dims, cfg["eps"], seed=cfg["seed"])
     bs_h = sources(cfg)
@@ -265,7 +393,8 @@ def run_ours(args, cfg):
     mem0 = _used_bytes(torch)
     lat = api.Lattice(dims)
     U_dev = torch.from_numpy(U).to(dev)
-    g = api.Gauge(lat, U_dev)
+    # links of the two precisions the solve uses
+    g = api.Gauge(lat, U_dev, precs=tuple(sorted({inner, outer})))
     V = lat.volume
     nr, nm = len(bs_h), len(masses)
     nb = args.source_batch or cfg.get("source_batch", nr)
@@ -273,8 +402,9 @@ def run_ours(args, cfg):
     bs = [torch.from_numpy(b).to(dev) for b in bs_h]
     # solution buffers for one batch of sources, reused by every batch
     xs = [[torch.empty((V, 4, 3), dtype=torch.complex128, device=dev) for _ in masses] for _ in range(nb)]
-    prm = api.params(inner_prec=inner, rhs_block=args.rhs_block, outer_prec=args.outer,
-                     inner_tol=args.inner_tol, reliable=int(args.reliable),
+    prm = api.params(inner_prec=inner, rhs_block=args.rhs_block, outer_prec=outer,
+                     inner_tol=args.inner_tol, reliable=int(args.reliable), guess_max=args.guess_max,
+                     verify_full=int(args.verify_full),
                      inner_solver=api.SOLVER_CG if args.inner_solver == "cg" else api.SOLVER_BICGSTAB,
                      mode={"graph": api.MODE_GRAPH, "persistent": api.MODE_PERSISTENT, "host": api.MODE_HOST}[args.mode])
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -317,9 +447,10 @@ def run_ours(args, cfg):
     torch.cuda.synchronize()
     clk = clocks.stop()
     launches = (api.launch_count() - launches0) / max(1, args.steps)
-    prof = api.profile_read(g)[inner]
+    prof = api.profile_read(g)
     api.profile_enable(g, False)
-    hop_variant = api.autotune(g, inner, nb)[0]   # the cached choice the solves used
+    hop_variant = api.autotune(g, inner, nb)[0]   # the cached choices the solves used
+    outer_variant = api.autotune(g, outer, nb)[0]
     barrier(ws)
     t_step = max_over_ranks(float(np.mean(step_ms)) / 1e3, ws)
 
@@ -330,6 +461,7 @@ def run_ours(args, cfg):
     # host link); otherwise each batch's sources are copied in and every
     # solution is copied out through an 8 GB pinned ring.  The copy path is
     # also timed, for comparison.
+    e2e_steps = max(1, min(args.steps, cfg.get("e2e_steps", args.steps)))
     bs_pin = [torch.from_numpy(b).pin_memory() for b in bs_h]
     x_bytes = V * 12 * 16
     h2d = sum(b.numel() * 16 for b in bs_pin)
@@ -339,7 +471,7 @@ def run_ours(args, cfg):
         n_slots = max(1, min(nr * nm, (8 << 30) // x_bytes))
         slots = [torch.empty((V, 4, 3), dtype=torch.complex128).pin_memory() for _ in range(n_slots)]
         times = []
-        for _ in range(max(1, args.steps)):
+        for _ in range(e2e_steps):
             flush.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -359,7 +491,7 @@ def run_ours(args, cfg):
     def e2e_zero_copy():
         xh = [[torch.empty((V, 4, 3), dtype=torch.complex128).pin_memory() for _ in masses] for _ in range(nb)]
         times = []
-        for _ in range(max(1, args.steps)):
+        for _ in range(e2e_steps):
             flush.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -373,24 +505,33 @@ def run_ours(args, cfg):
     t_e2e_copy = max_over_ranks(e2e_copy(), ws)
     t_e2e = max_over_ranks(e2e_zero_copy(), ws) if zero_copy else t_e2e_copy
 
+    # solution error against the oracle's stored solutions (untimed): the
+    # last batch is still in xs; the first batch is solved once more
+    errors = None
+    if rank == 0 and not args.dims:
+        have = {}
+        for j, r in enumerate(batches[-1]):
+            have[r] = xs[j]
+        errors = golden_errors(args.config, have, masses, dev) or {}
+        if len(batches) > 1:
+            solve_batch(batches[0])
+            torch.cuda.synchronize()
+            errors.update(golden_errors(args.config, {r: xs[j] for j, r in enumerate(batches[0])}, masses, dev)
+                          or {})
+
     peak, peak_kind = measured_peaks()
-    # hop roofline from the live event timings of the solve's own hop launches
-    if prof["launches"]:
-        per_launch_sites = prof["sites"] / prof["launches"]
-        per_launch_site_rhs = prof["site_rhs"] / prof["launches"]
-        bytes_launch = per_launch_sites * 8 * LINK_B[inner] + per_launch_site_rhs * 2 * SPINOR_B[inner]
-        avg_s = prof["ms"] / prof["launches"] / 1e3
-        achieved = bytes_launch / avg_s / 1e9
-        hop_gflops = 1320 * per_launch_site_rhs / avg_s / 1e9
-    else:
-        bytes_launch = avg_s = achieved = hop_gflops = None
-    # the timed hop's operands: links of one parity and nb input/output spinors
-    l2_resident = bytes_launch is not None and bytes_launch < 129e6
-    traffic = None
-    if (inner, hop_variant, nb) in HOP_TRAFFIC:
-        sites_cap, bytes_cap = HOP_TRAFFIC[(inner, hop_variant, nb)]
-        traffic = bytes_cap * (V // 2) / sites_cap
+    roof = roofline_entries(prof, inner, outer, V, peak, peak_kind, nb, hop_variant, outer_variant)
     iters = sum(st["iterations"] for row in all_stats for st in row)
+    restarts = sum(st["restarts"] for row in all_stats for st in row)
+    # launches per step of each hop class: four hops per inner iteration of a
+    # batch (the slowest rhs sets the batch's count), two per outer check
+    inner_hops = 4 * sum(max(all_stats[r][i]["iterations"] for r in rows) for rows in batches for i in range(nm))
+    outer_hops = 2 * sum(max(all_stats[r][i]["restarts"] for r in rows) for rows in batches for i in range(nm))
+    for key, n_h in (("inner", inner_hops), ("outer", outer_hops)):
+        if key in roof:
+            roof[key]["launches_per_step_est"] = n_h
+            roof[key]["step_share_est"] = n_h * roof[key]["avg_launch_us"] * 1e-6 / t_step
+    dominant = max(roof, key=lambda k: roof[k]["step_share_est"]) if roof else None
     worst = max(st["true_relres"] for row in all_stats for st in row)
     per_mass = {}
     for i, m in enumerate(masses):
@@ -398,44 +539,49 @@ def run_ours(args, cfg):
              "restarts": int(sum(all_stats[r][i]["restarts"] for r in range(nr))),
              "seconds": float(sum(all_stats[rows[0]][i]["seconds"] for rows in batches)),
              "max_true_relres": float(max(all_stats[r][i]["true_relres"] for r in range(nr)))}
+        if errors:
+            e["oracle_error"] = {k: v[i] for k, v in errors.items()}
         per_mass[f"{m:.4g}"] = e
 
+    dtype = {"f16": "f16 storage, f32 arithmetic", "f32": "f32", "f64": "f64"}[inner]
     line = {
         "metric": METRIC, "value": t_step, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": inner, "data": "synthetic",
+        "vs_baseline": None, "dtype": f"{outer} outer loop; inner solves in {dtype}", "data": "synthetic",
         "config": {"workload": cfg["name"], "sources": nr, "source_batch": nb, "masses": masses,
-                   "inner_prec": inner, "outer_prec": args.outer,
+                   "inner_prec": inner, "outer_prec": outer,
+                   "outer_arithmetic": ("FP64 residual recomputation b - M x, FP64 solution accumulator, FP64 "
+                                        "global reductions") if outer == "f64" else
+                                       "double-float (about 48-bit) residual, accumulator and reconstruction",
                    "inner_tol": args.inner_tol or "library default", "mode": args.mode,
+                   "guess_max": args.guess_max or "all earlier masses",
                    "outer_loop": "reliable updates" if args.reliable else "restarted defect correction",
                    "inner_solver": "CG on the normal equations" if args.inner_solver == "cg" else "BiCGstab",
+                   "full_residual": "recomputed with a hop D_eo x_o" if args.verify_full else
+                                    "even half from the last FP64 check, odd half from the reconstruction",
                    "tol": 1e-10, "l2": "flushed (256 MB write) before every step; working set > L2",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "e2e": {"value": t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "transfer": ("the solver reads the sources from and writes the solutions to page-locked host "
                              "memory (unified addressing)") if zero_copy else
                             "cudaMemcpy from pinned sources and to an 8 GB pinned ring",
-                "explicit_copies_value": t_e2e_copy},
+                "steps": e2e_steps, "explicit_copies_value": t_e2e_copy},
         "gpu_launches": int(round(launches)),
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     # a hop whose operands fit in the 129 MB L2 is latency-bound:
-                     # no HBM fraction is quoted for it
-                     "frac": (achieved / peak) if achieved and not l2_resident else None,
-                     "l2_resident": l2_resident, "traffic": traffic,
-                     "kernel": f"k_hop<{inner}> (D_oe p, first hop of each BiCGstab iteration), "
-                               f"autotuned variant {hop_variant}",
-                     "peak_kind": peak_kind, "bytes_per_launch": bytes_launch,
-                     "avg_launch_us": avg_s * 1e6 if avg_s else None, "timed_launches": prof["launches"],
-                     "gflops_1320": hop_gflops},
+        "roofline": dict(roof[dominant], hop_class=dominant) if dominant else None,
+        "rooflines": roof,
         "clocks": clk,
-        "iterations_per_step": int(iters), "max_true_relres": worst, "per_mass": per_mass,
+        "iterations_per_step": int(iters), "restarts_per_step": int(restarts), "max_true_relres": worst,
+        "per_mass": per_mass,
         "device_memory_gb": footprint / 1e9,
         "gauge_generation_s": gen_s,
     }
+    if errors:
+        line["oracle_error_max"] = max(e for v in errors.values() for e in v if e is not None)
+        line["oracle_error_sources"] = sorted(int(k) for k in errors)
     if rank == 0 and ws == 1 and not args.no_baseline:
         # BiCGstab-M on the same GPU, same sources and masses (context for the
         # paper's comparison; not part of the timed step), with its vectors
-        # and hops in double-float and in FP64.  Each on a fresh handle with
+        # and hops in FP64 and in double-float.  Each on a fresh handle with
         # only the links it uses, so its footprint is its own.
         g.close()
         del g, xs
@@ -444,12 +590,12 @@ def run_ours(args, cfg):
         point = cfg["sources"].startswith("point")
         shadow = torch.from_numpy(synth.gaussian_source(dims, seed=cfg["seed"] + 1000)).to(dev) if point else None
         nsrc = min(nr, args.baseline_sources or cfg.get("baseline_sources", nr))
-        for key, outer, precs in (("bicgstab_m_df", "df", ("df", "f32")), ("bicgstab_m_fp64", "f64", ("f64",))):
+        for key, bo, precs in (("bicgstab_m_fp64", "f64", ("f64",)), ("bicgstab_m_df", "df", ("df", "f32"))):
             torch.cuda.synchronize()
             torch.cuda.empty_cache()
             mem1 = _used_bytes(torch)
             gm = api.Gauge(lat, U_dev, precs=precs)
-            prm_m = api.params(shadow=shadow, outer_prec=outer)
+            prm_m = api.params(shadow=shadow, outer_prec=bo)
             t_m, it_m, worst_m, mem_m, polished = 0.0, 0, 0.0, 0, 0
             per_shift = None
             for r in range(nsrc):
@@ -468,7 +614,7 @@ def run_ours(args, cfg):
             gm.close()
             del gm
             line[key] = {"seconds_per_step": t_m * nr / nsrc, "sources_run": nsrc,
-                         "vectors_and_hops": "double-float" if outer == "df" else "FP64",
+                         "vectors_and_hops": "double-float" if bo == "df" else "FP64",
                          "iterations_per_source": it_m / nsrc, "max_true_relres": worst_m,
                          "iterations_per_mass_last_source": per_shift,
                          "shadow_residual": "Gaussian noise" if point else "b",
@@ -476,12 +622,24 @@ def run_ours(args, cfg):
                          "device_memory_gb": mem_m / 1e9,
                          "speedup_of_single_mass_scheme": (t_m * nr / nsrc) / t_step}
     if rank == 0 and ws == 1 and not args.no_cpu:
-        s_it, n_it, dt = oracle_sample(cfg, U, bs_h, target_s=args.cpu_seconds)
-        line["cpu_baseline"] = {"value": s_it * iters, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
-                                "sample": f"{n_it} FP64 oracle applications of M_prec (lightest mass, source 0) "
-                                          f"took {dt:.1f} s on one host core = {s_it:.2f} s per BiCGstab "
-                                          f"iteration (2 applications); scaled by the step's {iters} inner "
-                                          f"iterations"}
+        counts = oracle_counts(args.config) if not args.dims else None
+        threads = oracle_threads()
+        t_mprec, t_iter, spent = oracle_sample(cfg, U, bs_h[0])
+        if counts is not None:
+            its = int(round(nr * sum(counts["iterations"])))
+            v = oracle_workload_seconds(counts, nr, t_mprec, t_iter)
+            src = (f"the oracle's own {its} iterations for the workload (mean over the sources "
+                   f"{counts['sources']} in {counts['file']}, times {nr} sources)")
+        else:
+            # no stored oracle count for this lattice: the step's own inner
+            # iteration count stands in (said so in the sample string)
+            v = iters * t_iter + nr * nm * 4.5 * t_mprec
+            src = f"this run's {iters} inner iterations (no stored oracle count for this lattice)"
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "host": host_cpu(),
+                                "sample": f"one FP64 oracle M_prec application ({t_mprec:.2f} s) and one oracle "
+                                          f"BiCGstab iteration ({t_iter:.2f} s: two M_prec and the vector "
+                                          f"updates) on {threads} host threads, {spent:.1f} s in all; scaled by "
+                                          f"{src} plus the per-mass operator applications"}
     if rank == 0:
         print(json.dumps(line))
 
@@ -492,10 +650,15 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--config", choices=sorted(CONFIGS), default="c3")
+    ap.add_argument("--config", choices=sorted(CONFIGS), default="c5")
     ap.add_argument("--inner", choices=["f32", "f16", "f64"], default=None,
                     help="inner precision (default: the workload's, f32 unless it names one)")
-    ap.add_argument("--outer", choices=["df", "f64"], default="df")
+    ap.add_argument("--outer", choices=["f64", "df"], default="f64",
+                    help="precision of the residual recomputation, accumulator and reconstruction")
+    ap.add_argument("--guess-max", type=int, default=0,
+                    help="earlier masses the Lagrange guess uses (0: all, the paper's choice)")
+    ap.add_argument("--verify-full", action="store_true",
+                    help="recompute the even half of the full residual with one more hop per mass")
     ap.add_argument("--rhs-block", type=int, default=0)
     ap.add_argument("--inner-tol", type=float, default=0.0)
     ap.add_argument("--mode", choices=["graph", "persistent", "host"], default="graph")
@@ -508,7 +671,6 @@ def main():
                     help="sources for the BiCGstab-M comparison (default: the workload's, else all)")
     ap.add_argument("--source-batch", type=int, default=0,
                     help="sources per multimass_solve call (default: the workload's, else all)")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-baseline", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--ncu-step", action="store_true",

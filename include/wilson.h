@@ -38,10 +38,11 @@
  *    Sources and solutions are full-lattice vectors; the even/odd split is
  *    internal.  Site parity = (x+y+z+t) mod 2; site 0 is even.
  *  - Precisions: WL_F64, WL_F32, WL_F16 (FP16 storage with one FP32 norm
- *    per site, arithmetic in FP32) and WL_DF (double-float, see below).  Links are stored as their first two rows
- *    (12 reals) and the third row is rebuilt as conj(row0 x row1), which is
- *    exact for SU(3) links; double-float links keep all three rows (row 2
- *    formed in FP64 when the handle is created).
+ *    per site, arithmetic in FP32) and WL_DF (double-float, see below).
+ *    FP32 and FP16 links are stored as their first two rows (12 reals) and
+ *    the third row is rebuilt as conj(row0 x row1), which is exact for SU(3)
+ *    links; FP64 links keep all three rows as given and double-float links
+ *    all three rows with row 2 formed in FP64 when the handle is created.
  */
 #ifndef WILSON_H
 #define WILSON_H
@@ -134,6 +135,14 @@ typedef struct {
                             dropped by inner_tol                                      */
     int    inner_solver; /* WL_SOLVER_BICGSTAB (default) or WL_SOLVER_CG; CG works with
                             the graph and host modes and restarted defect correction  */
+    int    verify_full;  /* even-odd solves: how stats.true_relres gets the even half of
+                            the full-lattice residual.  0 (default): from the last
+                            outer check, b_prec - M_prec x_e, which equals
+                            b_e - x_e + kappa D_eo x_o up to the rounding of the
+                            rebuilt x_o = b_o + kappa D_oe x_e (Section 6.2.3), so no
+                            further hop; 1: recomputed with one more outer-precision
+                            hop D_eo x_o per rhs.  The odd half is the rounding of
+                            the rebuild either way.                                  */
 } wl_solver_params;
 
 typedef struct {
@@ -150,8 +159,8 @@ typedef struct {
  * inner_tol 0 (1e-6 for FP32, 3e-4 for FP16, 1e-12 for FP64; never below
  * what the outer target needs), max_restarts 100,
  * WL_GUESS_POLY, WL_MODE_GRAPH, rhs_block 0, graph_iters 8, eo 1,
- * outer_prec WL_DF, shadow NULL, guess_max 0, reliable 0,
- * inner_solver WL_SOLVER_BICGSTAB. */
+ * outer_prec WL_F64, shadow NULL, guess_max 0, reliable 0,
+ * inner_solver WL_SOLVER_BICGSTAB, verify_full 0. */
 int wl_params_default(wl_solver_params *p);
 
 /* Thread-local message describing the last failing call on this thread. */
@@ -180,10 +189,10 @@ int wl_spinor_export(const wl_lattice *lat, const void *internal, void *canon_c1
                      int parity, void *stream);
 
 /* Pack canonical complex128 links (device, [4][V][3][3]) into the internal
- * 12-real per-parity layout (Section 4, Eq. 8, compressed to two rows) for
- * every precision set in prec_mask (WL_F64 | WL_F32 | WL_F16).  The links
- * must be SU(3): the 12-real formats rebuild the third row from the first
- * two.  Links whose U U^dag - 1 or det U - 1 has an entry (real or
+ * per-parity layouts (Section 4, Eq. 8; FP32 and FP16 compressed to two
+ * rows, FP64 and double-float with all three) for every precision set in
+ * prec_mask (WL_F64 | WL_F32 | WL_F16 | WL_DF).  The links must be SU(3):
+ * the 12-real formats rebuild the third row from the first two.  Links whose U U^dag - 1 or det U - 1 has an entry (real or
  * imaginary part) above 1e-6 in magnitude, or a NaN, are rejected with
  * WL_ERR_ARG.  The gauge handle keeps a reference to lat, which must
  * outlive it.  Synchronises the stream before returning. */
@@ -344,8 +353,11 @@ typedef struct {
 
 /* Reset the counters of g and start (on = 1) or stop (on = 0) profiling. */
 int wl_profile_enable(wl_gauge *g, int on);
-/* Counters per inner precision: out[0] FP64, out[1] FP32, out[2] FP16. */
-int wl_profile_read(wl_gauge *g, wl_kernel_profile out[3]);
+/* Counters of the inner hop per inner precision: out[0] FP64, out[1] FP32,
+ * out[2] FP16; out[3]: the outer loop's residual hop D_oe x that opens every
+ * defect-correction check (outer precision), timed the same way, with
+ * site_rhs counting only the rhs that the launch processed. */
+int wl_profile_read(wl_gauge *g, wl_kernel_profile out[4]);
 
 /* Autotune the hop for (prec, n_rhs) on this gauge handle: every variant
  * (right-hand sides per thread, minimum resident blocks per SM) is timed

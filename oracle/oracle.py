@@ -289,27 +289,47 @@ def initial_guess(b, done_psi, done_m, m, guess="poly", guess_max=0):
     return (m + 4.0) * sum(cj * pj for cj, pj in zip(c, ps))
 
 
-def multimass_solve(U, dims, b, masses, tol=1e-10, guess="poly", maxiter=10000, antiperiodic=True, guess_max=0):
+def multimass_solve(U, dims, b, masses, tol=1e-10, guess="poly", maxiter=10000, antiperiodic=True, guess_max=0,
+                    on_solution=None):
     """The paper's single-mass scheme (Section 6.2, Section 7): masses solved
     heaviest first, each by even-odd-preconditioned BiCGstab started from the
     polynomial extrapolation through all previous solutions (extrapolating the
     paper-normalised solution psi = x / (m + 4) on even sites), or from the
     solution-space minimisation guess.  Returns kappa-form solutions in the
-    caller's mass order and per-mass stats."""
+    caller's mass order and per-mass stats.
+
+    With on_solution, each solution is handed to on_solution(i, x, stats) as
+    soon as it is found and is not kept (the returned xs[i] is None); the
+    polynomial guess then stores only the even sites of the earlier psi, the
+    only sites it uses, so that lattices of 10^7 sites fit in host memory.
+    The arithmetic is the same either way."""
     order = sorted(range(len(masses)), key=lambda i: -masses[i])
     odd = parity_mask(dims)
+    even = ~odd
+    lean = on_solution is not None and guess == "poly"
     done_m, done_psi = [], []
     xs, stats = [None] * len(masses), [None] * len(masses)
     for i in order:
         m = float(masses[i])
         x0 = initial_guess(b, done_psi, done_m, m, guess, guess_max)
         if x0 is not None:
-            x0 = x0.copy()
-            x0[odd] = 0
+            if lean:
+                full = np.zeros(np.shape(b), dtype=np.complex128)
+                full[even] = x0
+                x0 = full
+            else:
+                x0 = x0.copy()
+                x0[odd] = 0
         x, st = eo_solve(U, dims, b, m, x0e=x0, tol=tol, maxiter=maxiter, antiperiodic=antiperiodic)
-        xs[i], stats[i] = x, st
+        del x0
+        stats[i] = st
         done_m.append(m)
-        done_psi.append(x / (m + 4.0))
+        done_psi.append((x[even] if lean else x) / (m + 4.0))
+        if on_solution is None:
+            xs[i] = x
+        else:
+            on_solution(i, x, st)
+        del x
     return xs, stats
 
 

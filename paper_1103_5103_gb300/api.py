@@ -51,7 +51,7 @@ class SolverParams(ctypes.Structure):
     _fields_ = [("tol", _dbl), ("max_iter", _int), ("inner_prec", _int), ("inner_tol", _dbl),
                 ("max_restarts", _int), ("guess", _int), ("mode", _int), ("rhs_block", _int),
                 ("graph_iters", _int), ("eo", _int), ("outer_prec", _int), ("shadow", _vp),
-                ("guess_max", _int), ("reliable", _int), ("inner_solver", _int)]
+                ("guess_max", _int), ("reliable", _int), ("inner_solver", _int), ("verify_full", _int)]
 
 
 class SolverStats(ctypes.Structure):
@@ -147,7 +147,7 @@ def _canon(t: torch.Tensor, V: int, what: str):
 
 def params(**kw) -> SolverParams:
     """Default solver parameters (wl_params_default) with keyword overrides;
-    inner_prec accepts 'f64' | 'f32' | 'f16', outer_prec 'df' | 'f64' (the
+    inner_prec accepts 'f64' | 'f32' | 'f16', outer_prec 'f64' | 'df' (the
     defect correction's outer loop, and the vectors and hops of
     bicgstab_m_solve); shadow takes a canonical complex128 CUDA tensor (kept
     alive by the returned object)."""
@@ -327,10 +327,11 @@ def profile_enable(g: Gauge, on: bool = True):
 
 
 def profile_read(g: Gauge) -> dict:
-    """{'f64': {...}, 'f32': {...}, 'f16': {...}} hop launch counters."""
-    arr = (KernelProfile * 3)()
+    """Hop launch counters: the inner hop per inner precision ('f64', 'f32',
+    'f16') and the outer residual hop ('outer')."""
+    arr = (KernelProfile * 4)()
     _check(_lib.wl_profile_read(g.handle, arr))
-    return {"f64": arr[0].as_dict(), "f32": arr[1].as_dict(), "f16": arr[2].as_dict()}
+    return {"f64": arr[0].as_dict(), "f32": arr[1].as_dict(), "f16": arr[2].as_dict(), "outer": arr[3].as_dict()}
 
 
 def launch_count() -> int:

@@ -82,7 +82,7 @@ __global__ void k_link_force(Geom g, const void *links_even, const void *links_o
         if (mu == 3 && g.antiperiodic) sgn = -1.0;
     }
     const size_t m = cm[0] + (size_t)g.X * (cm[1] + (size_t)g.Y * (cm[2] + (size_t)g.Z * cm[3]));
-    // link U_mu(n) from the internal 12-real store, row 2 rebuilt
+    // link U_mu(n) from the internal store (all three rows for FP64 and DF)
     cx<typename PrecTraits<PL>::R> ul[9];
     LinkIO<PL>::load(static_cast<const char *>(par ? links_odd : links_even) + (size_t)mu * link_dir_bytes(PL, g.stride),
                      g.stride, i, ul);

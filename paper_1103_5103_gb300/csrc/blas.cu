@@ -81,7 +81,8 @@ __global__ void __launch_bounds__(kBlock) k_xr_update(Geom g, Vec x, Vec p, Vec 
     if (__ldcg(&S.done)) return;
     using R = RT<P>;
     using RX = RT<PX>;
-    double red[3] = {0.0, 0.0, 0.0};
+    using RedT = typename RedType<R>::T;
+    RedT red[3] = {RedT(0), RedT(0), RedT(0)};
     if (q.i < g.Vh) {
         const double are = __ldcg(&S.alpha_re), aim = __ldcg(&S.alpha_im);
         const double ore = __ldcg(&S.omega_re), oim = __ldcg(&S.omega_im);
@@ -115,9 +116,9 @@ __global__ void __launch_bounds__(kBlock) k_xr_update(Geom g, Vec x, Vec p, Vec 
             d = conjmad(rh[k], rv[k], d);
             n = fma(rv[k].re, rv[k].re, fma(rv[k].im, rv[k].im, n));
         }
-        red[0] = (double)d.re;
-        red[1] = (double)d.im;
-        red[2] = (double)n;
+        red[0] = d.re;
+        red[1] = d.im;
+        red[2] = n;
     }
     double tot[3];
     if (grid_sum<3>(red, partials + (size_t)q.r * q.nsb * kRedNV, &S.ticket[2], q.sb, q.nsb, tot) &&
@@ -185,7 +186,8 @@ __global__ void __launch_bounds__(kBlock) k_cg_xr(Geom g, Vec x, Vec p, Vec w, V
     if (__ldcg(&S.done)) return;
     using R = RT<P>;
     using RX = RT<PX>;
-    double red[1] = {0.0};
+    using RedT = typename RedType<R>::T;
+    RedT red[1] = {RedT(0)};
     if (q.i < g.Vh) {
         const double al = __ldcg(&S.alpha_re);
         cx<R> pv[12], wv[12], rv[12];
@@ -205,7 +207,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_xr(Geom g, Vec x, Vec p, Vec w, V
         R n = R(0);
 #pragma unroll
         for (int k = 0; k < 12; ++k) n = fma(rv[k].re, rv[k].re, fma(rv[k].im, rv[k].im, n));
-        red[0] = (double)n;
+        red[0] = n;
     }
     double tot[1];
     if (grid_sum<1>(red, partials + (size_t)q.r * q.nsb * kRedNV, &S.ticket[1], q.sb, q.nsb, tot) &&
@@ -294,9 +296,10 @@ __global__ void __launch_bounds__(kBlock) k_restart(Geom g, Vec r64, Vec r, Vec 
         if (q.sb == 0 && threadIdx.x == 0) S.done = 1;
         return;
     }
-    double red[3] = {0.0, 0.0, 0.0};
+    using R = RT<P>;
+    using RedT = typename RedType<R>::T;
+    RedT red[3] = {RedT(0), RedT(0), RedT(0)};
     if (q.i < g.Vh) {
-        using R = RT<P>;
         cx<RT<PO>> a[12];
         SpinorIO<PO>::load(r64.rhs(q.r), g.stride, q.i, a);
         cx<R> v[12];
@@ -324,9 +327,9 @@ __global__ void __launch_bounds__(kBlock) k_restart(Geom g, Vec r64, Vec r, Vec 
             d = conjmad(h[k], v[k], d);
             n = fma(v[k].re, v[k].re, fma(v[k].im, v[k].im, n));
         }
-        red[0] = (double)d.re;
-        red[1] = (double)d.im;
-        red[2] = (double)n;
+        red[0] = d.re;
+        red[1] = d.im;
+        red[2] = n;
     }
     double tot[3];
     if (grid_sum<3>(red, partials + (size_t)q.r * q.nsb * kRedNV, &S.ticket[3], q.sb, q.nsb, tot) &&
@@ -460,17 +463,18 @@ template <int P>
 __global__ void __launch_bounds__(kBlock) k_norm2(Geom g, Vec a, double *out, double *partials, unsigned *tickets)
 {
     const SiteIdx q = site_idx(a.nrhs);
-    double red[1] = {0.0};
+    using NT = typename NormT<RT<P>>::T;
+    NT red[1] = {NT(0)};
     if (q.i < g.Vh) {
         cx<RT<P>> v[12];
         ld<P>(a, q.r, g.stride, q.i, v);
-        typename NormT<RT<P>>::T n = 0;
+        NT n = 0;
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
             norm_acc(n, v[k].re);
             norm_acc(n, v[k].im);
         }
-        red[0] = (double)n;
+        red[0] = n;
     }
     double tot[1];
     if (grid_sum<1>(red, partials + (size_t)q.r * q.nsb * kRedNV, &tickets[q.r], q.sb, q.nsb, tot) &&

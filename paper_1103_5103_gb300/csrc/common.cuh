@@ -207,7 +207,18 @@ __host__ __device__ constexpr int spinor_site_bytes(int prec)
 }
 __host__ __device__ constexpr int link_site_bytes(int prec)
 {
-    return prec == WL_F64 ? 96 : prec == WL_F32 ? 48 : prec == WL_DF ? 144 : 24;
+    return prec == WL_F64 ? 144 : prec == WL_F32 ? 48 : prec == WL_DF ? 144 : 24;
+}
+
+// Start value of every hop accumulator: -0.0.  x + (-0.0) == x exactly for
+// every x (+0 and -0 included), so the compiler may turn the first
+// accumulation into each output component into a move; with +0.0 it may
+// not (+0 + -0 is +0), and the first of the eight transporters would cost
+// 24 adds per site and rhs.
+template <typename R>
+__device__ __forceinline__ cx<R> acc_zero()
+{
+    return {R(-0.0f), R(-0.0f)};
 }
 
 // Squared magnitude accumulated per site: FP32 for FP32 and double-float
@@ -250,6 +261,9 @@ __device__ __forceinline__ cx<To> cconv(cx<From> z)
 //   DF:  float4  [12][stride]  (chunk k = component k as re.hi, re.lo, im.hi, im.lo)
 template <int P> struct SpinorIO;
 
+// load_unscaled(base, stride, i, v) returns a factor f with site value =
+// f * v: the per-site norm for FP16 storage (v the unscaled halves), 1 for
+// the other formats (v the values).
 template <> struct SpinorIO<WL_F64> {
     using R = double;
     template <bool CG = false>
@@ -261,6 +275,12 @@ template <> struct SpinorIO<WL_F64> {
             double2 t = ldx<CG>(p + (size_t)k * stride + i);
             v[k] = {t.x, t.y};
         }
+    }
+    template <bool CG = false>
+    static __device__ __forceinline__ R load_unscaled(const void *base, int stride, int i, cx<R> (&v)[12])
+    {
+        load<CG>(base, stride, i, v);
+        return 1.0;
     }
     static __device__ __forceinline__ void roundtrip(cx<R> (&)[12]) {}
     static __device__ __forceinline__ void store(void *base, int stride, int i, const cx<R> (&v)[12])
@@ -283,6 +303,12 @@ template <> struct SpinorIO<WL_F32> {
             v[2 * k] = {t.x, t.y};
             v[2 * k + 1] = {t.z, t.w};
         }
+    }
+    template <bool CG = false>
+    static __device__ __forceinline__ R load_unscaled(const void *base, int stride, int i, cx<R> (&v)[12])
+    {
+        load<CG>(base, stride, i, v);
+        return 1.f;
     }
     static __device__ __forceinline__ void roundtrip(cx<R> (&)[12]) {}
     static __device__ __forceinline__ void store(void *base, int stride, int i, const cx<R> (&v)[12])
@@ -322,6 +348,22 @@ template <> struct SpinorIO<WL_F16> {
     static __device__ __forceinline__ const float *norms(const void *base, int stride)
     {
         return reinterpret_cast<const float *>(static_cast<const uint4 *>(base) + 3 * (size_t)stride);
+    }
+    template <bool CG = false>
+    static __device__ __forceinline__ R load_unscaled(const void *base, int stride, int i, cx<R> (&v)[12])
+    {
+        const uint4 *p = static_cast<const uint4 *>(base);
+        const float n = ldx<CG>(norms(base, stride) + i);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            uint4 t = ldx<CG>(p + (size_t)k * stride + i);
+            float2 a = unpack_half2(t.x), b = unpack_half2(t.y), c = unpack_half2(t.z), d = unpack_half2(t.w);
+            v[4 * k + 0] = {a.x, a.y};
+            v[4 * k + 1] = {b.x, b.y};
+            v[4 * k + 2] = {c.x, c.y};
+            v[4 * k + 3] = {d.x, d.y};
+        }
+        return n;
     }
     template <bool CG = false>
     static __device__ __forceinline__ void load(const void *base, int stride, int i, cx<R> (&v)[12])
@@ -379,6 +421,12 @@ template <> struct SpinorIO<WL_DF> {
             v[k] = {df(t.x, t.y), df(t.z, t.w)};
         }
     }
+    template <bool CG = false>
+    static __device__ __forceinline__ R load_unscaled(const void *base, int stride, int i, cx<R> (&v)[12])
+    {
+        load<CG>(base, stride, i, v);
+        return df(1.f);
+    }
     static __device__ __forceinline__ void roundtrip(cx<R> (&)[12]) {}
     static __device__ __forceinline__ void store(void *base, int stride, int i, const cx<R> (&v)[12])
     {
@@ -391,10 +439,11 @@ template <> struct SpinorIO<WL_DF> {
     }
 };
 
-// Links: per parity, per direction, the first two rows (6 complex, k = 3*row + col):
-//   F64: double2 [4][6][stride];  F32: float4 [4][3][stride];  F16: uint2 [4][3][stride]
+// Links: per parity, per direction (k = 3*row + col):
+//   F32: float4 [4][3][stride];  F16: uint2 [4][3][stride]  (rows 0-1, 6 complex;
+//        row 2 is rebuilt as conj(row0 x row1))
+//   F64: double2 [4][9][stride]  (all three rows)
 //   DF:  float4 [4][9][stride] (re.hi, re.lo, im.hi, im.lo), all three rows
-// Except for DF, row 2 is rebuilt as conj(row0 x row1).
 template <int P> struct LinkIO;
 
 template <typename R>
@@ -409,18 +458,21 @@ __device__ __forceinline__ void reconstruct_row2(cx<R> (&u)[9])
     u[8] = {c.re, -c.im};
 }
 
+// FP64 links keep all three rows as given (18 reals): the FP64 hop is bound
+// by the FP64 pipe (1/57 of the FP32 rate on GB300), where rebuilding row 2
+// costs about 10% of its instructions, and not by memory, where the extra
+// 48 B per link are cheap.
 template <> struct LinkIO<WL_F64> {
     using R = double;
-    static constexpr int chunks = 6;
+    static constexpr int chunks = 9;
     static __device__ __forceinline__ void load(const void *dirbase, int stride, int i, cx<R> (&u)[9])
     {
         const double2 *p = static_cast<const double2 *>(dirbase);
 #pragma unroll
-        for (int k = 0; k < 6; ++k) {
+        for (int k = 0; k < 9; ++k) {
             double2 t = __ldg(p + (size_t)k * stride + i);
             u[k] = {t.x, t.y};
         }
-        reconstruct_row2(u);
     }
 };
 template <> struct LinkIO<WL_F32> {
@@ -513,18 +565,84 @@ __device__ __forceinline__ void block_sum(double (&v)[NV])
     __syncthreads();
 }
 
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide sum of NV FP32 values per thread, result in FP64 (valid in
+// thread 0): FP32 inside each warp, FP64 across the warps.  The per-thread
+// values are FP32 partials over one site, so 32 of them summed in FP32 stay
+// in the same accuracy class, and GB300 runs FP64 adds at 1/57 of the FP32
+// rate: a warp sum of doubles costs each thread five of them per value.
+template <int NV>
+__device__ __forceinline__ void block_sum(float (&vf)[NV], double (&v)[NV])
+{
+    __shared__ double sh[32][NV];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) vf[k] = warp_sum(vf[k]);
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) sh[warp][k] = (double)vf[k];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double t = lane < nw ? sh[lane][k] : 0.0;
+            v[k] = warp_sum(t);
+        }
+    }
+    __syncthreads();
+}
+
+// Per-thread reduction type: FP32 partials for FP32 arithmetic (FP16
+// storage included), FP64 otherwise (FP64 and double-float data).
+template <typename R> struct RedType { using T = double; };
+template <> struct RedType<float> { using T = float; };
+template <typename T, typename R>
+__device__ __forceinline__ T red_cast(R x)
+{
+    if constexpr (sizeof(T) == sizeof(float)) return x;
+    else return to_double(x);
+}
+
 // Grid-wide deterministic reduction without a second launch ("last block"
 // pattern): every block deposits its NV partial sums in partials[blk][NV];
 // the block that arrives last (atomic ticket) adds the partials in block
 // order and returns true in all of its threads with the totals in tot
 // (valid in thread 0).  The ticket is reset to zero for the next use.
-// `nblk` blocks take part, numbered blk = 0..nblk-1.
+// `nblk` blocks take part, numbered blk = 0..nblk-1.  Per-thread values
+// may be FP32 (summed as block_sum above) or FP64; blocks combine in FP64.
+template <int NV>
+__device__ __forceinline__ bool grid_finish(double (&v)[NV], double *partials, unsigned *ticket, int blk,
+                                            int nblk, double (&tot)[NV]);
+
+template <int NV>
+__device__ __forceinline__ bool grid_sum(float (&vf)[NV], double *partials, unsigned *ticket, int blk,
+                                         int nblk, double (&tot)[NV])
+{
+    double v[NV];
+    block_sum<NV>(vf, v);
+    return grid_finish<NV>(v, partials, ticket, blk, nblk, tot);
+}
+
 template <int NV>
 __device__ __forceinline__ bool grid_sum(double (&v)[NV], double *partials, unsigned *ticket, int blk,
                                          int nblk, double (&tot)[NV])
 {
-    __shared__ bool is_last;
     block_sum<NV>(v);
+    return grid_finish<NV>(v, partials, ticket, blk, nblk, tot);
+}
+
+template <int NV>
+__device__ __forceinline__ bool grid_finish(double (&v)[NV], double *partials, unsigned *ticket, int blk,
+                                            int nblk, double (&tot)[NV])
+{
+    __shared__ bool is_last;
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int k = 0; k < NV; ++k) partials[(size_t)blk * NV + k] = v[k];

@@ -35,11 +35,22 @@ template <> struct Proj<1> { static constexpr int a1 = 0, c1 = 2, a2 = 1, c2 = 0
 template <> struct Proj<2> { static constexpr int a1 = 1, c1 = 3, a2 = 0, c2 = 1; };  // (0,-i,0,1) (i,0,1,0)
 template <> struct Proj<3> { static constexpr int a1 = 1, c1 = 0, a2 = 0, c2 = 0; };  // (0,1,0,1) (1,0,1,0)
 
-// acc += (neg ? -1 : 1) * L psi (1 -/+ gamma_MU) with L = u (ADJ = false) or
-// u^dag.  PLUS = 0 selects (1 - gamma_MU), PLUS = 1 selects (1 + gamma_MU).
-// Spinor component k = 3*spin + colour.
+// acc += sc * L psi (1 -/+ gamma_MU) with L = u (ADJ = false) or u^dag.
+// PLUS = 0 selects (1 - gamma_MU), PLUS = 1 selects (1 + gamma_MU).
+// Spinor component k = 3*spin + colour.  sc carries the time-boundary sign
+// and, for FP16 storage, the neighbour's per-site norm (psi then holds the
+// unscaled halves): shrink and colour multiplication are linear, so the
+// scale is applied once, in the multiply-adds of the expand, instead of to
+// the 24 loaded values.  For sc = +-1 the fused multiply-add is exactly
+// the add or subtract it replaces.
+template <typename R>
+__device__ __forceinline__ cx<R> cfma(R s, cx<R> z, cx<R> a)
+{
+    return {fma(s, z.re, a.re), fma(s, z.im, a.im)};
+}
+
 template <int MU, int PLUS, bool ADJ, typename R>
-__device__ __forceinline__ void transport(cx<R> (&acc)[12], const cx<R> (&psi)[12], const cx<R> (&u)[9], bool neg)
+__device__ __forceinline__ void transport(cx<R> (&acc)[12], const cx<R> (&psi)[12], const cx<R> (&u)[9], R sc)
 {
     constexpr int A1 = Proj<MU>::a1, A2 = Proj<MU>::a2;
     constexpr int C1 = (Proj<MU>::c1 + 2 * PLUS) & 3, C2 = (Proj<MU>::c2 + 2 * PLUS) & 3;
@@ -66,16 +77,16 @@ __device__ __forceinline__ void transport(cx<R> (&acc)[12], const cx<R> (&psi)[1
                 s2 = conjmad(u[3 * b + a], h2[b], s2);
             }
         }
-        w1[a] = neg ? cx<R>{-s1.re, -s1.im} : s1;
-        w2[a] = neg ? cx<R>{-s2.re, -s2.im} : s2;
+        w1[a] = s1;
+        w2[a] = s2;
     }
-    // expand: res_s += w_k v_k^dag[s]
+    // expand: res_s += sc w_k v_k^dag[s]
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        acc[3 * A1 + c] = acc[3 * A1 + c] + uphase<C1>(w1[c]);
-        acc[9 + c] = acc[9 + c] + w1[c];
-        acc[3 * A2 + c] = acc[3 * A2 + c] + uphase<C2>(w2[c]);
-        acc[6 + c] = acc[6 + c] + w2[c];
+        acc[3 * A1 + c] = cfma(sc, uphase<C1>(w1[c]), acc[3 * A1 + c]);
+        acc[9 + c] = cfma(sc, w1[c], acc[9 + c]);
+        acc[3 * A2 + c] = cfma(sc, uphase<C2>(w2[c]), acc[3 * A2 + c]);
+        acc[6 + c] = cfma(sc, w2[c], acc[6 + c]);
     }
 }
 
@@ -136,9 +147,9 @@ __device__ __forceinline__ void hop_dir(const HopArgs &a, int i, const Coord &c,
     for (int r = 0; r < NB; ++r) {
         if (NB > 1 && r0 + r >= a.nrhs) break;
         cx<R> psi[12];
-        SpinorIO<P>::template load<CG>(static_cast<const char *>(a.in) + (size_t)(r0 + r) * a.rhs_bytes, g.stride, fwd,
-                                       psi);
-        transport<MU, DAG ? 1 : 0, false>(acc[r], psi, u, sf);
+        const R n = SpinorIO<P>::template load_unscaled<CG>(
+            static_cast<const char *>(a.in) + (size_t)(r0 + r) * a.rhs_bytes, g.stride, fwd, psi);
+        transport<MU, DAG ? 1 : 0, false>(acc[r], psi, u, sf ? -n : n);
     }
     // backward: U_mu(n-mu)^dag psi_{n-mu} (1 + gamma_mu)   [dagger: (1 - gamma_mu)]
     LinkIO<P>::load(static_cast<const char *>(a.links_in) + dir_off, g.stride, bwd, u);
@@ -146,9 +157,9 @@ __device__ __forceinline__ void hop_dir(const HopArgs &a, int i, const Coord &c,
     for (int r = 0; r < NB; ++r) {
         if (NB > 1 && r0 + r >= a.nrhs) break;
         cx<R> psi[12];
-        SpinorIO<P>::template load<CG>(static_cast<const char *>(a.in) + (size_t)(r0 + r) * a.rhs_bytes, g.stride, bwd,
-                                       psi);
-        transport<MU, DAG ? 0 : 1, true>(acc[r], psi, u, sb);
+        const R n = SpinorIO<P>::template load_unscaled<CG>(
+            static_cast<const char *>(a.in) + (size_t)(r0 + r) * a.rhs_bytes, g.stride, bwd, psi);
+        transport<MU, DAG ? 0 : 1, true>(acc[r], psi, u, sb ? -n : n);
     }
 }
 
@@ -465,7 +476,7 @@ __global__ void __launch_bounds__(128, MINB) k_hop_prefetch_f32(HopArgs a, EpiSt
     b.in = static_cast<const char *>(a.in) + (size_t)r * a.rhs_bytes;
     cx<float> acc[1][12];
 #pragma unroll
-    for (int k = 0; k < 12; ++k) acc[0][k] = {0.f, 0.f};
+    for (int k = 0; k < 12; ++k) acc[0][k] = acc_zero<float>();
     hop_accumulate_prefetch_f32<DAG>(b, i, acc[0]);
     epi.template operator()<WL_F32, 1>(a, i, true, r, acc);
 }
@@ -565,9 +576,9 @@ __device__ __forceinline__ void async_step(const HopArgs &a, const AsyncCtx &c, 
             psi[2 * k + 1] = {t.z, t.w};
         }
         if constexpr (FWD)
-            transport<MU, DAG ? 1 : 0, false>(acc[r], psi, u, MU == 3 && c.neg_f);
+            transport<MU, DAG ? 1 : 0, false>(acc[r], psi, u, MU == 3 && c.neg_f ? -1.f : 1.f);
         else
-            transport<MU, DAG ? 0 : 1, true>(acc[r], psi, u, MU == 3 && c.neg_b);
+            transport<MU, DAG ? 0 : 1, true>(acc[r], psi, u, MU == 3 && c.neg_b ? -1.f : 1.f);
     }
 }
 
@@ -627,7 +638,7 @@ __global__ void __launch_bounds__(128, MINB) k_hop_async(HopArgs a, EpiStore epi
 #pragma unroll
     for (int r = 0; r < NB; ++r)
 #pragma unroll
-        for (int k = 0; k < 12; ++k) acc[r][k] = {0.f, 0.f};
+        for (int k = 0; k < 12; ++k) acc[r][k] = acc_zero<float>();
     if (active) hop_accumulate_async<DAG, NB>(a, i, r0, nr, stage, acc);
     epi.template operator()<WL_F32, NB>(a, i, active, r0, acc);
 }
@@ -659,7 +670,7 @@ __global__ void __launch_bounds__(128, MINB) k_hop_rolled(HopArgs a, EpiStore ep
     b.in = static_cast<const char *>(a.in) + (size_t)r * a.rhs_bytes;
     cx<R> acc[1][12];
 #pragma unroll
-    for (int k = 0; k < 12; ++k) acc[0][k] = {R(0), R(0)};
+    for (int k = 0; k < 12; ++k) acc[0][k] = acc_zero<R>();
     hop_accumulate_rolled<P, DAG>(b, i, acc[0]);
     epi.template operator()<P, 1>(a, i, true, r, acc);
 }
@@ -682,7 +693,7 @@ __global__ void __launch_bounds__(128, MINB) k_hop(HopArgs a, EpiStore epi)
 #pragma unroll
     for (int r = 0; r < NB; ++r)
 #pragma unroll
-        for (int k = 0; k < 12; ++k) acc[r][k] = {R(0), R(0)};
+        for (int k = 0; k < 12; ++k) acc[r][k] = acc_zero<R>();
     hop_accumulate<P, DAG, NB>(a, i, r0, acc);
     epi.template operator()<P, NB>(a, i, true, r0, acc);
 }
@@ -699,13 +710,14 @@ __device__ __forceinline__ void hop_reduce_body(const HopArgs &a, const EpiReduc
     const int i = sb * blockDim.x + threadIdx.x;
     const bool active = i < a.g.Vh;
     const double coef = e.coef_dev ? __ldcg(e.coef_dev) : e.coef;
-    double red[NV];
+    using RedT = typename RedType<R>::T;
+    RedT red[NV];
 #pragma unroll
-    for (int k = 0; k < NV; ++k) red[k] = 0.0;
+    for (int k = 0; k < NV; ++k) red[k] = RedT(0);
     if (active) {
         cx<R> acc[1][12];
 #pragma unroll
-        for (int k = 0; k < 12; ++k) acc[0][k] = {R(0), R(0)};
+        for (int k = 0; k < 12; ++k) acc[0][k] = acc_zero<R>();
         if constexpr (P == WL_DF) {
             // double-float: the rolled transporter loop (the unrolled one
             // overflows the instruction cache)
@@ -734,9 +746,9 @@ __device__ __forceinline__ void hop_reduce_body(const HopArgs &a, const EpiReduc
                 d = conjmad(rh[k], o[k], d);
                 n = fma(o[k].re, o[k].re, fma(o[k].im, o[k].im, n));
             }
-            red[0] = to_double(d.re);
-            red[1] = to_double(d.im);
-            red[2] = to_double(n);
+            red[0] = red_cast<RedT>(d.re);
+            red[1] = red_cast<RedT>(d.im);
+            red[2] = red_cast<RedT>(n);
         } else if constexpr (KIND == 1) {
             cx<R> d = {R(0), R(0)};
             R n = R(0);
@@ -745,14 +757,14 @@ __device__ __forceinline__ void hop_reduce_body(const HopArgs &a, const EpiReduc
                 d = conjmad(o[k], xv[k], d);
                 n = fma(o[k].re, o[k].re, fma(o[k].im, o[k].im, n));
             }
-            red[0] = to_double(d.re);
-            red[1] = to_double(d.im);
-            red[2] = to_double(n);
+            red[0] = red_cast<RedT>(d.re);
+            red[1] = red_cast<RedT>(d.im);
+            red[2] = red_cast<RedT>(n);
         } else {
             R n = R(0);
 #pragma unroll
             for (int k = 0; k < 12; ++k) n = fma(o[k].re, o[k].re, fma(o[k].im, o[k].im, n));
-            red[2] = to_double(n);
+            red[2] = red_cast<RedT>(n);
         }
     }
     double tot[NV];

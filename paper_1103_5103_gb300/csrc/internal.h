@@ -75,7 +75,7 @@ struct wl_gauge {
     wl::Workspace ws;
     std::mutex mu;      // one solve at a time per handle (shared workspace)
     int profiling = 0;
-    wl_kernel_profile prof[3] = {};
+    wl_kernel_profile prof[4] = {};   // inner hop per precision index (F64, F32, F16); [3] outer residual hop
 };
 
 namespace wl {

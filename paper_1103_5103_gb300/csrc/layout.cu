@@ -168,7 +168,8 @@ __global__ void __launch_bounds__(kFullSites) k_import_full(Geom g, const double
     }
 }
 
-// Pack rows 0 and 1 of U_mu at the sites of one parity.
+// Pack U_mu at the sites of one parity: rows 0 and 1 for F32 and F16, all
+// three rows for F64 (as given) and DF (row 2 formed in FP64).
 template <int P>
 __global__ void k_pack_links(Geom g, const double2 *__restrict__ U, void *out, int parity)
 {
@@ -182,7 +183,7 @@ __global__ void k_pack_links(Geom g, const double2 *__restrict__ U, void *out, i
     char *dir = static_cast<char *>(out) + (size_t)mu * link_dir_bytes(P, g.stride);
     if (P == WL_F64) {
         double2 *p = reinterpret_cast<double2 *>(dir);
-        for (int k = 0; k < 6; ++k) p[(size_t)k * g.stride + i] = u[k];
+        for (int k = 0; k < 9; ++k) p[(size_t)k * g.stride + i] = u[k];
     } else if (P == WL_F32) {
         float4 *p = reinterpret_cast<float4 *>(dir);
         for (int k = 0; k < 3; ++k) {
@@ -333,11 +334,12 @@ extern "C" int wl_params_default(wl_solver_params *p)
     p->rhs_block = 0;
     p->graph_iters = 8;
     p->eo = 1;
-    p->outer_prec = WL_DF;
+    p->outer_prec = WL_F64;
     p->shadow = nullptr;
     p->guess_max = 0;
     p->reliable = 0;
     p->inner_solver = WL_SOLVER_BICGSTAB;
+    p->verify_full = 0;
     return WL_OK;
 }
 

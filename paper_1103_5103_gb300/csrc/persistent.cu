@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(kPersistBlock, 1) k_bicgstab_persistent(Persis
             h.in = A.p.ptr;
             cx<R> acc[1][12];
 #pragma unroll
-            for (int k = 0; k < 12; ++k) acc[0][k] = {R(0), R(0)};
+            for (int k = 0; k < 12; ++k) acc[0][k] = acc_zero<R>();
             hop_accumulate<P, false, 1, true>(h, i, r, acc);
             SpinorIO<P>::store(A.tmp.rhs(r), g.stride, i, acc[0]);
         }
@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(kPersistBlock, 1) k_bicgstab_persistent(Persis
             if (i < g.Vh) {
                 cx<R> acc[1][12];
 #pragma unroll
-                for (int k = 0; k < 12; ++k) acc[0][k] = {R(0), R(0)};
+                for (int k = 0; k < 12; ++k) acc[0][k] = acc_zero<R>();
                 hop_accumulate<P, false, 1, true>(A.hop_even, i, r, acc);
                 cx<R> pv[12], o[12], rh[12];
                 SpinorIO<P>::template load<true>(A.p.rhs(r), g.stride, i, pv);
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(kPersistBlock, 1) k_bicgstab_persistent(Persis
             h.in = A.s.ptr;
             cx<R> acc[1][12];
 #pragma unroll
-            for (int k = 0; k < 12; ++k) acc[0][k] = {R(0), R(0)};
+            for (int k = 0; k < 12; ++k) acc[0][k] = acc_zero<R>();
             hop_accumulate<P, false, 1, true>(h, i, r, acc);
             SpinorIO<P>::store(A.tmp.rhs(r), g.stride, i, acc[0]);
         }
@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(kPersistBlock, 1) k_bicgstab_persistent(Persis
             if (i < g.Vh) {
                 cx<R> acc[1][12];
 #pragma unroll
-                for (int k = 0; k < 12; ++k) acc[0][k] = {R(0), R(0)};
+                for (int k = 0; k < 12; ++k) acc[0][k] = acc_zero<R>();
                 hop_accumulate<P, false, 1, true>(A.hop_even, i, r, acc);
                 cx<R> sv[12], o[12];
                 SpinorIO<P>::template load<true>(A.s.rhs(r), g.stride, i, sv);

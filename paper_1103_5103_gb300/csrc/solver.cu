@@ -372,10 +372,12 @@ static double default_inner_tol(int prec)
 // caller has already put b_prec - M_prec x into dc_r64: the first check
 // uses it without hops; it never declares convergence by itself (that needs
 // a hop-based check, which also produces D_oe x for the reconstruction).
+// rn2_out (optional) receives ||b_prec - M_prec x||^2 of each rhs's final x
+// from its last hop-based check.
 static int eo_defect_correction(wl_gauge *g, const Vec &bprec, const Vec &x64, double kappa,
                                 const wl_solver_params &prm, const std::vector<double> &bnorm,
                                 std::vector<wl_solver_stats> &stats, cudaStream_t s, const Vec *y_out = nullptr,
-                                bool r0_given = false)
+                                bool r0_given = false, std::vector<double> *rn2_out = nullptr)
 {
     const Geom &geo = g->lat->geom;
     const int nrhs = bprec.nrhs;
@@ -407,17 +409,37 @@ static int eo_defect_correction(wl_gauge *g, const Vec &bprec, const Vec &x64, d
     WL_CUDA_TRY(cudaMemsetAsync(in.sc.outer_done, 0, sizeof(int) * nrhs, s));
     int total_restarts = 0;
     bool lincomb_check = r0_given;
+    // live timing of the first residual hop of every check (wl_profile_enable)
+    struct Ev {
+        cudaEvent_t e[2] = {nullptr, nullptr};
+        ~Ev() { for (auto x : e) if (x) cudaEventDestroy(x); }
+    } ev;
+    if (g->profiling)
+        for (auto &x : ev.e) WL_CUDA_TRY(cudaEventCreate(&x));
     for (;;) {
         // r = bprec - x + kappa^2 D_eo D_oe x for the rhs still iterating;
         // D_oe x stays in tmp64 (the reconstruction uses the last one)
+        int n_hop = 0;  // rhs the residual hops process
         if (!lincomb_check) {
+            for (int r = 0; r < nrhs; ++r) n_hop += outer_done[r] ? 0 : 1;
+            if (ev.e[0]) WL_CUDA_TRY(cudaEventRecord(ev.e[0], s));
             WL_TRY(hop_ex(g, x64, tmp64, nullptr, 0.0, nullptr, 0.0, 1.0, WL_ODD, 0, 0, in.sc.outer_done, 1, s));
+            if (ev.e[1]) WL_CUDA_TRY(cudaEventRecord(ev.e[1], s));
             WL_TRY(hop_ex(g, tmp64, r64, &bprec, 1.0, &x64, -1.0, k2, WL_EVEN, 0, 0, in.sc.outer_done, 1, s,
                           y_out));
         }
         WL_TRY(blas_norm2(geo, r64, in.sc.norms, in.sc.partials, in.sc.tickets, s));
         WL_CUDA_TRY(cudaMemcpyAsync(h_rn2, in.sc.norms, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
         WL_CUDA_TRY(cudaStreamSynchronize(s));
+        if (ev.e[0] && n_hop > 0) {
+            float ms = 0.f;
+            WL_CUDA_TRY(cudaEventElapsedTime(&ms, ev.e[0], ev.e[1]));
+            wl_kernel_profile &P = g->prof[3];
+            P.launches += 1;
+            P.ms += ms;
+            P.site_rhs += (double)geo.Vh * n_hop;
+            P.sites += (double)geo.Vh;
+        }
         int n_active = 0;
         for (int r = 0; r < nrhs; ++r) {
             const double rn = std::sqrt(h_rn2[r]);
@@ -489,6 +511,7 @@ static int eo_defect_correction(wl_gauge *g, const Vec &bprec, const Vec &x64, d
         stats[r].matvecs = 2 * iters[r] + restarts[r] + 1;
         stats[r].restarts = restarts[r];
     }
+    if (rn2_out) rn2_out->assign(h_rn2, h_rn2 + nrhs);
     (void)total_restarts;
     return WL_OK;
 }
@@ -581,6 +604,15 @@ struct AsyncExport {
 // with bprec = b_e + kappa D_eo b_o prepared by the caller: solve, rebuild
 // x_o = b_o + kappa D_oe x_e, compute the full-lattice residual, export x
 // (on s, or on the side stream of ax).
+//
+// Full-lattice residual (Section 6.2.3).  With x_o rebuilt from the D_oe x_e
+// of the last check, r_o = b_o - x_o + kappa D_oe x_e is the rounding of that
+// rebuild (the reconstruction pass returns its norm) and
+//   r_e = b_e - x_e + kappa D_eo x_o = b_prec - M_prec x_e + kappa D_eo (x_o - b_o - kappa D_oe x_e),
+// i.e. the preconditioned residual of the last check plus kappa D_eo applied
+// to that rounding, below 1e-15 of ||x||.  So ||r||^2 = ||r_prec||^2 + ||r_o||^2
+// needs no further hop; prm.verify_full recomputes r_e with one more hop
+// D_eo x_o instead.
 static int solve_one_mass(wl_gauge *g, const Vec &be, const Vec &bo, const Vec &bprec, const Vec &xe, double m0,
                           const wl_solver_params &prm, const std::vector<double> &bnorm2, void *const *x_out,
                           int x_out_stride, std::vector<wl_solver_stats> &stats, cudaStream_t s,
@@ -594,7 +626,8 @@ static int solve_one_mass(wl_gauge *g, const Vec &be, const Vec &bo, const Vec &
     WL_TRY(make_vec(g, ax ? (slot ? "mm_xo1" : "mm_xo0") : "mm_xo", xe.prec, nrhs, &xo));
     std::vector<double> bnorm(nrhs);
     for (int r = 0; r < nrhs; ++r) bnorm[r] = std::sqrt(bnorm2[r]);
-    WL_TRY(eo_defect_correction(g, bprec, xe, kappa, prm, bnorm, stats, s, y_out, r0_given));
+    std::vector<double> rn2;
+    WL_TRY(eo_defect_correction(g, bprec, xe, kappa, prm, bnorm, stats, s, y_out, r0_given, &rn2));
     // The last residual check left D_oe x_e (final x_e) in dc_tmp64:
     // x_o = b_o + kappa D_oe x_e and the odd residual in one vector pass.
     Vec dx;
@@ -606,8 +639,12 @@ static int solve_one_mass(wl_gauge *g, const Vec &be, const Vec &bo, const Vec &
     std::vector<double> ro2(nrhs);
     WL_CUDA_TRY(cudaMemcpyAsync(ro2.data(), sc.norms, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
     WL_CUDA_TRY(cudaStreamSynchronize(s));
-    std::vector<double> rel;
-    WL_TRY(full_relres(g, be, bo, xe, xo, kappa, bnorm, rel, s, &ro2));
+    std::vector<double> rel(nrhs);
+    if (prm.verify_full) {
+        WL_TRY(full_relres(g, be, bo, xe, xo, kappa, bnorm, rel, s, &ro2));
+    } else {
+        for (int r = 0; r < nrhs; ++r) rel[r] = bnorm[r] > 0 ? std::sqrt(rn2[r] + ro2[r]) / bnorm[r] : 0.0;
+    }
     std::vector<void *> outs(nrhs);
     for (int r = 0; r < nrhs; ++r) {
         stats[r].mass = m0;
@@ -632,7 +669,8 @@ static int check_params(const wl_gauge *g, const wl_solver_params *p)
         (p->reliable != 0 && p->reliable != 1) ||
         (p->inner_solver != WL_SOLVER_BICGSTAB && p->inner_solver != WL_SOLVER_CG) ||
         (p->inner_solver == WL_SOLVER_CG && (p->reliable || p->mode == WL_MODE_PERSISTENT)) ||
-        p->rhs_block < 0 || p->rhs_block > 4 || (p->outer_prec != WL_F64 && p->outer_prec != WL_DF)) {
+        p->rhs_block < 0 || p->rhs_block > 4 || (p->outer_prec != WL_F64 && p->outer_prec != WL_DF) ||
+        (p->verify_full != 0 && p->verify_full != 1)) {
         set_error("solver parameters out of range");
         return WL_ERR_ARG;
     }
@@ -685,7 +723,7 @@ extern "C" int wl_profile_enable(wl_gauge *g, int on)
     return WL_OK;
 }
 
-extern "C" int wl_profile_read(wl_gauge *g, wl_kernel_profile out[3])
+extern "C" int wl_profile_read(wl_gauge *g, wl_kernel_profile out[4])
 {
     if (!g || !out) { set_error("wl_profile_read: NULL"); return WL_ERR_ARG; }
     std::lock_guard<std::mutex> lock(g->mu);

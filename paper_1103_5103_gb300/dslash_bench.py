@@ -18,7 +18,7 @@ import torch
 
 from . import api, synth
 
-LINK_B = {"f64": 96, "df": 144, "f32": 48, "f16": 24}  # double-float links keep all three rows
+LINK_B = {"f64": 144, "df": 144, "f32": 48, "f16": 24}  # FP64 and double-float links keep all three rows
 SPINOR_B = {"f64": 192, "df": 192, "f32": 96, "f16": 52}
 
 

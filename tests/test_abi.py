@@ -36,8 +36,8 @@ def test_host_only_calls():
     p = api.params()
     assert p.tol == 1e-10 and p.inner_prec == api.F32 and p.eo == 1
     # the fields after the pointer member land where the C struct has them
-    assert p.outer_prec == api.DF and p.shadow is None and p.guess_max == 0 and p.reliable == 0
-    assert p.inner_solver == api.SOLVER_BICGSTAB
+    assert p.outer_prec == api.F64 and p.shadow is None and p.guess_max == 0 and p.reliable == 0
+    assert p.inner_solver == api.SOLVER_BICGSTAB and p.verify_full == 0
     assert p.guess == api.GUESS_POLY and p.mode == api.MODE_GRAPH and p.graph_iters == 8
     lat = api.Lattice((4, 4, 4, 8))
     assert lat.spinor_bytes("f64") == 192 * 256 and lat.spinor_bytes("f32") == 96 * 256

@@ -1,8 +1,9 @@
 """The reference arm of bench.py (`--impl reference`) times the FP64 oracle
 on the host. These CPU tests pin the JSON line it prints: the keys the
-benchmark contract needs, the scaling of the sampled time per BiCGstab
-iteration by the step's iteration count, rank 0 alone printing, and the
-`unavailable` line for a workload without a recorded iteration count."""
+benchmark contract needs, the scaling of the sampled oracle times by the
+oracle's own iteration counts (stored by an oracle-only script under
+tests/golden, never taken from the optimised arm), rank 0 alone printing,
+and the `unavailable` line for a workload without stored counts."""
 import argparse
 import json
 import os
@@ -27,33 +28,55 @@ def _tiny_cfg():
     return cfg
 
 
+COUNTS = {"iterations": [10.0, 8.0, 3.0], "restarts": [2.0, 1.0, 0.0], "sources": [0, 11],
+          "file": "tests/golden/c3_oracle_multimass.json"}
+
+
 def test_reference_line_keys_and_scaling(monkeypatch, capsys):
     monkeypatch.delenv("RANK", raising=False)
     monkeypatch.delenv("WORLD_SIZE", raising=False)
-    per_iter = [0.5, 0.5, 0.5, 2.0, 4.0]   # warm-up samples first, then the timed ones
+    samples = [(1.0, 2.0, 9.0)] * 3 + [(1.0, 2.5, 9.0), (2.0, 3.5, 9.0)]  # warm-up first, then timed
     calls = []
 
-    def fake_sample(cfg, U, bs, target_s=15.0):
-        calls.append(target_s)
-        return per_iter[len(calls) - 1], 3, 1.0
+    def fake_sample(cfg, U, b):
+        calls.append(1)
+        return samples[len(calls) - 1]
 
     monkeypatch.setattr(bench, "oracle_sample", fake_sample)
+    monkeypatch.setattr(bench, "oracle_counts", lambda config: COUNTS)
+    monkeypatch.setattr(bench, "oracle_threads", lambda: 4)
     bench.run_reference(_args(), _tiny_cfg())
     line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
-    n = bench.REF_ITERS_PER_STEP["c3"]
     assert len(calls) == 5                      # 3 warm-up + 2 timed samples
+
+    def step(t_mprec, t_iter):   # 12 sources; per mass iterations x t_iter + (4.5 + restarts) x t_mprec
+        return 12 * sum(i * t_iter + (4.5 + r) * t_mprec for i, r in zip(COUNTS["iterations"], COUNTS["restarts"]))
     assert line["impl"] == "reference"
-    assert line["value"] == pytest.approx(n * (2.0 + 4.0) / 2)   # mean of the timed steps only
+    assert line["value"] == pytest.approx((step(1.0, 2.5) + step(2.0, 3.5)) / 2)   # timed steps only
     assert line["ms_per_step"] == pytest.approx(line["value"] * 1e3)
     assert line["unit"] == bench.UNIT and line["metric"] == bench.METRIC
     assert line["higher_is_better"] is False and line["steps"] == 2 and line["warmup"] == 3
-    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
-    assert line["cpu_baseline"]["value"] == line["value"] and line["cpu_baseline"]["sample"]
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 4
+    assert line["cpu_baseline"]["value"] == line["value"]
+    sample = line["cpu_baseline"]["sample"]
+    assert "oracle's own 252 iterations" in sample and COUNTS["file"] in sample
     assert line["e2e"] == {"value": line["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
     assert line["config"]["workload"] == bench.CONFIGS["c3"]["name"]
-    # each sample is bounded so that the whole run takes about 90 s
-    assert all(5.0 <= t <= 90.0 for t in calls)
+
+
+def test_oracle_counts_come_from_the_oracle_only_golden_file():
+    """The counts the reference arm scales by are the oracle's own, stored
+    by tests/golden/make_oracle_multimass.py (which imports only oracle/ and
+    the input generator) for the 24^3x64 and 48^3x96 workloads."""
+    src = open(os.path.join(ROOT, "tests", "golden", "make_oracle_multimass.py")).read()
+    assert "from oracle import oracle" in src and "api" not in src.replace("argparse", "")
+    for config, n_mass in (("c3", 8), ("c5", 16)):
+        c = bench.oracle_counts(config)
+        if c is None:
+            pytest.skip(f"no stored oracle counts for {config}")
+        assert len(c["iterations"]) == n_mass and all(v > 0 for v in c["iterations"])
+        assert len(c["restarts"]) == n_mass and c["sources"]
 
 
 def test_reference_other_ranks_print_nothing(monkeypatch, capsys):

@@ -148,13 +148,22 @@ def test_profiling_counts_hop_launches(api, mode):
     n0 = api.launch_count()
     prm = api.params(mode=api.MODE_GRAPH if mode == "graph" else api.MODE_HOST)
     xs, stats = api.multimass_solve(g, [b, b], [0.3, 0.1], prm)
-    prof = api.profile_read(g)["f32"]
+    both = api.profile_read(g)
+    prof, outer = both["f32"], both["outer"]
     api.profile_enable(g, False)
     iters = stats[0][0]["iterations"] + stats[0][1]["iterations"]
     assert 0 < prof["launches"] <= iters
     assert prof["launches"] >= iters // 2
     assert 0 < prof["ms"] / prof["launches"] < 10.0
     assert prof["site_rhs"] == 2 * prof["sites"] == 2 * prof["launches"] * lat.volume // 2
+    # the outer residual hop: one timed launch per hop-based check, covering
+    # the rhs still iterating (at least one check per mass, each with one or
+    # both rhs)
+    restarts = sum(st["restarts"] for st in stats[0])
+    assert 2 <= outer["launches"] and restarts <= outer["launches"] <= restarts + 2
+    assert outer["sites"] == outer["launches"] * lat.volume // 2
+    assert outer["sites"] <= outer["site_rhs"] <= 2 * outer["sites"]
+    assert 0 < outer["ms"] / outer["launches"] < 10.0
     assert api.launch_count() - n0 >= 7 * prof["launches"]
     # a following solve is unaffected
     _, st2 = api.multimass_solve(g, [b], [0.2], api.params())
@@ -257,11 +266,11 @@ def test_bicgstab_m_point_source_without_shadow_reports_breakdown(api):
 
 
 def test_bicgstab_m_needs_links_of_its_precision(api):
-    """Double-float BiCGstab-M (the default outer_prec) on a handle with
-    FP64 links only, and an inner precision as outer_prec, are argument
-    errors."""
+    """FP64 BiCGstab-M (the default outer_prec) on a handle with
+    double-float links only, and an inner precision as outer_prec, are
+    argument errors."""
     dims = (4, 4, 4, 4)
-    U, lat, g = _gauge(api, dims, 0.3, 1, precs=("f64",))
+    U, lat, g = _gauge(api, dims, 0.3, 1, precs=("df",))
     b = _cuda(synth.z2_source(dims, 2))
     xs = [torch.empty_like(b) for _ in range(2)]
     for prm in (api.params(), api.params(outer_prec="f32")):
@@ -491,3 +500,34 @@ def test_nan_source_breaks_down_alone(api):
     with pytest.raises(api.WilsonError) as e:
         api.multimass_solve(g, [_cuda(nan)], masses, api.params())
     assert e.value.status == api.WL_ERR_BREAKDOWN
+
+
+@pytest.mark.parametrize("outer", ["f64", "df"])
+def test_full_residual_from_last_check_equals_recomputed(api, outer):
+    """The reported full-lattice residual takes its even half from the last
+    outer check, b_prec - M_prec x_e (Section 6.2.3: equal to b_e - x_e +
+    kappa D_eo x_o up to the rounding of the rebuilt x_o).  Recomputing it
+    with the extra hop D_eo x_o (verify_full = 1) gives the same figure to
+    well under a percent, the same solutions, and both agree with the
+    oracle's full-lattice residual of the returned x."""
+    dims = (8, 8, 8, 16)
+    U, lat, g = _gauge(api, dims, 0.5, 71, precs=("f64", "f32", "f16", "df"))
+    bs = [synth.point_source(dims, 1, 1), synth.z2_source(dims, 72)]
+    masses = [0.4, 0.2, 0.1]
+    res = {}
+    for vf in (0, 1):
+        xs, st = api.multimass_solve(g, [_cuda(b) for b in bs], masses,
+                                     api.params(inner_prec="f16", outer_prec=outer, verify_full=vf))
+        res[vf] = (xs, st)
+    # double-float residuals carry about 48-bit rounding: a few 1e-15 of
+    # ||b||, a few 1e-4 of a 1e-11 residual
+    slack = {"f64": 1e-3, "df": 2e-2}[outer]
+    for r, b in enumerate(bs):
+        for i, m in enumerate(masses):
+            a, c = res[0][1][r][i]["true_relres"], res[1][1][r][i]["true_relres"]
+            assert 0 < a <= 1e-10 and 0 < c <= 1e-10, (r, m, a, c)
+            assert abs(a - c) <= slack * c, (r, m, a, c)
+            x0, x1 = res[0][0][r][i].cpu().numpy(), res[1][0][r][i].cpu().numpy()
+            assert rel(x1, x0) < 1e-14
+            o = O.true_relres(U, dims, b, x0, m)
+            assert abs(o - a) <= slack * o, (r, m, o, a)
