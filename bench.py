@@ -35,6 +35,7 @@ import statistics
 import subprocess
 import sys
 import tempfile
+import threading
 import time
 
 import numpy as np
@@ -393,33 +394,86 @@ def run_ours(args, cfg):
     mem0 = _used_bytes(torch)
     lat = api.Lattice(dims)
     U_dev = torch.from_numpy(U).to(dev)
-    # links of the two precisions the solve uses
-    g = api.Gauge(lat, U_dev, precs=tuple(sorted({inner, outer})))
     V = lat.volume
     nr, nm = len(bs_h), len(masses)
     nb = args.source_batch or cfg.get("source_batch", nr)
     batches = [list(range(i, min(nr, i + nb))) for i in range(0, nr, nb)]
+    # workers: batches solved at the same time, each on its own stream and
+    # gauge handle (a handle serialises its calls), with its own solution
+    # buffers; the FP64 residual hops of one overlap the inner solves of
+    # another when they run on a small grid (outer_blocks_per_sm)
+    nw = max(1, min(len(batches), args.streams or cfg.get("streams", 1)))
+    # links of the two precisions the solve uses
+    gs = [api.Gauge(lat, U_dev, precs=tuple(sorted({inner, outer}))) for _ in range(nw)]
+    g = gs[0]
     bs = [torch.from_numpy(b).to(dev) for b in bs_h]
-    # solution buffers for one batch of sources, reused by every batch
-    xs = [[torch.empty((V, 4, 3), dtype=torch.complex128, device=dev) for _ in masses] for _ in range(nb)]
+    # solution buffers for one batch of sources per worker, reused by its batches
+    xs_w = [[[torch.empty((V, 4, 3), dtype=torch.complex128, device=dev) for _ in masses] for _ in range(nb)]
+            for _ in range(nw)]
+    xs = xs_w[0]
+    ob = args.outer_blocks if args.outer_blocks >= 0 else cfg.get("outer_blocks", 0)
     prm = api.params(inner_prec=inner, rhs_block=args.rhs_block, outer_prec=outer,
                      inner_tol=args.inner_tol, reliable=int(args.reliable), guess_max=args.guess_max,
-                     verify_full=int(args.verify_full),
+                     verify_full=int(args.verify_full), outer_blocks_per_sm=ob if outer == "f64" else 0,
                      inner_solver=api.SOLVER_CG if args.inner_solver == "cg" else api.SOLVER_BICGSTAB,
                      mode={"graph": api.MODE_GRAPH, "persistent": api.MODE_PERSISTENT, "host": api.MODE_HOST}[args.mode])
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
+    wstreams = [stream] if nw == 1 else [torch.cuda.Stream(device=dev) for _ in range(nw)]
+    owner = {bi: bi % nw for bi in range(len(batches))}   # batch -> worker
 
-    def solve_batch(rows):
-        _, st = api.multimass_solve(g, [bs[r] for r in rows], masses, prm, xs=xs[:len(rows)])
+    def solve_batch(bi, srcs=None, outs=None):
+        w = owner[bi]
+        rows = batches[bi]
+        _, st = api.multimass_solve(gs[w], srcs or [bs[r] for r in rows], masses, prm,
+                                    xs=outs or xs_w[w][:len(rows)], stream=wstreams[w])
         return st
+
+    def run_batches(fn):
+        """fn(bi) for every batch: in order on one stream, or batch bi on
+        worker bi % nw, the workers in threads of their own (the library
+        releases the interpreter lock in every call).  The workers' streams
+        start after the work already queued on the main stream, and the
+        main stream waits for all of them."""
+        if nw == 1:
+            return [fn(bi) for bi in range(len(batches))]
+        ev0 = torch.cuda.Event()
+        ev0.record(stream)
+        for ws_ in wstreams:
+            ws_.wait_event(ev0)
+        out, errs = [None] * len(batches), []
+
+        def work(w):
+            try:
+                for bi in range(w, len(batches), nw):
+                    out[bi] = fn(bi)
+            except BaseException as e:   # re-raised in the main thread
+                errs.append(e)
+        th = [threading.Thread(target=work, args=(w,)) for w in range(nw)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        if errs:
+            raise errs[0]
+        for ws_ in wstreams:
+            ev = torch.cuda.Event()
+            ev.record(ws_)
+            stream.wait_event(ev)
+        return out
 
     def step():
         st = []
-        for rows in batches:
-            st += solve_batch(rows)
+        for r in run_batches(solve_batch):
+            st += r
         return st
 
+    # the first pass runs the batches one after another: each handle tunes
+    # its hop variants on its first call, with CUDA-event timings that
+    # concurrent work would disturb
+    for bi in range(len(batches)):
+        solve_batch(bi)
+        torch.cuda.synchronize()
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -427,7 +481,8 @@ def run_ours(args, cfg):
     # timed region: flush L2 before each step (inputs are also larger than L2)
     barrier(ws)
     torch.cuda.synchronize()
-    api.profile_enable(g, True)
+    for gw in gs:
+        api.profile_enable(gw, True)
     launches0 = api.launch_count()
     clocks = ClockSampler(dev.index or 0)
     step_ms = []
@@ -447,10 +502,11 @@ def run_ours(args, cfg):
     torch.cuda.synchronize()
     clk = clocks.stop()
     launches = (api.launch_count() - launches0) / max(1, args.steps)
-    prof = api.profile_read(g)
-    api.profile_enable(g, False)
+    prof = api.profile_read(g)   # worker 0's handle
+    for gw in gs:
+        api.profile_enable(gw, False)
     hop_variant = api.autotune(g, inner, nb)[0]   # the cached choices the solves used
-    outer_variant = api.autotune(g, outer, nb)[0]
+    outer_variant = (7000 + 100 * min(nb, 2) + ob) if (ob and outer == "f64") else api.autotune(g, outer, nb)[0]
     barrier(ws)
     t_step = max_over_ranks(float(np.mean(step_ms)) / 1e3, ws)
 
@@ -468,40 +524,49 @@ def run_ours(args, cfg):
     d2h = nr * nm * x_bytes
 
     def e2e_copy():
-        n_slots = max(1, min(nr * nm, (8 << 30) // x_bytes))
-        slots = [torch.empty((V, 4, 3), dtype=torch.complex128).pin_memory() for _ in range(n_slots)]
+        # an 8 GB pinned ring per worker for the solutions
+        n_slots = max(1, min(nr * nm, (8 << 30) // x_bytes // nw))
+        slots = [[torch.empty((V, 4, 3), dtype=torch.complex128).pin_memory() for _ in range(n_slots)]
+                 for _ in range(nw)]
+        count = [0] * nw
+
+        def one(bi):
+            w = owner[bi]
+            with torch.cuda.stream(wstreams[w]):
+                for r in batches[bi]:
+                    bs[r].copy_(bs_pin[r], non_blocking=True)
+                st = solve_batch(bi)
+                for j in range(len(batches[bi])):
+                    for i in range(nm):
+                        slots[w][count[w] % n_slots].copy_(xs_w[w][j][i], non_blocking=True)
+                        count[w] += 1
+            return st
+
         times = []
         for _ in range(e2e_steps):
             flush.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            k = 0
-            for rows in batches:
-                for r in rows:
-                    bs[r].copy_(bs_pin[r], non_blocking=True)
-                solve_batch(rows)
-                for j in range(len(rows)):
-                    for i in range(nm):
-                        slots[k % n_slots].copy_(xs[j][i], non_blocking=True)
-                        k += 1
+            run_batches(one)
             torch.cuda.synchronize()
             times.append((time.perf_counter() - t0) * 1e3)
         return float(np.mean(times)) / 1e3
 
     def e2e_zero_copy():
-        xh = [[torch.empty((V, 4, 3), dtype=torch.complex128).pin_memory() for _ in masses] for _ in range(nb)]
+        xh = [[[torch.empty((V, 4, 3), dtype=torch.complex128).pin_memory() for _ in masses] for _ in range(nb)]
+              for _ in range(nw)]
         times = []
         for _ in range(e2e_steps):
             flush.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            for rows in batches:
-                api.multimass_solve(g, [bs_pin[r] for r in rows], masses, prm, xs=xh[:len(rows)])
+            run_batches(lambda bi: solve_batch(bi, [bs_pin[r] for r in batches[bi]],
+                                               xh[owner[bi]][:len(batches[bi])]))
             torch.cuda.synchronize()
             times.append((time.perf_counter() - t0) * 1e3)
         return float(np.mean(times)) / 1e3
 
-    zero_copy = nb * nm * x_bytes <= (24 << 30)
+    zero_copy = nw * nb * nm * x_bytes <= (24 << 30)
     t_e2e_copy = max_over_ranks(e2e_copy(), ws)
     t_e2e = max_over_ranks(e2e_zero_copy(), ws) if zero_copy else t_e2e_copy
 
@@ -509,15 +574,15 @@ def run_ours(args, cfg):
     # last batch is still in xs; the first batch is solved once more
     errors = None
     if rank == 0 and not args.dims:
-        have = {}
-        for j, r in enumerate(batches[-1]):
-            have[r] = xs[j]
-        errors = golden_errors(args.config, have, masses, dev) or {}
-        if len(batches) > 1:
-            solve_batch(batches[0])
+        torch.cuda.synchronize()
+        last = len(batches) - 1
+        errors = golden_errors(args.config, {r: xs_w[owner[last]][j] for j, r in enumerate(batches[last])},
+                               masses, dev) or {}
+        if last > 0:
+            solve_batch(0)
             torch.cuda.synchronize()
-            errors.update(golden_errors(args.config, {r: xs[j] for j, r in enumerate(batches[0])}, masses, dev)
-                          or {})
+            errors.update(golden_errors(args.config, {r: xs_w[owner[0]][j] for j, r in enumerate(batches[0])},
+                                        masses, dev) or {})
 
     peak, peak_kind = measured_peaks()
     roof = roofline_entries(prof, inner, outer, V, peak, peak_kind, nb, hop_variant, outer_variant)
@@ -559,6 +624,7 @@ def run_ours(args, cfg):
                    "inner_solver": "CG on the normal equations" if args.inner_solver == "cg" else "BiCGstab",
                    "full_residual": "recomputed with a hop D_eo x_o" if args.verify_full else
                                     "even half from the last FP64 check, odd half from the reconstruction",
+                   "concurrent_batches": nw, "outer_blocks_per_sm": ob if outer == "f64" else None,
                    "tol": 1e-10, "l2": "flushed (256 MB write) before every step; working set > L2",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "e2e": {"value": t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
@@ -583,8 +649,9 @@ def run_ours(args, cfg):
         # paper's comparison; not part of the timed step), with its vectors
         # and hops in FP64 and in double-float.  Each on a fresh handle with
         # only the links it uses, so its footprint is its own.
-        g.close()
-        del g, xs
+        for gw in gs:
+            gw.close()
+        del g, gs, xs, xs_w
         # with rhat = b a point source breaks the recurrences down at once
         # (<b, r_1> = 0): such sources get a Gaussian shadow residual
         point = cfg["sources"].startswith("point")
@@ -655,6 +722,12 @@ def main():
                     help="inner precision (default: the workload's, f32 unless it names one)")
     ap.add_argument("--outer", choices=["f64", "df"], default="f64",
                     help="precision of the residual recomputation, accumulator and reconstruction")
+    ap.add_argument("--streams", type=int, default=0,
+                    help="batches solved at the same time on their own streams and handles (default: the "
+                         "workload's, else 1)")
+    ap.add_argument("--outer-blocks", type=int, default=-1,
+                    help="FP64 residual hops as a grid-stride kernel of this many blocks per SM (0: full grid; "
+                         "default: the workload's)")
     ap.add_argument("--guess-max", type=int, default=0,
                     help="earlier masses the Lagrange guess uses (0: all, the paper's choice)")
     ap.add_argument("--verify-full", action="store_true",

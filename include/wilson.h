@@ -143,6 +143,13 @@ typedef struct {
                             further hop; 1: recomputed with one more outer-precision
                             hop D_eo x_o per rhs.  The odd half is the rounding of
                             the rebuild either way.                                  */
+    int    outer_blocks_per_sm; /* FP64 outer loop: 0 (default) launches the residual
+                            hops with the autotuned full grid; 1 or 2 launches them as
+                            a grid-stride kernel of that many 128-thread blocks per SM.
+                            The FP64 hop is bound by the FP64 pipe and needs few warps;
+                            the small grid leaves the rest of each SM to work on other
+                            streams, such as the inner solve of another batch of
+                            sources solved at the same time on another handle.      */
 } wl_solver_params;
 
 typedef struct {
@@ -160,7 +167,7 @@ typedef struct {
  * what the outer target needs), max_restarts 100,
  * WL_GUESS_POLY, WL_MODE_GRAPH, rhs_block 0, graph_iters 8, eo 1,
  * outer_prec WL_F64, shadow NULL, guess_max 0, reliable 0,
- * inner_solver WL_SOLVER_BICGSTAB, verify_full 0. */
+ * inner_solver WL_SOLVER_BICGSTAB, verify_full 0, outer_blocks_per_sm 0. */
 int wl_params_default(wl_solver_params *p);
 
 /* Thread-local message describing the last failing call on this thread. */
@@ -367,6 +374,32 @@ int wl_profile_read(wl_gauge *g, wl_kernel_profile out[4]);
  * from and appended to it.  *variant = 100 * rhs-per-thread + min-blocks,
  * *best_us its time per launch.  Synchronises the stream. */
 int wl_autotune(wl_gauge *g, int prec, int n_rhs, void *stream, int *variant, double *best_us);
+
+/* Number of bounded waits that gave up on the device since the last reset
+ * (no paper counterpart).  The TMA-staged hop variants wait on an mbarrier
+ * for each tile's copies; a wait that does not complete within about a
+ * second of clock cycles is counted here, and that block stops instead of
+ * hanging.  Reads the counter into *count after synchronising the stream
+ * and, with reset = 1, sets it back to zero.  Autotuning and the inner
+ * solver check it and return WL_ERR_TIMEOUT when it is non-zero. */
+int wl_wait_faults(unsigned *count, int reset, void *stream);
+
+/* Bounds-checked build (no paper counterpart): libwilson_checked.so is the
+ * same library compiled with every site index of an internal spinor or link
+ * access tested against its array length.  The first violation in each
+ * translation unit is recorded and the access is redirected to site 0 (a
+ * load) or dropped (a store); nothing traps.  Synchronising calls
+ * (multimass_solve, bicgstab_solve, bicgstab_m_solve,
+ * wilson_solve_backward, and in this build wilson_dslash,
+ * wilson_dslash_dag, wilson_hop, wilson_hop_multi) then return
+ * WL_ERR_CHECKED.  wl_checked_status synchronises the device and writes the
+ * first recorded violation to *first (0: none; otherwise bit 63 set, the
+ * access kind -- 1 spinor load, 2 spinor store, 3 link load -- in bits
+ * 32-39 and the site index in bits 0-31), clearing the records if reset
+ * is 1.  In the ordinary library *first is always 0.
+ * wl_is_checked_build returns 1 in the checked library, 0 otherwise. */
+int wl_checked_status(unsigned long long *first, int reset);
+int wl_is_checked_build(void);
 
 /* Failure-path check of the persistent solver (WL_MODE_PERSISTENT): runs
  * one cooperative launch of the persistent BiCGstab on zero vectors with

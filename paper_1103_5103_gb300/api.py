@@ -17,7 +17,10 @@ import os
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libwilson.so")
+# WL_LIBRARY=checked loads the bounds-checked build (every internal site
+# index tested, violations recorded instead of trapping)
+LIB_PATH = os.path.join(_HERE, "libwilson_checked.so" if os.environ.get("WL_LIBRARY") == "checked"
+                        else "libwilson.so")
 
 WL_OK, WL_ERR_ARG, WL_ERR_CUDA, WL_ERR_OOM, WL_ERR_NOCONV, WL_ERR_BREAKDOWN, WL_ERR_TIMEOUT, WL_ERR_CHECKED = range(8)
 F64, F32, F16, DF = 1, 2, 4, 8
@@ -51,7 +54,8 @@ class SolverParams(ctypes.Structure):
     _fields_ = [("tol", _dbl), ("max_iter", _int), ("inner_prec", _int), ("inner_tol", _dbl),
                 ("max_restarts", _int), ("guess", _int), ("mode", _int), ("rhs_block", _int),
                 ("graph_iters", _int), ("eo", _int), ("outer_prec", _int), ("shadow", _vp),
-                ("guess_max", _int), ("reliable", _int), ("inner_solver", _int), ("verify_full", _int)]
+                ("guess_max", _int), ("reliable", _int), ("inner_solver", _int), ("verify_full", _int),
+                ("outer_blocks_per_sm", _int)]
 
 
 class SolverStats(ctypes.Structure):
@@ -94,6 +98,9 @@ _sig("bicgstab_solve", [_vp, _vp, _vp, _dbl, ctypes.POINTER(SolverParams), ctype
 _sig("wl_launch_count", [ctypes.POINTER(ctypes.c_longlong)])
 _sig("wl_autotune", [_vp, _int, _int, _vp, ctypes.POINTER(_int), ctypes.POINTER(_dbl)])
 _sig("wl_profile_enable", [_vp, _int])
+_sig("wl_wait_faults", [ctypes.POINTER(ctypes.c_uint), _int, _vp])
+_sig("wl_checked_status", [ctypes.POINTER(ctypes.c_ulonglong), _int])
+_sig("wl_is_checked_build", [])
 _sig("wl_persistent_selftest", [_vp, _int, _int, _dbl, _vp])
 _sig("wl_profile_read", [_vp, ctypes.POINTER(KernelProfile)])
 _sig("wilson_solve_backward", [_vp, _vp, _vp, ctypes.POINTER(_vp), ctypes.POINTER(_dbl), _int,
@@ -334,6 +341,25 @@ def profile_read(g: Gauge) -> dict:
     return {"f64": arr[0].as_dict(), "f32": arr[1].as_dict(), "f16": arr[2].as_dict(), "outer": arr[3].as_dict()}
 
 
+def wait_faults(reset: bool = True, stream=None) -> int:
+    """Bounded device waits (TMA-staged hops) that gave up since the last reset."""
+    n = ctypes.c_uint()
+    _check(_lib.wl_wait_faults(ctypes.byref(n), int(reset), _stream(stream)))
+    return n.value
+
+
+def checked_status(reset: bool = True) -> int:
+    """First out-of-range site index recorded by the bounds-checked build
+    (0: none; always 0 in the ordinary build)."""
+    v = ctypes.c_ulonglong()
+    _check(_lib.wl_checked_status(ctypes.byref(v), int(reset)))
+    return v.value
+
+
+def is_checked_build() -> bool:
+    return bool(_lib.wl_is_checked_build())
+
+
 def launch_count() -> int:
     """Kernels launched by the library in this process (wl_launch_count)."""
     n = ctypes.c_longlong()
@@ -341,8 +367,10 @@ def launch_count() -> int:
     return n.value
 
 
-HOP_VARIANTS = {"f32": [101, 105, 106, 108, 201, 204, 205, 401, 404, 301, 304, 305, 1104, 1106, 1202, 1203], "f16": [101, 105, 106, 108, 110, 201, 204, 206, 401, 404],
-                "f64": [101, 103, 201], "df": [101, 103, 104, 105, 106]}
+HOP_VARIANTS = {"f32": [101, 105, 106, 108, 201, 204, 205, 401, 404, 301, 304, 305, 1104, 1106, 1202, 1203, 9001, 9002,
+                        9004, 9102, 9104],
+                "f16": [101, 105, 106, 108, 110, 201, 204, 206, 401, 404, 9001, 9002, 9004, 9102, 9104],
+                "f64": [101, 103, 201, 7101, 7102, 7201, 7202], "df": [101, 103, 104, 105, 106]}
 
 
 def autotune(g: Gauge, prec, nrhs: int, stream=None):

@@ -264,5 +264,5 @@ extern "C" int wilson_solve_backward(wl_gauge *g, const void *b, const void *con
         }
     }
     WL_CUDA_TRY(cudaStreamSynchronize(s));
-    return WL_OK;
+    return checked_result(WL_OK);
 }

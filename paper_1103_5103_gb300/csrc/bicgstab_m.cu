@@ -639,5 +639,5 @@ extern "C" int bicgstab_m_solve(wl_gauge *g, const void *b, void *const *x, cons
         set_error("bicgstab_m_solve: the shifted recurrences broke down after " + std::to_string(hs.iters) +
                   " iterations (<rhat, r> or <rhat, v> vanished; with rhat = b a point source this happens at "
                   "once: pass a shadow residual); unconverged masses were finished by single-mass BiCGstab");
-    return worst;
+    return checked_result(worst);
 }

@@ -33,6 +33,49 @@ void set_error(const std::string &msg);
 
 inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// ----------------------------------------------------- bounds-checked build
+// With WL_CHECKED defined (libwilson_checked.so, built beside the library)
+// every site index of an internal spinor or link access is tested against
+// the length of its array.  The first violation in each translation unit
+// is recorded in a device word -- bit 63 set, the access kind (1 spinor
+// load, 2 spinor store, 3 link load) in bits 32-39, the index in bits 0-31
+// -- and the access goes to site 0 (a load) or is dropped (a store), so
+// nothing outside the arrays is touched and nothing traps.  The C-ABI calls
+// that synchronise return WL_ERR_CHECKED when a word is set;
+// wl_checked_status reads and clears them.  In the ordinary build the
+// checks compile to nothing.
+int checked_register(int (*reader)(unsigned long long *, bool));
+int checked_status(unsigned long long *first, bool reset);
+
+#ifdef WL_CHECKED
+namespace checked {
+static __device__ unsigned long long first_violation;   // one per translation unit
+}
+__device__ __forceinline__ bool in_range(int i, int n, unsigned kind)
+{
+    if ((unsigned)i < (unsigned)n) return true;
+    atomicCAS(&checked::first_violation, 0ull, (1ull << 63) | ((unsigned long long)kind << 32) | (unsigned)i);
+    return false;
+}
+#define WL_LOAD_IDX(i, n, kind) (::wl::in_range((i), (n), (kind)) ? (i) : 0)
+#define WL_STORE_OK(i, n, kind) ::wl::in_range((i), (n), (kind))
+namespace checked {
+static int read_word(unsigned long long *v, bool reset)
+{
+    WL_CUDA_TRY(cudaMemcpyFromSymbol(v, first_violation, sizeof(unsigned long long)));
+    if (reset && *v) {
+        const unsigned long long zero = 0;
+        WL_CUDA_TRY(cudaMemcpyToSymbol(first_violation, &zero, sizeof(unsigned long long)));
+    }
+    return WL_OK;
+}
+static const int registered = checked_register(&read_word);
+}  // namespace checked
+#else
+#define WL_LOAD_IDX(i, n, kind) (i)
+#define WL_STORE_OK(i, n, kind) true
+#endif
+
 // Kernel launch accounting (wl_launch_count): note_launch(s) after a launch
 // on stream s counts it unless s is being captured into a graph; graph
 // replays add their kernel-node count through add_launches.
@@ -269,6 +312,7 @@ template <> struct SpinorIO<WL_F64> {
     template <bool CG = false>
     static __device__ __forceinline__ void load(const void *base, int stride, int i, cx<R> (&v)[12])
     {
+        i = WL_LOAD_IDX(i, stride, 1);
         const double2 *p = static_cast<const double2 *>(base);
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
@@ -285,6 +329,7 @@ template <> struct SpinorIO<WL_F64> {
     static __device__ __forceinline__ void roundtrip(cx<R> (&)[12]) {}
     static __device__ __forceinline__ void store(void *base, int stride, int i, const cx<R> (&v)[12])
     {
+        if (!WL_STORE_OK(i, stride, 2)) return;
         double2 *p = static_cast<double2 *>(base);
 #pragma unroll
         for (int k = 0; k < 12; ++k) p[(size_t)k * stride + i] = make_double2(v[k].re, v[k].im);
@@ -296,6 +341,7 @@ template <> struct SpinorIO<WL_F32> {
     template <bool CG = false>
     static __device__ __forceinline__ void load(const void *base, int stride, int i, cx<R> (&v)[12])
     {
+        i = WL_LOAD_IDX(i, stride, 1);
         const float4 *p = static_cast<const float4 *>(base);
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
@@ -313,6 +359,7 @@ template <> struct SpinorIO<WL_F32> {
     static __device__ __forceinline__ void roundtrip(cx<R> (&)[12]) {}
     static __device__ __forceinline__ void store(void *base, int stride, int i, const cx<R> (&v)[12])
     {
+        if (!WL_STORE_OK(i, stride, 2)) return;
         float4 *p = static_cast<float4 *>(base);
 #pragma unroll
         for (int k = 0; k < 6; ++k)
@@ -352,6 +399,7 @@ template <> struct SpinorIO<WL_F16> {
     template <bool CG = false>
     static __device__ __forceinline__ R load_unscaled(const void *base, int stride, int i, cx<R> (&v)[12])
     {
+        i = WL_LOAD_IDX(i, stride, 1);
         const uint4 *p = static_cast<const uint4 *>(base);
         const float n = ldx<CG>(norms(base, stride) + i);
 #pragma unroll
@@ -368,6 +416,7 @@ template <> struct SpinorIO<WL_F16> {
     template <bool CG = false>
     static __device__ __forceinline__ void load(const void *base, int stride, int i, cx<R> (&v)[12])
     {
+        i = WL_LOAD_IDX(i, stride, 1);
         const uint4 *p = static_cast<const uint4 *>(base);
         const float n = ldx<CG>(norms(base, stride) + i);
 #pragma unroll
@@ -382,6 +431,7 @@ template <> struct SpinorIO<WL_F16> {
     }
     static __device__ __forceinline__ void store(void *base, int stride, int i, const cx<R> (&v)[12])
     {
+        if (!WL_STORE_OK(i, stride, 2)) return;
         float m = site_scale(v);
         const float inv = m > 0.f ? 1.0f / m : 0.f;
         uint4 *p = static_cast<uint4 *>(base);
@@ -414,6 +464,7 @@ template <> struct SpinorIO<WL_DF> {
     template <bool CG = false>
     static __device__ __forceinline__ void load(const void *base, int stride, int i, cx<R> (&v)[12])
     {
+        i = WL_LOAD_IDX(i, stride, 1);
         const float4 *p = static_cast<const float4 *>(base);
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
@@ -430,6 +481,7 @@ template <> struct SpinorIO<WL_DF> {
     static __device__ __forceinline__ void roundtrip(cx<R> (&)[12]) {}
     static __device__ __forceinline__ void store(void *base, int stride, int i, const cx<R> (&v)[12])
     {
+        if (!WL_STORE_OK(i, stride, 2)) return;
         float4 *p = static_cast<float4 *>(base);
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
@@ -467,6 +519,7 @@ template <> struct LinkIO<WL_F64> {
     static constexpr int chunks = 9;
     static __device__ __forceinline__ void load(const void *dirbase, int stride, int i, cx<R> (&u)[9])
     {
+        i = WL_LOAD_IDX(i, stride, 3);
         const double2 *p = static_cast<const double2 *>(dirbase);
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
@@ -480,6 +533,7 @@ template <> struct LinkIO<WL_F32> {
     static constexpr int chunks = 3;
     static __device__ __forceinline__ void load(const void *dirbase, int stride, int i, cx<R> (&u)[9])
     {
+        i = WL_LOAD_IDX(i, stride, 3);
         const float4 *p = static_cast<const float4 *>(dirbase);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -495,6 +549,7 @@ template <> struct LinkIO<WL_F16> {
     static constexpr int chunks = 3;
     static __device__ __forceinline__ void load(const void *dirbase, int stride, int i, cx<R> (&u)[9])
     {
+        i = WL_LOAD_IDX(i, stride, 3);
         const uint2 *p = static_cast<const uint2 *>(dirbase);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -517,6 +572,7 @@ template <> struct LinkIO<WL_DF> {
     static constexpr int chunks = 9;
     static __device__ __forceinline__ void load(const void *dirbase, int stride, int i, cx<R> (&u)[9])
     {
+        i = WL_LOAD_IDX(i, stride, 3);
         const float4 *p = static_cast<const float4 *>(dirbase);
 #pragma unroll
         for (int k = 0; k < 9; ++k) {

@@ -7,6 +7,16 @@ namespace wl {
 
 static const void *links_of(wl_gauge *g, int prec, int parity) { return g->links[prec_index(prec)][parity]; }
 
+// SM count of the current device (grid-stride launches).
+int sm_count()
+{
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+        v > 0)
+        return v;
+    return 1;
+}
+
 static int check_links(wl_gauge *g, int prec)
 {
     if (!(g->prec_mask & prec) || !links_of(g, prec, 0)) {
@@ -55,6 +65,7 @@ int hop_ex(wl_gauge *g, const Vec &in, const Vec &out, const Vec *x1, double a1,
     case WL_DF: st = hop_launch_prec<WL_DF>(variant, dagger, a, e, s); break;
     default: set_error("hop: bad precision"); return WL_ERR_ARG;
     }
+    if (st == WL_VARIANT_NA) return WL_ERR_ARG;
     WL_TRY(st);
     WL_CUDA_TRY(cudaGetLastError());
     note_launch(s);
@@ -133,6 +144,19 @@ using namespace wl;
 
 // ---------------------------------------------------------------- C ABI
 
+// In the bounds-checked build the dslash calls synchronise the stream and
+// report a recorded out-of-range index.
+static int dslash_checked(int st, void *stream)
+{
+#ifdef WL_CHECKED
+    if (st == WL_OK) WL_CUDA_TRY(cudaStreamSynchronize(as_stream(stream)));
+    return checked_result(st);
+#else
+    (void)stream;
+    return st;
+#endif
+}
+
 extern "C" int wilson_hop(wl_gauge *g, const void *in, void *out, const void *x, double coef, int prec,
                           int out_parity, int dagger, void *stream)
 {
@@ -146,7 +170,8 @@ extern "C" int wilson_hop(wl_gauge *g, const void *in, void *out, const void *x,
     vi.rhs_bytes = vo.rhs_bytes = vx.rhs_bytes = spinor_bytes(g->lat->geom, prec);
     vo.ptr = out;
     vx.ptr = const_cast<void *>(x);
-    return hop(g, vi, vo, x ? &vx : nullptr, coef, out_parity, dagger ? 1 : 0, 1, as_stream(stream));
+    return dslash_checked(hop(g, vi, vo, x ? &vx : nullptr, coef, out_parity, dagger ? 1 : 0, 1, as_stream(stream)),
+                          stream);
 }
 
 extern "C" int wilson_hop_multi(wl_gauge *g, const void *in, void *out, const void *x, double coef, int prec,
@@ -169,7 +194,8 @@ extern "C" int wilson_hop_multi(wl_gauge *g, const void *in, void *out, const vo
     vi.prec = vo.prec = vx.prec = prec;
     vi.nrhs = vo.nrhs = vx.nrhs = n_rhs;
     vi.rhs_bytes = vo.rhs_bytes = vx.rhs_bytes = rhs_stride;
-    return hop(g, vi, vo, x ? &vx : nullptr, coef, out_parity, dagger ? 1 : 0, rhs_block, as_stream(stream));
+    return dslash_checked(hop(g, vi, vo, x ? &vx : nullptr, coef, out_parity, dagger ? 1 : 0, rhs_block,
+                              as_stream(stream)), stream);
 }
 
 static int dslash_common(wl_gauge *g, const void *in, void *out, double kappa, int prec, int op, int dagger,
@@ -210,11 +236,11 @@ static int dslash_common(wl_gauge *g, const void *in, void *out, double kappa, i
 
 extern "C" int wilson_dslash(wl_gauge *g, const void *in, void *out, double kappa, int prec, int op, void *stream)
 {
-    return dslash_common(g, in, out, kappa, prec, op, 0, stream);
+    return dslash_checked(dslash_common(g, in, out, kappa, prec, op, 0, stream), stream);
 }
 
 extern "C" int wilson_dslash_dag(wl_gauge *g, const void *in, void *out, double kappa, int prec, int op,
                                  void *stream)
 {
-    return dslash_common(g, in, out, kappa, prec, op, 1, stream);
+    return dslash_checked(dslash_common(g, in, out, kappa, prec, op, 1, stream), stream);
 }

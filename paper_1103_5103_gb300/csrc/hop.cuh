@@ -698,6 +698,49 @@ __global__ void __launch_bounds__(128, MINB) k_hop(HopArgs a, EpiStore epi)
     epi.template operator()<P, NB>(a, i, true, r0, acc);
 }
 
+// Grid-stride form of k_hop: a fixed grid of blocks_per_sm x SM-count
+// blocks, each looping over the (site block, rhs group) tiles.  Meant for
+// the FP64 hop, which is bound by the FP64 pipe (1/57 of the FP32 rate on
+// GB300) and needs only a few warps per SM to keep it busy: with a small
+// grid it leaves most warp slots and issue cycles to kernels of another
+// stream running at the same time (another batch's FP32/FP16 inner solve),
+// instead of occupying the GPU for its whole duration.
+template <int P, bool DAG, int NB, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_hop_gs(HopArgs a, EpiStore epi)
+{
+    using R = typename PrecTraits<P>::R;
+    const int nsb = (a.g.Vh + 127) / 128;
+    const int ntiles = nsb * a.ngroups;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int grp = t % a.ngroups;
+        const int sb = t / a.ngroups;
+        const int r0 = grp * NB;
+        if (a.skip) {
+            bool all_done = true;
+            for (int r = r0; r < r0 + NB && r < a.nrhs; ++r) all_done &= rhs_done(a, r);
+            if (all_done) continue;
+        }
+        const int i = sb * blockDim.x + threadIdx.x;
+        if (i >= a.g.Vh) continue;
+        cx<R> acc[NB][12];
+#pragma unroll
+        for (int r = 0; r < NB; ++r)
+#pragma unroll
+            for (int k = 0; k < 12; ++k) acc[r][k] = acc_zero<R>();
+        hop_accumulate<P, DAG, NB>(a, i, r0, acc);
+        epi.template operator()<P, NB>(a, i, true, r0, acc);
+    }
+}
+
+int sm_count();
+
+template <int P, bool DAG, int NB, int MINB>
+void launch_k_hop_gs(HopArgs a, const EpiStore &e, cudaStream_t s)
+{
+    a.ngroups = (a.nrhs + NB - 1) / NB;
+    k_hop_gs<P, DAG, NB, MINB><<<MINB * sm_count(), 128, 0, s>>>(a, e);
+}
+
 template <int P, bool DAG, int KIND>
 __device__ __forceinline__ void hop_reduce_body(const HopArgs &a, const EpiReduce<KIND> &e)
 {
@@ -818,8 +861,16 @@ __device__ __forceinline__ void hop_reduce_body(const HopArgs &a, const EpiReduc
     }
 }
 
+// Resident blocks per SM the reduction-fused hop asks the register
+// allocator for: six (80 registers, no spills) for FP16 storage, where
+// occupancy hides the load latency; the other precisions need more
+// registers than that (FP32 would spill at 80).
+template <int P> struct ReduceMinBlocks {
+    static constexpr int value = P == WL_F16 ? 6 : 1;
+};
+
 template <int P, bool DAG, int KIND>
-__global__ void __launch_bounds__(128) k_hop_reduce(HopArgs a, EpiReduce<KIND> e)
+__global__ void __launch_bounds__(128, ReduceMinBlocks<P>::value) k_hop_reduce(HopArgs a, EpiReduce<KIND> e)
 {
     hop_reduce_body<P, DAG, KIND>(a, e);
 }
@@ -859,6 +910,12 @@ void launch_reduce_kind(int dagger, const HopArgs &a, const void *epi, cudaStrea
     else
         launch_k_hop_reduce<P, false, KIND>(a, e, s);
 }
+
+// Returned by a launcher whose variant does not apply to the lattice.
+constexpr int WL_VARIANT_NA = -100;
+
+// TMA-staged hop (hop_tma.cu), FP32 and FP16, variants 9000 + rhs per tile.
+int hop_launch_tma(int prec, int variant, int dagger, const HopArgs &a, const EpiStore &e, cudaStream_t s);
 
 // Per-precision entry points (hop_<prec>.cu).  variant: see hop_variants().
 template <int P> int hop_launch_prec(int variant, int dagger, const HopArgs &a, const EpiStore &e, cudaStream_t s);

@@ -1,6 +1,7 @@
 // Hop kernel instantiations for F32 (one translation unit per precision so the
 // library builds in parallel).  Variant v = 100 * (rhs per thread) + (minimum resident
-// blocks per SM requested from the register allocator).
+// blocks per SM requested from the register allocator); 9000 + 100 b + R is the
+// TMA-staged hop with R rhs per tile and register budget b (hop_tma.cu).
 #include "hop.cuh"
 
 namespace wl {
@@ -8,6 +9,12 @@ namespace wl {
 template <>
 int hop_launch_prec<WL_F32>(int v, int dagger, const HopArgs &a, const EpiStore &e, cudaStream_t s)
 {
+    if (v >= 9000 && v < 9300 && !dagger) {
+        const int st = hop_launch_tma(WL_F32, v, dagger, a, e, s);
+        if (st != WL_OK) return st;
+        WL_CUDA_TRY(cudaGetLastError());
+        return WL_OK;
+    }
     if (dagger) {
         switch (v / 100) {
         case 1: launch_k_hop<WL_F32, true, 1, 1>(a, e, s); break;

@@ -1,9 +1,11 @@
 // Hop kernel instantiations for F64 (one translation unit per precision so the
 // library builds in parallel).  Variant v = 100 * (rhs per thread) + (minimum resident
-// blocks per SM requested from the register allocator).
+// blocks per SM requested from the register allocator); v = 7000 + 100 * (rhs per
+// thread) + B is the grid-stride form with B blocks per SM (k_hop_gs).
 #include "hop.cuh"
 
 namespace wl {
+
 
 template <>
 int hop_launch_prec<WL_F64>(int v, int dagger, const HopArgs &a, const EpiStore &e, cudaStream_t s)
@@ -19,6 +21,10 @@ int hop_launch_prec<WL_F64>(int v, int dagger, const HopArgs &a, const EpiStore 
         case 101: launch_k_hop<WL_F64, false, 1, 1>(a, e, s); break;
         case 103: launch_k_hop<WL_F64, false, 1, 3>(a, e, s); break;
         case 201: launch_k_hop<WL_F64, false, 2, 1>(a, e, s); break;
+        case 7101: launch_k_hop_gs<WL_F64, false, 1, 1>(a, e, s); break;
+        case 7102: launch_k_hop_gs<WL_F64, false, 1, 2>(a, e, s); break;
+        case 7201: launch_k_hop_gs<WL_F64, false, 2, 1>(a, e, s); break;
+        case 7202: launch_k_hop_gs<WL_F64, false, 2, 2>(a, e, s); break;
         default:
             switch (v / 100) {
             case 1: launch_k_hop<WL_F64, false, 1, 1>(a, e, s); break;

@@ -42,6 +42,15 @@ struct Workspace {
     void release();
 };
 
+// Page-locked host staging of small per-rhs arrays, by name, kept for the
+// life of the handle: cudaMallocHost and cudaFreeHost are slow and may
+// synchronise the device, so no solve calls them once the buffers exist.
+struct HostPinned {
+    std::map<std::string, DevBuf> bufs;
+    int get(const std::string &name, size_t bytes, void **out);
+    void release();
+};
+
 
 
 
@@ -73,6 +82,7 @@ struct wl_gauge {
     unsigned prec_mask;
     void *links[4][2];  // [prec index][parity] -> 4 directions of 12-real links
     wl::Workspace ws;
+    wl::HostPinned pinned;
     std::mutex mu;      // one solve at a time per handle (shared workspace)
     int profiling = 0;
     wl_kernel_profile prof[4] = {};   // inner hop per precision index (F64, F32, F16); [3] outer residual hop
@@ -160,6 +170,24 @@ int persistent_inner(wl_gauge *g, int prec, int nrhs, const Vec &r, const Vec &r
 // thread; rhs_block < 0 selects variant -rhs_block; 0 takes the tuned one.
 const std::vector<int> &hop_variants(int prec);
 int hop_variant_for(wl_gauge *g, int prec, int nrhs, int rhs_block);
+// Bounded device waits (TMA-staged hops) that gave up since the last reset.
+int wait_faults(unsigned *count, bool reset, cudaStream_t s);
+
+// Bounds-checked build: status of a synchronising C-ABI call, replaced by
+// WL_ERR_CHECKED when an out-of-range site index was recorded (the words are
+// left set for wl_checked_status).  The ordinary build returns status as is.
+inline int checked_result(int status)
+{
+#ifdef WL_CHECKED
+    unsigned long long v = 0;
+    if (checked_status(&v, false) == WL_OK && v) {
+        set_error("bounds-checked build: out-of-range site index " + std::to_string(v & 0xffffffffull) +
+                  " (access kind " + std::to_string((v >> 32) & 0xff) + ")");
+        return WL_ERR_CHECKED;
+    }
+#endif
+    return status;
+}
 int autotune_hop(wl_gauge *g, int prec, int nrhs, cudaStream_t s, TuneResult *out);
 
 // ---- solver.cu

@@ -5,6 +5,9 @@
 #include <cstring>
 #include <string>
 
+#include <mutex>
+#include <vector>
+
 #include "internal.h"
 
 namespace wl {
@@ -24,6 +27,60 @@ void note_launch(cudaStream_t s)
 void add_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 size_t spinor_bytes(const Geom &g, int prec) { return (size_t)spinor_site_bytes(prec) * g.stride; }
+
+// Readers of the per-translation-unit violation words of the bounds-checked
+// build (each unit registers one at static initialisation).
+static std::vector<int (*)(unsigned long long *, bool)> &checked_readers()
+{
+    static std::vector<int (*)(unsigned long long *, bool)> v;
+    return v;
+}
+static std::mutex g_checked_mu;
+
+int checked_register(int (*reader)(unsigned long long *, bool))
+{
+    std::lock_guard<std::mutex> lock(g_checked_mu);
+    checked_readers().push_back(reader);
+    return 1;
+}
+
+int checked_status(unsigned long long *first, bool reset)
+{
+    *first = 0;
+    std::lock_guard<std::mutex> lock(g_checked_mu);
+    for (auto rd : checked_readers()) {
+        unsigned long long v = 0;
+        WL_TRY(rd(&v, reset));
+        if (v && !*first) *first = v;
+    }
+    return WL_OK;
+}
+
+int HostPinned::get(const std::string &name, size_t bytes, void **out)
+{
+    DevBuf &b = bufs[name];
+    if (b.bytes < bytes) {
+        if (b.ptr) cudaFreeHost(b.ptr);
+        b.ptr = nullptr;
+        b.bytes = 0;
+        cudaError_t e = cudaMallocHost(&b.ptr, bytes);
+        if (e != cudaSuccess) {
+            b.ptr = nullptr;
+            set_error("pinned staging '" + name + "': " + cudaGetErrorString(e));
+            return WL_ERR_OOM;
+        }
+        b.bytes = bytes;
+    }
+    *out = b.ptr;
+    return WL_OK;
+}
+
+void HostPinned::release()
+{
+    for (auto &kv : bufs)
+        if (kv.second.ptr) cudaFreeHost(kv.second.ptr);
+    bufs.clear();
+}
 
 int Workspace::get(const std::string &name, size_t bytes, void **out)
 {
@@ -321,6 +378,25 @@ extern "C" int wl_launch_count(long long *out)
     return WL_OK;
 }
 
+extern "C" int wl_is_checked_build(void)
+{
+#ifdef WL_CHECKED
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+extern "C" int wl_checked_status(unsigned long long *first, int reset)
+{
+    if (!first) {
+        set_error("wl_checked_status: NULL");
+        return WL_ERR_ARG;
+    }
+    WL_CUDA_TRY(cudaDeviceSynchronize());
+    return checked_status(first, reset != 0);
+}
+
 extern "C" int wl_params_default(wl_solver_params *p)
 {
     if (!p) { set_error("wl_params_default: NULL"); return WL_ERR_ARG; }
@@ -340,6 +416,7 @@ extern "C" int wl_params_default(wl_solver_params *p)
     p->reliable = 0;
     p->inner_solver = WL_SOLVER_BICGSTAB;
     p->verify_full = 0;
+    p->outer_blocks_per_sm = 0;
     return WL_OK;
 }
 
@@ -547,6 +624,7 @@ extern "C" int wl_gauge_destroy(wl_gauge *g)
             if (g->links[pi][par]) cudaFree(g->links[pi][par]);
     g->inner_graph.release();
     g->ws.release();
+    g->pinned.release();
     delete g;
     return WL_OK;
 }

@@ -26,25 +26,6 @@
 
 namespace wl {
 
-// Pinned host staging for small per-rhs arrays.
-struct Pinned {
-    void *p = nullptr;
-    size_t bytes = 0;
-    int reserve(size_t b)
-    {
-        if (b <= bytes) return WL_OK;
-        if (p) cudaFreeHost(p);
-        p = nullptr;
-        WL_CUDA_TRY(cudaMallocHost(&p, b));
-        bytes = b;
-        return WL_OK;
-    }
-    ~Pinned()
-    {
-        if (p) cudaFreeHost(p);
-    }
-};
-
 // Scratch of one batched solve: per-rhs state, reduction partials, flags.
 struct Scratch {
     BiState *state = nullptr;    // [nrhs]
@@ -208,9 +189,9 @@ static int run_inner(Inner &in, const wl_solver_params &prm, int max_iter, std::
 {
     const int nrhs = in.nrhs;
     const int rb = prm.rhs_block;  // 0: the autotuned hop variant
-    Pinned pin;
-    WL_TRY(pin.reserve(sizeof(BiState) * nrhs));
-    BiState *hs = static_cast<BiState *>(pin.p);
+    void *pin = nullptr;
+    WL_TRY(in.g->pinned.get("inner_state", sizeof(BiState) * nrhs, &pin));
+    BiState *hs = static_cast<BiState *>(pin);
     host_state.resize(nrhs);
     if (prm.mode == WL_MODE_PERSISTENT) {
         // one cooperative launch for all iterations; 1 s bound on every barrier wait
@@ -344,6 +325,15 @@ static int run_inner(Inner &in, const wl_solver_params &prm, int max_iter, std::
         if (all || done_iters >= max_iter) break;
     }
     std::memcpy(host_state.data(), hs, sizeof(BiState) * nrhs);
+    if (status == WL_OK && hop_variant_for(in.g, in.prec, nrhs, rb) >= 9000) {
+        // a TMA-staged hop that stopped waiting leaves its tile unwritten
+        unsigned faults = 0;
+        WL_TRY(wait_faults(&faults, true, s));
+        if (faults) {
+            set_error("inner solve: a TMA-staged hop gave up waiting for its copies");
+            return WL_ERR_TIMEOUT;
+        }
+    }
     return status;
 }
 
@@ -391,9 +381,9 @@ static int eo_defect_correction(wl_gauge *g, const Vec &bprec, const Vec &x64, d
     Vec r64, tmp64;  // outer precision (FP64 or double-float)
     WL_TRY(make_vec(g, "dc_r64", x64.prec, nrhs, &r64));
     WL_TRY(make_vec(g, "dc_tmp64", x64.prec, nrhs, &tmp64));
-    Pinned pin;
-    WL_TRY(pin.reserve(nrhs * (sizeof(double) * 2 + sizeof(int) * 2)));
-    double *h_rn2 = static_cast<double *>(pin.p);
+    void *pin = nullptr;
+    WL_TRY(g->pinned.get("dc_scalars", nrhs * (sizeof(double) * 2 + sizeof(int) * 2), &pin));
+    double *h_rn2 = static_cast<double *>(pin);
     double *h_delta2 = h_rn2 + nrhs;
     int *h_active = reinterpret_cast<int *>(h_delta2 + nrhs);
     int *h_outer = h_active + nrhs;
@@ -409,6 +399,10 @@ static int eo_defect_correction(wl_gauge *g, const Vec &bprec, const Vec &x64, d
     WL_CUDA_TRY(cudaMemsetAsync(in.sc.outer_done, 0, sizeof(int) * nrhs, s));
     int total_restarts = 0;
     bool lincomb_check = r0_given;
+    // outer residual hops: autotuned full grid, or the FP64 grid-stride form
+    const int ohop = (prm.outer_blocks_per_sm > 0 && x64.prec == WL_F64)
+                         ? -(7000 + 100 * (nrhs >= 2 ? 2 : 1) + prm.outer_blocks_per_sm)
+                         : 0;
     // live timing of the first residual hop of every check (wl_profile_enable)
     struct Ev {
         cudaEvent_t e[2] = {nullptr, nullptr};
@@ -423,9 +417,9 @@ static int eo_defect_correction(wl_gauge *g, const Vec &bprec, const Vec &x64, d
         if (!lincomb_check) {
             for (int r = 0; r < nrhs; ++r) n_hop += outer_done[r] ? 0 : 1;
             if (ev.e[0]) WL_CUDA_TRY(cudaEventRecord(ev.e[0], s));
-            WL_TRY(hop_ex(g, x64, tmp64, nullptr, 0.0, nullptr, 0.0, 1.0, WL_ODD, 0, 0, in.sc.outer_done, 1, s));
+            WL_TRY(hop_ex(g, x64, tmp64, nullptr, 0.0, nullptr, 0.0, 1.0, WL_ODD, 0, ohop, in.sc.outer_done, 1, s));
             if (ev.e[1]) WL_CUDA_TRY(cudaEventRecord(ev.e[1], s));
-            WL_TRY(hop_ex(g, tmp64, r64, &bprec, 1.0, &x64, -1.0, k2, WL_EVEN, 0, 0, in.sc.outer_done, 1, s,
+            WL_TRY(hop_ex(g, tmp64, r64, &bprec, 1.0, &x64, -1.0, k2, WL_EVEN, 0, ohop, in.sc.outer_done, 1, s,
                           y_out));
         }
         WL_TRY(blas_norm2(geo, r64, in.sc.norms, in.sc.partials, in.sc.tickets, s));
@@ -670,7 +664,7 @@ static int check_params(const wl_gauge *g, const wl_solver_params *p)
         (p->inner_solver != WL_SOLVER_BICGSTAB && p->inner_solver != WL_SOLVER_CG) ||
         (p->inner_solver == WL_SOLVER_CG && (p->reliable || p->mode == WL_MODE_PERSISTENT)) ||
         p->rhs_block < 0 || p->rhs_block > 4 || (p->outer_prec != WL_F64 && p->outer_prec != WL_DF) ||
-        (p->verify_full != 0 && p->verify_full != 1)) {
+        (p->verify_full != 0 && p->verify_full != 1) || p->outer_blocks_per_sm < 0 || p->outer_blocks_per_sm > 2) {
         set_error("solver parameters out of range");
         return WL_ERR_ARG;
     }
@@ -766,7 +760,7 @@ extern "C" int bicgstab_solve(wl_gauge *g, const void *b, void *x, double m0, co
     WL_CUDA_TRY(cudaStreamSynchronize(s));
     st[0].seconds = tm.sec();
     *stats = st[0];
-    return st[0].status;
+    return checked_result(st[0].status);
 }
 
 // Solution-space minimisation guess (Section 6.2.2) for mass m from the
@@ -868,9 +862,9 @@ extern "C" int multimass_solve(wl_gauge *g, const void *const *b, void *const *x
     std::vector<Vec> sol(n_mass);  // even-site solutions (outer precision) in solve order
     std::vector<Vec> ys(n_mass);   // y_j = D_eo D_oe x_j of those solutions
     std::vector<wl_solver_stats> st(n_rhs);
-    Pinned pin;
-    WL_TRY(pin.reserve(sizeof(double) * 128 * n_rhs));
-    double *hc = static_cast<double *>(pin.p);
+    void *pin = nullptr;
+    WL_TRY(g->pinned.get("mm_coef", sizeof(double) * 128 * n_rhs, &pin));
+    double *hc = static_cast<double *>(pin);
     // solution-space minimisation: Gram matrix <x_i, x_j> and <b, x_j> per rhs
     std::vector<std::vector<std::vector<std::complex<double>>>> gram;
     std::vector<std::vector<std::complex<double>>> bx;
@@ -1006,5 +1000,5 @@ extern "C" int multimass_solve(wl_gauge *g, const void *const *b, void *const *x
     }
     WL_TRY(ax.join(s));
     WL_CUDA_TRY(cudaStreamSynchronize(s));
-    return worst;
+    return checked_result(worst);
 }

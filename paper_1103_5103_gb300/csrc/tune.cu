@@ -18,9 +18,10 @@ namespace wl {
 
 const std::vector<int> &hop_variants(int prec)
 {
-    static const std::vector<int> f32 = {101, 105, 106, 108, 201, 204, 205, 401, 404, 301, 304, 305, 1104, 1106, 1202, 1203};
-    static const std::vector<int> f16 = {101, 105, 106, 108, 110, 201, 204, 206, 401, 404};
-    static const std::vector<int> f64 = {101, 103, 201};
+    static const std::vector<int> f32 = {101, 105, 106, 108, 201, 204, 205, 401, 404, 301, 304, 305, 1104, 1106, 1202, 1203,
+                                         9001, 9002, 9004, 9102, 9104};
+    static const std::vector<int> f16 = {101, 105, 106, 108, 110, 201, 204, 206, 401, 404, 9001, 9002, 9004, 9102, 9104};
+    static const std::vector<int> f64 = {101, 103, 201, 7101, 7102, 7201, 7202};
     static const std::vector<int> dfv = {101, 103, 104, 105, 106};
     static const std::vector<int> none;
     switch (prec) {
@@ -94,6 +95,7 @@ int autotune_hop(wl_gauge *g, int prec, int nrhs, cudaStream_t s, TuneResult *ou
         int st = WL_OK;
         for (int k = 0; k < 2 && st == WL_OK; ++k)
             st = hop_ex(g, in, o, nullptr, 0.0, nullptr, 0.0, 1.0, WL_ODD, 0, -v, nullptr, 0, s);
+        if (st == WL_ERR_ARG && v >= 9000 && v < 9300) continue;   // TMA tiles do not fit this lattice
         cudaEventRecord(e0, s);
         for (int k = 0; k < reps && st == WL_OK; ++k)
             st = hop_ex(g, in, o, nullptr, 0.0, nullptr, 0.0, 1.0, WL_ODD, 0, -v, nullptr, 0, s);
@@ -115,6 +117,12 @@ int autotune_hop(wl_gauge *g, int prec, int nrhs, cudaStream_t s, TuneResult *ou
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    unsigned faults = 0;
+    WL_TRY(wait_faults(&faults, true, s));
+    if (faults) {
+        set_error("autotune: a TMA-staged hop gave up waiting for its copies");
+        return WL_ERR_TIMEOUT;
+    }
     if (out) best.table = out->table;
     g->tune[key] = best;
     if (out) *out = best;

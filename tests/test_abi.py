@@ -22,13 +22,30 @@ def test_build_and_exports():
     import subprocess
     import __graft_entry__ as ge
     ge.build()
-    lib = os.path.join(ROOT, "paper_1103_5103_gb300", "libwilson.so")
-    out = subprocess.check_output(["nm", "-D", "--defined-only", lib]).decode()
-    exported = {l.split()[-1] for l in out.splitlines() if " T " in l}
     declared = _declared()
     assert declared, "no declarations parsed"
-    missing = declared - exported
-    assert not missing, f"declared but not exported: {sorted(missing)}"
+    # the library and its bounds-checked build export the same ABI
+    for name in ("libwilson.so", "libwilson_checked.so"):
+        lib = os.path.join(ROOT, "paper_1103_5103_gb300", name)
+        out = subprocess.check_output(["nm", "-D", "--defined-only", lib]).decode()
+        exported = {l.split()[-1] for l in out.splitlines() if " T " in l}
+        missing = declared - exported
+        assert not missing, f"{name}: declared but not exported: {sorted(missing)}"
+
+
+def test_checked_build_is_the_checked_one():
+    """WL_LIBRARY=checked loads libwilson_checked.so, which says so; the
+    ordinary library does not (host-only calls, no GPU needed)."""
+    import subprocess
+    import sys
+    code = "from paper_1103_5103_gb300 import api; print(api.LIB_PATH, api.is_checked_build())"
+    for env, name, flag in ((None, "libwilson.so", "False"), ("checked", "libwilson_checked.so", "True")):
+        e = dict(os.environ)
+        e.pop("WL_LIBRARY", None)
+        if env:
+            e["WL_LIBRARY"] = env
+        out = subprocess.check_output([sys.executable, "-c", code], env=e, cwd=ROOT).decode().split()
+        assert out[0].endswith(name) and out[1] == flag, out
 
 
 def test_host_only_calls():

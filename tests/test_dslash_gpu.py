@@ -262,3 +262,53 @@ def test_every_hop_variant_and_autotune(api, prec):
     v, us = api.autotune(g, prec, nrhs)
     assert v in api.HOP_VARIANTS[prec] and us > 0
     assert api.autotune(g, prec, nrhs)[0] == v          # cached
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16"])
+@pytest.mark.parametrize("dims", [(8, 12, 6, 10), (16, 8, 4, 6)])
+def test_tma_staged_hop_matches_register_hop(api, prec, dims):
+    """The TMA-staged hop (variants 9000 + rhs per tile: links and spinor
+    rows copied into shared memory by cp.async.bulk.tensor) gives, element
+    for element, the result of the register kernel for several row blocks
+    per slice, rhs counts that leave a ragged last group, both output
+    parities and the xpay epilogue; against the oracle too; and no bounded
+    wait gives up.  Lattices with X/2 not a multiple of 4 are refused."""
+    U, lat, g = _setup(api, dims, "random", precs=(prec,))
+    odd = O.parity_mask(dims)
+    stride = (lat.spinor_bytes(prec) + 255) // 256 * 256
+    for nrhs in (1, 3, 7):
+        a = torch.empty(stride * nrhs, dtype=torch.uint8, device="cuda")
+        xv = torch.empty_like(a)
+        srcs = [synth.gaussian_source(dims, 400 + r) for r in range(nrhs)]
+        for par in (0, 1):
+            for r in range(nrhs):
+                lat.spinor_import(_cuda(srcs[r]), a[r * stride:(r + 1) * stride], prec, 1 - par)
+                lat.spinor_import(_cuda(srcs[(r + 1) % nrhs]), xv[r * stride:(r + 1) * stride], prec, par)
+            mask = odd if par == 1 else ~odd
+
+            def export(buf, r):
+                out = torch.zeros((lat.volume, 4, 3), dtype=torch.complex128, device="cuda")
+                lat.spinor_export(buf[r * stride:(r + 1) * stride], out, prec, par)
+                return out.cpu().numpy()[mask]
+            want = torch.zeros_like(a)
+            api.hop_batch(g, a, want, nrhs, stride, 0.25, prec, par, -101, x=xv)
+            for v in (9001, 9002, 9004, 9102, 9104):
+                got = torch.zeros_like(a)
+                api.hop_batch(g, a, got, nrhs, stride, 0.25, prec, par, -v, x=xv)
+                for r in range(nrhs):
+                    # same arithmetic; the compiler may contract the row-2
+                    # rebuild differently, and FP16 storage rounds at 2^-11
+                    assert rel(export(got, r), export(want, r)) < {"f32": 1e-6, "f16": 2e-3}[prec], (v, nrhs, par, r)
+            for r in range(nrhs):
+                src = srcs[r].copy()
+                src[mask] = 0   # the input lives on the other parity
+                ref = srcs[(r + 1) % nrhs] + 0.25 * O.hop(U, dims, src)
+                assert rel(export(want, r), ref[mask]) < TOL[prec], (nrhs, par, r)
+    assert api.wait_faults() == 0
+    bad = (6, 4, 4, 4)   # X/2 = 3
+    _, lat2, g2 = _setup(api, bad, "random", precs=(prec,))
+    s2 = (lat2.spinor_bytes(prec) + 255) // 256 * 256
+    a2 = torch.zeros(s2, dtype=torch.uint8, device="cuda")
+    with pytest.raises(api.WilsonError) as e:
+        api.hop_batch(g2, a2, torch.zeros_like(a2), 1, s2, 1.0, prec, 0, -9001)
+    assert e.value.status == api.WL_ERR_ARG

@@ -531,3 +531,44 @@ def test_full_residual_from_last_check_equals_recomputed(api, outer):
             assert rel(x1, x0) < 1e-14
             o = O.true_relres(U, dims, b, x0, m)
             assert abs(o - a) <= slack * o, (r, m, o, a)
+
+
+def test_grid_stride_outer_hops_and_concurrent_handles(api):
+    """FP64 residual hops as a grid-stride kernel (outer_blocks_per_sm 1, 2)
+    give the solutions of the full-grid launch; and two batches solved at the
+    same time on two handles and two streams, from two host threads, give
+    the solutions of the same batches solved one after the other."""
+    import threading
+    dims = (8, 8, 8, 16)
+    U, lat, _ = _gauge(api, dims, 0.5, 81, precs=("f64", "f16"))
+    bs = [_cuda(synth.point_source(dims, s, 1)) for s in range(4)]
+    masses = [0.4, 0.2, 0.1]
+    gs = [api.Gauge(lat, _cuda(U), precs=("f64", "f16")) for _ in range(2)]
+    ref = []
+    for k in range(2):
+        ref.append(api.multimass_solve(gs[0], bs[2 * k:2 * k + 2], masses, api.params(inner_prec="f16"))[0])
+    for ob in (1, 2):
+        xs, st = api.multimass_solve(gs[0], bs[0:2], masses, api.params(inner_prec="f16", outer_blocks_per_sm=ob))
+        for r in range(2):
+            for i in range(len(masses)):
+                assert st[r][i]["true_relres"] <= 1e-10
+                assert rel(xs[r][i].cpu().numpy(), ref[0][r][i].cpu().numpy()) < 1e-14, (ob, r, i)
+    streams = [torch.cuda.Stream() for _ in range(2)]
+    out = [None, None]
+
+    def work(k):
+        out[k] = api.multimass_solve(gs[k], bs[2 * k:2 * k + 2], masses,
+                                     api.params(inner_prec="f16", outer_blocks_per_sm=1), stream=streams[k])
+    th = [threading.Thread(target=work, args=(k,)) for k in range(2)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    torch.cuda.synchronize()
+    for k in range(2):
+        xs, st = out[k]
+        for r in range(2):
+            for i, m in enumerate(masses):
+                assert st[r][i]["status"] == api.WL_OK and st[r][i]["true_relres"] <= 1e-10
+                assert rel(xs[r][i].cpu().numpy(), ref[k][r][i].cpu().numpy()) < 1e-14, (k, r, i)
+                assert O.true_relres(U, dims, bs[2 * k + r].cpu().numpy(), xs[r][i].cpu().numpy(), m) <= 1.02e-10
