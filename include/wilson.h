@@ -384,6 +384,28 @@ int wl_autotune(wl_gauge *g, int prec, int n_rhs, void *stream, int *variant, do
  * solver check it and return WL_ERR_TIMEOUT when it is non-zero. */
 int wl_wait_faults(unsigned *count, int reset, void *stream);
 
+/* One fused vector kernel of the BiCGstab iteration (Section 5: the vector
+ * utilities, here one pass per update with its reductions) applied to
+ * caller-owned internal half-lattice vectors: n_rhs vectors of precision
+ * prec (WL_F64, WL_F32 or WL_F16; the layout wl_spinor_import writes),
+ * rhs_stride bytes apart (a multiple of 256), vecs[k] the first rhs of
+ * operand k.  Per-rhs complex scalars in scal[6 r .. 6 r + 5] = alpha,
+ * omega, beta (re, im each).  A test hook for the kernels the solvers run:
+ *   WL_VEC_S      s = r - alpha v                          vecs r, v, s
+ *   WL_VEC_XR     x += alpha p + omega s; r = s - omega t  vecs x, p, s, t, r, rhat
+ *                 (x is FP32 for FP32 and FP16 data, FP64 for FP64);
+ *                 dots[3 r ..]: <rhat, r> (re, im) and ||r||^2 of the new r
+ *   WL_VEC_P      p = r + beta (p - omega v)               vecs r, p, v
+ *   WL_VEC_NORM2  dots[r] = ||a||^2                        vecs a
+ * Inner products: FP32 per site, FP32 within a warp, FP64 across warps and
+ * blocks.  Synchronises the stream. */
+#define WL_VEC_S     0
+#define WL_VEC_XR    1
+#define WL_VEC_P     2
+#define WL_VEC_NORM2 3
+int wl_vector_op(wl_gauge *g, int kind, int prec, int n_rhs, size_t rhs_stride, void *const *vecs,
+                 const double *scal, double *dots, void *stream);
+
 /* Bounds-checked build (no paper counterpart): libwilson_checked.so is the
  * same library compiled with every site index of an internal spinor or link
  * access tested against its array length.  The first violation in each

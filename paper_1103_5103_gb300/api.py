@@ -100,6 +100,8 @@ _sig("wl_autotune", [_vp, _int, _int, _vp, ctypes.POINTER(_int), ctypes.POINTER(
 _sig("wl_profile_enable", [_vp, _int])
 _sig("wl_wait_faults", [ctypes.POINTER(ctypes.c_uint), _int, _vp])
 _sig("wl_checked_status", [ctypes.POINTER(ctypes.c_ulonglong), _int])
+_sig("wl_vector_op", [_vp, _int, _int, _int, ctypes.c_size_t, ctypes.POINTER(_vp), ctypes.POINTER(_dbl),
+                      ctypes.POINTER(_dbl), _vp])
 _sig("wl_is_checked_build", [])
 _sig("wl_persistent_selftest", [_vp, _int, _int, _dbl, _vp])
 _sig("wl_profile_read", [_vp, ctypes.POINTER(KernelProfile)])
@@ -346,6 +348,28 @@ def wait_faults(reset: bool = True, stream=None) -> int:
     n = ctypes.c_uint()
     _check(_lib.wl_wait_faults(ctypes.byref(n), int(reset), _stream(stream)))
     return n.value
+
+
+VEC_S, VEC_XR, VEC_P, VEC_NORM2 = 0, 1, 2, 3
+
+
+def vector_op(g: Gauge, kind: int, prec, n_rhs: int, rhs_stride: int, vecs, scal=None, stream=None):
+    """wl_vector_op on internal vectors (uint8 CUDA tensors holding n_rhs
+    vectors rhs_stride bytes apart); scal: per-rhs (alpha, omega, beta)
+    complex triples.  Returns the dots (list) for VEC_XR / VEC_NORM2."""
+    vp = (_vp * len(vecs))(*[_ptr(v).value for v in vecs])
+    sc = None
+    if scal is not None:
+        flat = []
+        for a, o, b in scal:
+            flat += [complex(a).real, complex(a).imag, complex(o).real, complex(o).imag,
+                     complex(b).real, complex(b).imag]
+        sc = (_dbl * len(flat))(*flat)
+    nd = 3 * n_rhs if kind == VEC_XR else n_rhs
+    d = (_dbl * nd)()
+    _check(_lib.wl_vector_op(g.handle, int(kind), _prec(prec), int(n_rhs), int(rhs_stride), vp, sc, d,
+                             _stream(stream)))
+    return list(d)
 
 
 def checked_status(reset: bool = True) -> int:

@@ -708,6 +708,72 @@ extern "C" int wl_persistent_selftest(wl_gauge *g, int prec, int inject_missing_
                             2, wait_limit_s, inject_missing_arrival ? 1 : 0, s);
 }
 
+extern "C" int wl_vector_op(wl_gauge *g, int kind, int prec, int n_rhs, size_t rhs_stride, void *const *vecs,
+                            const double *scal, double *dots, void *stream)
+{
+    const int nv = kind == WL_VEC_S ? 3 : kind == WL_VEC_XR ? 6 : kind == WL_VEC_P ? 3 : kind == WL_VEC_NORM2 ? 1 : 0;
+    if (!g || nv == 0 || !vecs || n_rhs < 1 || n_rhs > 64 || !valid_prec(prec) || prec == WL_DF ||
+        (kind != WL_VEC_NORM2 && !scal) || ((kind == WL_VEC_XR || kind == WL_VEC_NORM2) && !dots)) {
+        set_error("wl_vector_op: bad argument");
+        return WL_ERR_ARG;
+    }
+    const Geom &geo = g->lat->geom;
+    const size_t need = (spinor_bytes(geo, prec) + 255) & ~(size_t)255;
+    const size_t need_x = (spinor_bytes(geo, prec == WL_F64 ? WL_F64 : WL_F32) + 255) & ~(size_t)255;
+    if (rhs_stride < std::max(need, kind == WL_VEC_XR ? need_x : need) || rhs_stride % 256) {
+        set_error("wl_vector_op: rhs_stride must be a multiple of 256 holding one internal vector");
+        return WL_ERR_ARG;
+    }
+    for (int k = 0; k < nv; ++k)
+        if (!vecs[k]) { set_error("wl_vector_op: NULL vector"); return WL_ERR_ARG; }
+    std::lock_guard<std::mutex> lock(g->mu);
+    cudaStream_t s = as_stream(stream);
+    Vec v[6];
+    for (int k = 0; k < nv; ++k) {
+        v[k].ptr = vecs[k];
+        v[k].prec = prec;
+        v[k].nrhs = n_rhs;
+        v[k].rhs_bytes = rhs_stride;
+    }
+    Scratch sc;
+    WL_TRY(get_scratch(g, n_rhs, &sc, s));
+    std::vector<BiState> hs(n_rhs);
+    for (int r = 0; r < n_rhs && kind != WL_VEC_NORM2; ++r) {
+        BiState &b = hs[r];
+        std::memset(&b, 0, sizeof(b));
+        b.alpha_re = scal[6 * r + 0];
+        b.alpha_im = scal[6 * r + 1];
+        b.omega_re = scal[6 * r + 2];
+        b.omega_im = scal[6 * r + 3];
+        b.beta_re = scal[6 * r + 4];
+        b.beta_im = scal[6 * r + 5];
+        b.rho_re = 1.0;       // previous <rhat, r>: lets the update evaluate beta
+        b.target2 = -1.0;     // never converged
+    }
+    if (kind != WL_VEC_NORM2)
+        WL_CUDA_TRY(cudaMemcpyAsync(sc.state, hs.data(), sizeof(BiState) * n_rhs, cudaMemcpyHostToDevice, s));
+    if (kind == WL_VEC_S) {
+        WL_TRY(blas_s_update(geo, v[0], v[1], v[2], sc.state, s));
+    } else if (kind == WL_VEC_P) {
+        WL_TRY(blas_p_update(geo, v[0], v[1], v[2], sc.state, s));
+    } else if (kind == WL_VEC_XR) {
+        v[0].prec = prec == WL_F64 ? WL_F64 : WL_F32;   // the accumulator of the inner solve
+        WL_TRY(blas_xr_update(geo, v[0], v[1], v[2], v[3], v[4], v[5], sc.state, sc.partials, s));
+        WL_CUDA_TRY(cudaMemcpyAsync(hs.data(), sc.state, sizeof(BiState) * n_rhs, cudaMemcpyDeviceToHost, s));
+    } else {
+        WL_TRY(blas_norm2(geo, v[0], sc.norms, sc.partials, sc.tickets, s));
+        WL_CUDA_TRY(cudaMemcpyAsync(dots, sc.norms, sizeof(double) * n_rhs, cudaMemcpyDeviceToHost, s));
+    }
+    WL_CUDA_TRY(cudaStreamSynchronize(s));
+    if (kind == WL_VEC_XR)
+        for (int r = 0; r < n_rhs; ++r) {
+            dots[3 * r + 0] = hs[r].rho_re;
+            dots[3 * r + 1] = hs[r].rho_im;
+            dots[3 * r + 2] = hs[r].rr;
+        }
+    return checked_result(WL_OK);
+}
+
 extern "C" int wl_profile_enable(wl_gauge *g, int on)
 {
     if (!g) { set_error("wl_profile_enable: NULL"); return WL_ERR_ARG; }
