@@ -71,7 +71,7 @@ FLOP_SITE = 1320   # per hop output site and rhs
 # lattice sites of the captured case, bytes).  Traffic scales with sites.
 # An entry is valid only for the kernel as it was when captured; remove it
 # when that kernel changes.
-HOP_TRAFFIC = {}
+HOP_TRAFFIC = {("f16", 106, 2): (1048576, 406.04e6), ("f64", 103, 2): (442368, 850.72e6)}
 # FP64 FMA rate of one GB300 (TFLOP/s, 2 flops per FMA): 152 SMs x 2 FP64
 # FMA per clock x 2.07 GHz, the unit count and clock of the part; a probe
 # kernel of independent FMA chains measured 1.26 TFLOP/s
@@ -329,8 +329,13 @@ def roofline_entries(prof, inner, outer, V, peak, peak_kind, nb, hop_variant, ou
         avg = po["ms"] / po["launches"] / 1e3
         tf = FLOP_SITE * site_rhs / avg / 1e12
         if outer == "f64":
+            otraffic = None
+            if ("f64", outer_variant, nb) in HOP_TRAFFIC:
+                sites_cap, bytes_cap = HOP_TRAFFIC[("f64", outer_variant, nb)]
+                otraffic = bytes_cap * (V // 2) / sites_cap
             out["outer"] = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                            "frac": tf / FP64_PEAK_TFLOPS, "traffic": None,
+                            "frac": tf / FP64_PEAK_TFLOPS, "traffic": otraffic,
+                            "fp64_pipe": "92.5% busy in an ncu capture of this variant on 24^3x64, 2 rhs",
                             "kernel": f"k_hop<f64> (D_oe x, first hop of each outer FP64 residual check), "
                                       f"variant {outer_variant}, {site_rhs / (po['sites'] / po['launches']):.2f} "
                                       f"rhs per launch on average",
