@@ -35,11 +35,14 @@ COUNTS = {"iterations": [10.0, 8.0, 3.0], "restarts": [2.0, 1.0, 0.0], "sources"
 def test_reference_line_keys_and_scaling(monkeypatch, capsys):
     monkeypatch.delenv("RANK", raising=False)
     monkeypatch.delenv("WORLD_SIZE", raising=False)
-    samples = [(1.0, 2.0, 9.0)] * 3 + [(1.0, 2.5, 9.0), (2.0, 3.5, 9.0)]  # warm-up first, then timed
+    # the calibration (M_prec 1.0 s, iteration 2.5 s), then per step one
+    # application: warm-up first, then the timed ones
+    samples = [(1.0, 2.5, 9.0)] + [(1.0, None, 1.0)] * 3 + [(1.0, None, 1.0), (2.0, None, 2.0)]
     calls = []
 
-    def fake_sample(cfg, U, b):
-        calls.append(1)
+    def fake_sample(cfg, U, b, iteration=True):
+        calls.append(iteration)
+        assert iteration == (len(calls) == 1)
         return samples[len(calls) - 1]
 
     monkeypatch.setattr(bench, "oracle_sample", fake_sample)
@@ -47,12 +50,12 @@ def test_reference_line_keys_and_scaling(monkeypatch, capsys):
     monkeypatch.setattr(bench, "oracle_threads", lambda: 4)
     bench.run_reference(_args(), _tiny_cfg())
     line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
-    assert len(calls) == 5                      # 3 warm-up + 2 timed samples
+    assert len(calls) == 6                      # calibration, 3 warm-up + 2 timed samples
 
     def step(t_mprec, t_iter):   # 12 sources; per mass iterations x t_iter + (4.5 + restarts) x t_mprec
         return 12 * sum(i * t_iter + (4.5 + r) * t_mprec for i, r in zip(COUNTS["iterations"], COUNTS["restarts"]))
     assert line["impl"] == "reference"
-    assert line["value"] == pytest.approx((step(1.0, 2.5) + step(2.0, 3.5)) / 2)   # timed steps only
+    assert line["value"] == pytest.approx((step(1.0, 2.5) + step(2.0, 5.0)) / 2)   # timed steps only
     assert line["ms_per_step"] == pytest.approx(line["value"] * 1e3)
     assert line["unit"] == bench.UNIT and line["metric"] == bench.METRIC
     assert line["higher_is_better"] is False and line["steps"] == 2 and line["warmup"] == 3
