@@ -428,6 +428,7 @@ def run_ours(args, cfg):
     prm = api.params(inner_prec=inner, rhs_block=args.rhs_block, outer_prec=outer,
                      inner_tol=args.inner_tol, reliable=int(args.reliable), guess_max=args.guess_max,
                      verify_full=int(args.verify_full), outer_blocks_per_sm=ob if outer == "f64" else 0,
+                     graph_iters=args.graph_iters,
                      inner_solver=api.SOLVER_CG if args.inner_solver == "cg" else api.SOLVER_BICGSTAB,
                      mode={"graph": api.MODE_GRAPH, "persistent": api.MODE_PERSISTENT, "host": api.MODE_HOST}[args.mode])
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -632,6 +633,7 @@ def run_ours(args, cfg):
                                         "global reductions") if outer == "f64" else
                                        "double-float (about 48-bit) residual, accumulator and reconstruction",
                    "inner_tol": args.inner_tol or "library default", "mode": args.mode,
+                   "graph_iters": args.graph_iters,
                    "guess_max": args.guess_max or "all earlier masses",
                    "outer_loop": "reliable updates" if args.reliable else "restarted defect correction",
                    "inner_solver": "CG on the normal equations" if args.inner_solver == "cg" else "BiCGstab",
@@ -741,6 +743,8 @@ def main():
     ap.add_argument("--outer-blocks", type=int, default=-1,
                     help="FP64 residual hops as a grid-stride kernel of this many blocks per SM (0: full grid; "
                          "default: the workload's)")
+    ap.add_argument("--graph-iters", type=int, default=8,
+                    help="inner iterations per captured CUDA graph")
     ap.add_argument("--guess-max", type=int, default=0,
                     help="earlier masses the Lagrange guess uses (0: all, the paper's choice)")
     ap.add_argument("--verify-full", action="store_true",

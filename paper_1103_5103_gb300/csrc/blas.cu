@@ -105,8 +105,7 @@ __global__ void __launch_bounds__(kBlock) k_xr_update(Geom g, Vec x, Vec p, Vec 
         cx<R> rv[12];
 #pragma unroll
         for (int k = 0; k < 12; ++k) rv[k] = sv_[k] - om * tv[k];
-        SpinorIO<P>::roundtrip(rv);
-        st<P>(r, q.r, g.stride, q.i, rv);
+        SpinorIO<P>::store_rounded(r.rhs(q.r), g.stride, q.i, rv);
         cx<R> rh[12];
         ld<P>(rhat, q.r, g.stride, q.i, rh);
         cx<R> d = {R(0), R(0)};
@@ -202,8 +201,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_xr(Geom g, Vec x, Vec p, Vec w, V
             rv[k] = {fma(-(R)al, wv[k].re, rv[k].re), fma(-(R)al, wv[k].im, rv[k].im)};
         }
         SpinorIO<PX>::store(x.rhs(q.r), g.stride, q.i, xv);
-        SpinorIO<P>::roundtrip(rv);
-        st<P>(r, q.r, g.stride, q.i, rv);
+        SpinorIO<P>::store_rounded(r.rhs(q.r), g.stride, q.i, rv);
         R n = R(0);
 #pragma unroll
         for (int k = 0; k < 12; ++k) n = fma(rv[k].re, rv[k].re, fma(rv[k].im, rv[k].im, n));
@@ -305,8 +303,7 @@ __global__ void __launch_bounds__(kBlock) k_restart(Geom g, Vec r64, Vec r, Vec 
         cx<R> v[12];
 #pragma unroll
         for (int k = 0; k < 12; ++k) v[k] = cconv<R>(a[k]);
-        SpinorIO<P>::roundtrip(v);
-        st<P>(r, q.r, g.stride, q.i, v);
+        SpinorIO<P>::store_rounded(r.rhs(q.r), g.stride, q.i, v);
         cx<R> h[12];
         if (mode == 1) {
             st<P>(rhat, q.r, g.stride, q.i, v);
@@ -570,6 +567,78 @@ int blas_lincomb2(const Geom &g, const double *c1_dev, const Vec *const *in, int
     else if (o.prec == WL_F64)
         k_lincomb<WL_F64, false><<<grid, kBlock, 0, s>>>(g, li, k, k2, o.rhs_bytes, o.nrhs, c1_dev, c2_dev, o1, o2);
     else { set_error("blas_lincomb: outer precision only"); return WL_ERR_ARG; }
+    WL_CUDA_TRY(cudaGetLastError());
+    note_launch(s);
+    return WL_OK;
+}
+
+// Initial guess and first residual of a mass in one pass over the stored
+// solutions x_j and their y_j = D_eo D_oe x_j (j < k):
+//   x = sum_j c_j x_j,   r = b_prec - x + sum_j d_j y_j   (d_j = kappa^2 c_j),
+// which by linearity is b_prec - M_prec x without a hop.  Written as
+// b_prec - x + ..., x is formed once and subtracted, not recombined from
+// the x_j: 48 k + 24 FMAs per site and rhs instead of 72 k + 24 -- in FP64,
+// whose FMA rate on GB300 is 1/57 of FP32's, that is the cost of the pass.
+// in: x_0..x_{k-1}, y_0..y_{k-1}, b_prec.  Coefficients per rhs: c[r k + j],
+// d[r k + j] (complex: re, im pairs).
+template <int PO, bool CPLX>
+__global__ void __launch_bounds__(kBlock) k_guess_residual(Geom g, LinIn in, int k, size_t rhs_bytes, int nrhs,
+                                                           const double *c, const double *d, Vec xo, Vec ro)
+{
+    using R = RT<PO>;
+    const SiteIdx q = site_idx(nrhs);
+    if (q.i >= g.Vh) return;
+    const size_t off = (size_t)q.r * rhs_bytes;
+    cx<R> x[12], r[12], v[12];
+#pragma unroll
+    for (int e = 0; e < 12; ++e) x[e] = acc_zero<R>();
+    for (int j = 0; j < k; ++j) {
+        SpinorIO<PO>::load(static_cast<const char *>(in.p[j]) + off, g.stride, q.i, v);
+        if constexpr (CPLX) {
+            const double *w = c + 2 * ((size_t)q.r * k + j);
+            const cx<R> z = {Conv<R>::from(w[0]), Conv<R>::from(w[1])};
+#pragma unroll
+            for (int e = 0; e < 12; ++e) x[e] = cmad(z, v[e], x[e]);
+        } else {
+            const R w = Conv<R>::from(c[(size_t)q.r * k + j]);
+#pragma unroll
+            for (int e = 0; e < 12; ++e) x[e] = {fma(w, v[e].re, x[e].re), fma(w, v[e].im, x[e].im)};
+        }
+    }
+    SpinorIO<PO>::load(static_cast<const char *>(in.p[2 * k]) + off, g.stride, q.i, r);
+#pragma unroll
+    for (int e = 0; e < 12; ++e) r[e] = r[e] - x[e];
+    for (int j = 0; j < k; ++j) {
+        SpinorIO<PO>::load(static_cast<const char *>(in.p[k + j]) + off, g.stride, q.i, v);
+        if constexpr (CPLX) {
+            const double *w = d + 2 * ((size_t)q.r * k + j);
+            const cx<R> z = {Conv<R>::from(w[0]), Conv<R>::from(w[1])};
+#pragma unroll
+            for (int e = 0; e < 12; ++e) r[e] = cmad(z, v[e], r[e]);
+        } else {
+            const R w = Conv<R>::from(d[(size_t)q.r * k + j]);
+#pragma unroll
+            for (int e = 0; e < 12; ++e) r[e] = {fma(w, v[e].re, r[e].re), fma(w, v[e].im, r[e].im)};
+        }
+    }
+    SpinorIO<PO>::store(xo.rhs(q.r), g.stride, q.i, x);
+    SpinorIO<PO>::store(ro.rhs(q.r), g.stride, q.i, r);
+}
+
+int blas_guess_residual(const Geom &g, const double *c_dev, const double *d_dev, const Vec *const *in, int k,
+                        const Vec &x, const Vec &r, cudaStream_t s, bool complex_coef)
+{
+    if (k < 0 || k > 15) { set_error("blas_guess_residual: 0..15 earlier solutions"); return WL_ERR_ARG; }
+    LinIn li;
+    for (int j = 0; j < 2 * k + 1; ++j) li.p[j] = in[j]->ptr;
+    const int grid = grid_of(g, x.nrhs);
+#define WL_GR(PO, CP) k_guess_residual<PO, CP><<<grid, kBlock, 0, s>>>(g, li, k, x.rhs_bytes, x.nrhs, c_dev, d_dev, x, r)
+    if (x.prec == WL_DF && complex_coef) WL_GR(WL_DF, true);
+    else if (x.prec == WL_DF) WL_GR(WL_DF, false);
+    else if (x.prec == WL_F64 && complex_coef) WL_GR(WL_F64, true);
+    else if (x.prec == WL_F64) WL_GR(WL_F64, false);
+    else { set_error("blas_guess_residual: outer precision only"); return WL_ERR_ARG; }
+#undef WL_GR
     WL_CUDA_TRY(cudaGetLastError());
     note_launch(s);
     return WL_OK;

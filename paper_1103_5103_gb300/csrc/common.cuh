@@ -327,6 +327,10 @@ template <> struct SpinorIO<WL_F64> {
         return 1.0;
     }
     static __device__ __forceinline__ void roundtrip(cx<R> (&)[12]) {}
+    static __device__ __forceinline__ void store_rounded(void *base, int stride, int i, cx<R> (&v)[12])
+    {
+        store(base, stride, i, v);
+    }
     static __device__ __forceinline__ void store(void *base, int stride, int i, const cx<R> (&v)[12])
     {
         if (!WL_STORE_OK(i, stride, 2)) return;
@@ -357,6 +361,10 @@ template <> struct SpinorIO<WL_F32> {
         return 1.f;
     }
     static __device__ __forceinline__ void roundtrip(cx<R> (&)[12]) {}
+    static __device__ __forceinline__ void store_rounded(void *base, int stride, int i, cx<R> (&v)[12])
+    {
+        store(base, stride, i, v);
+    }
     static __device__ __forceinline__ void store(void *base, int stride, int i, const cx<R> (&v)[12])
     {
         if (!WL_STORE_OK(i, stride, 2)) return;
@@ -457,6 +465,25 @@ template <> struct SpinorIO<WL_F16> {
             v[k] = {h.x * m, h.y * m};
         }
     }
+    // store, and replace v by the stored values (one scale and one packing
+    // for both)
+    static __device__ __forceinline__ void store_rounded(void *base, int stride, int i, cx<R> (&v)[12])
+    {
+        if (!WL_STORE_OK(i, stride, 2)) return;
+        const float m = site_scale(v);
+        const float inv = m > 0.f ? 1.0f / m : 0.f;
+        uint32_t w[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            w[k] = pack_half2(v[k].re * inv, v[k].im * inv);
+            const float2 h = unpack_half2(w[k]);
+            v[k] = {h.x * m, h.y * m};
+        }
+        uint4 *p = static_cast<uint4 *>(base);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) p[(size_t)k * stride + i] = make_uint4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
+        const_cast<float *>(norms(base, stride))[i] = m;
+    }
 };
 
 template <> struct SpinorIO<WL_DF> {
@@ -479,6 +506,10 @@ template <> struct SpinorIO<WL_DF> {
         return df(1.f);
     }
     static __device__ __forceinline__ void roundtrip(cx<R> (&)[12]) {}
+    static __device__ __forceinline__ void store_rounded(void *base, int stride, int i, cx<R> (&v)[12])
+    {
+        store(base, stride, i, v);
+    }
     static __device__ __forceinline__ void store(void *base, int stride, int i, const cx<R> (&v)[12])
     {
         if (!WL_STORE_OK(i, stride, 2)) return;

@@ -777,8 +777,7 @@ __device__ __forceinline__ void hop_reduce_body(const HopArgs &a, const EpiReduc
         for (int k = 0; k < 12; ++k) o[k] = R(e.a1) * xv[k] + R(coef) * acc[0][k];
         // Reductions use the stored (rounded) values so that they describe
         // exactly the vector the next kernels read.
-        SpinorIO<P>::roundtrip(o);
-        SpinorIO<P>::store(static_cast<char *>(e.out) + off, a.g.stride, i, o);
+        SpinorIO<P>::store_rounded(static_cast<char *>(e.out) + off, a.g.stride, i, o);
         if constexpr (KIND == 0) {
             cx<R> rh[12];
             SpinorIO<P>::load(static_cast<const char *>(e.rhat) + off, a.g.stride, i, rh);

@@ -146,6 +146,10 @@ int blas_lincomb(const Geom &g, const double *cre_dev, const double *cim_dev, co
                  const Vec &out, cudaStream_t s);
 // out = sum_{j<k} c1_j in_j and out2 = sum_{j<k2} c2_j in_j in one pass;
 // complex_coef: the coefficients are (re, im) pairs, c[2 * (r * k + j) + {0, 1}]
+// x = sum_j c_j x_j and r = b_prec - x + sum_j d_j y_j in one pass;
+// in = x_0..x_{k-1}, y_0..y_{k-1}, b_prec (k <= 15).
+int blas_guess_residual(const Geom &g, const double *c_dev, const double *d_dev, const Vec *const *in, int k,
+                        const Vec &x, const Vec &r, cudaStream_t s, bool complex_coef);
 int blas_lincomb2(const Geom &g, const double *c1_dev, const Vec *const *in, int k, const Vec *out,
                   const double *c2_dev, int k2, const Vec *out2, cudaStream_t s, bool complex_coef = false);
 // For each rhs r: dots[r][j] = <in_j[r], a[r]> (j < n, n <= 16), FP64 sums

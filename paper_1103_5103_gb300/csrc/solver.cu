@@ -972,10 +972,11 @@ extern "C" int multimass_solve(wl_gauge *g, const void *const *b, void *const *x
         if (p->guess_max > 0) kk = std::min(kk, p->guess_max);
         const int j0 = k - kk;
         const bool ssm = p->guess == WL_GUESS_SSM && kk > 0;
-        const int ni = 2 * kk + 1;  // inputs of the residual combination
         // x_guess = sum_j g_j x_j (g_j real for POLY, complex for SSM); by
         // linearity the first residual b_prec - x_guess + kappa^2 sum_j g_j y_j,
         // with y_j = D_eo D_oe x_j kept from mass j, needs no hop.
+        // Coefficients: g_j at coef[r kk + j], kappa^2 g_j at coef[32 n_rhs + r kk + j]
+        // (complex: re, im pairs).
         if (!ssm) {
             // Lagrange extrapolation of psi = x / (m + 4) (Eq. Poly):
             // g_j = (m + 4) w_j / (m_j + 4), w_j = prod_{i != j} (m - m_i) / (m_j - m_i)
@@ -990,43 +991,34 @@ extern "C" int multimass_solve(wl_gauge *g, const void *const *b, void *const *x
                     }
                 cj[j] = (m + 4.0) * w / (mj + 4.0);
             }
-            for (int r = 0; r < n_rhs; ++r) {
+            for (int r = 0; r < n_rhs; ++r)
                 for (int j = 0; j < kk; ++j) {
-                    hc[r * kk + j] = cj[j];                        // x_guess
-                    hc[32 * n_rhs + r * ni + j] = -cj[j];          // - x_j
-                    hc[32 * n_rhs + r * ni + kk + j] = k2 * cj[j]; // + kappa^2 y_j
+                    hc[r * kk + j] = cj[j];
+                    hc[32 * n_rhs + r * kk + j] = k2 * cj[j];
                 }
-                hc[32 * n_rhs + r * ni + 2 * kk] = 1.0;            // + b_prec
-            }
-            WL_CUDA_TRY(cudaMemcpyAsync(sc.coef, hc, sizeof(double) * 64 * n_rhs, cudaMemcpyHostToDevice, s));
         } else {
             for (int r = 0; r < n_rhs; ++r) {
                 std::vector<std::complex<double>> gj(kk);
                 ssm_guess(gram[r], bx[r], bn2[r], m, m0, order, j0, kk, gj);
                 for (int j = 0; j < kk; ++j) {
-                    const std::complex<double> a = gj[j], c = -gj[j], d = k2 * gj[j];
-                    hc[2 * (r * kk + j)] = a.real();
-                    hc[2 * (r * kk + j) + 1] = a.imag();
-                    hc[32 * n_rhs + 2 * (r * ni + j)] = c.real();
-                    hc[32 * n_rhs + 2 * (r * ni + j) + 1] = c.imag();
-                    hc[32 * n_rhs + 2 * (r * ni + kk + j)] = d.real();
-                    hc[32 * n_rhs + 2 * (r * ni + kk + j) + 1] = d.imag();
+                    const std::complex<double> d = k2 * gj[j];
+                    hc[2 * (r * kk + j)] = gj[j].real();
+                    hc[2 * (r * kk + j) + 1] = gj[j].imag();
+                    hc[32 * n_rhs + 2 * (r * kk + j)] = d.real();
+                    hc[32 * n_rhs + 2 * (r * kk + j) + 1] = d.imag();
                 }
-                hc[32 * n_rhs + 2 * (r * ni + 2 * kk)] = 1.0;
-                hc[32 * n_rhs + 2 * (r * ni + 2 * kk) + 1] = 0.0;
             }
-            WL_CUDA_TRY(cudaMemcpyAsync(sc.coef, hc, sizeof(double) * 96 * n_rhs, cudaMemcpyHostToDevice, s));
         }
-        if (kk == 0) WL_CUDA_TRY(cudaMemsetAsync(sol[k].ptr, 0, sol[k].rhs_bytes * n_rhs, s));
+        if (kk > 0) WL_CUDA_TRY(cudaMemcpyAsync(sc.coef, hc, sizeof(double) * 64 * n_rhs, cudaMemcpyHostToDevice, s));
         {
             // x_guess and the first residual in one pass over the stored x_j, y_j
-            std::vector<const Vec *> ins(ni);
+            std::vector<const Vec *> ins(2 * kk + 1);
             for (int j = 0; j < kk; ++j) {
                 ins[j] = &sol[j0 + j];
                 ins[kk + j] = &ys[j0 + j];
             }
             ins[2 * kk] = &bprec;
-            WL_TRY(blas_lincomb2(geo, sc.coef, ins.data(), kk, &sol[k], sc.coef + 32 * n_rhs, ni, &r0, s, ssm));
+            WL_TRY(blas_guess_residual(geo, sc.coef, sc.coef + 32 * n_rhs, ins.data(), kk, sol[k], r0, s, ssm));
         }
         for (int r = 0; r < n_rhs; ++r) std::memset(&st[r], 0, sizeof(wl_solver_stats));
         WL_TRY(solve_one_mass(g, be, bo, bprec, sol[k], m, *p, bn2, x + im, n_mass, st, s, &ys[k], true, axp));
