@@ -124,7 +124,9 @@ typedef struct {
                             a shadow such as Gaussian noise.  <rhat, b> must not
                             vanish (WL_ERR_ARG).                                      */
     int    guess_max;    /* multimass_solve: previous masses the guess uses, the most
-                            recently solved (nearest) ones; 0 = all of them         */
+                            recently solved (nearest) ones; 0 = all of them.  With
+                            a limit the solver keeps only guess_max + 1 stored
+                            solutions per source (a ring), not one per mass      */
     int    reliable;     /* mixed-precision outer loop: 0 = restarted defect
                             correction (Section 6.2.4: each outer step restarts the
                             inner BiCGstab on the FP64-class residual); 1 = reliable

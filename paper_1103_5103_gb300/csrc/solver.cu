@@ -927,6 +927,8 @@ extern "C" int multimass_solve(wl_gauge *g, const void *const *b, void *const *x
     std::sort(order.begin(), order.end(), [&](int a, int c) { return m0[a] > m0[c]; });
     std::vector<Vec> sol(n_mass);  // even-site solutions (outer precision) in solve order
     std::vector<Vec> ys(n_mass);   // y_j = D_eo D_oe x_j of those solutions
+    const int ring = (p->guess != WL_GUESS_ZERO && p->guess_max > 0) ? std::min(n_mass, p->guess_max + 1)
+                     : p->guess == WL_GUESS_ZERO ? 1 : n_mass;
     std::vector<wl_solver_stats> st(n_rhs);
     void *pin = nullptr;
     WL_TRY(g->pinned.get("mm_coef", sizeof(double) * 128 * n_rhs, &pin));
@@ -960,8 +962,11 @@ extern "C" int multimass_solve(wl_gauge *g, const void *const *b, void *const *x
         Timer tm;
         const int im = order[k];
         const double m = m0[im];
-        WL_TRY(make_vec(g, "mm_sol" + std::to_string(k), PO, n_rhs, &sol[k]));
-        WL_TRY(make_vec(g, "mm_y" + std::to_string(k), PO, n_rhs, &ys[k]));
+        // a guess through the last guess_max masses needs only that many
+        // stored solutions: the buffers form a ring of guess_max + 1
+        const int slot = k % ring;
+        WL_TRY(make_vec(g, "mm_sol" + std::to_string(slot), PO, n_rhs, &sol[k]));
+        WL_TRY(make_vec(g, "mm_y" + std::to_string(slot), PO, n_rhs, &ys[k]));
         WL_TRY(blas_xpay(geo, be, 1.0 / (2.0 * m + 8.0), dbo, bprec, s));
         Vec r0;
         WL_TRY(make_vec(g, "dc_r64", PO, n_rhs, &r0));
