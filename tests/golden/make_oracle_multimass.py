@@ -8,13 +8,13 @@ first, Lagrange guess through all earlier solutions, even-odd BiCGstab to a
   x           -- the solution polished by the oracle's even-odd BiCGstab to
                  a 1e-13 residual (exact to far below the 1e-8 the GPU
                  solutions are compared at), at the source site, its eight
-                 neighbours and 128 random sites.
+                 neighbours and random sites (128 drawn, 32 kept).
 
 Only oracle/ and the shared input generator are used.  The oracle's
 per-site loops run on all host cores (OMP_NUM_THREADS to change):
 
-    python tests/golden/make_oracle_multimass.py --config c3 --sources 0 1 2 ...
-    python tests/golden/make_oracle_multimass.py --config c5 --sources 0
+    python tests/golden/make_oracle_multimass.py --config c3 --sources 0 1 ... 11 --trim 32
+    python tests/golden/make_oracle_multimass.py --config c5 --sources 0 11 --trim 32
 
 24^3x64 takes a few minutes per source on eight cores, 48^3x96 about an
 hour and 50 GB of host memory.
@@ -53,15 +53,38 @@ def sample_sites(dims, n_random=128, seed=7):
     return sorted(set(nb) | set(int(v) for v in rng.choice(V, size=n_random, replace=False)))
 
 
+def trim(path, n_random):
+    """Keep the source site, its neighbours and the n_random lowest of the
+    stored random sites (the file stays a few hundred kB to a few MB)."""
+    with open(path) as f:
+        out = json.load(f)
+    dims = out["dims"]
+    keep_nb = set(sample_sites(dims, n_random=0))
+    sites = out["sites"]
+    rand = sorted(s for s in sites if s not in keep_nb)[:n_random]
+    keep = sorted(keep_nb | set(rand))
+    idx = [sites.index(s) for s in keep]
+    for rec in out["sources"].values():
+        rec["x"] = [None if x is None else [x[i] for i in idx] for x in rec["x"]]
+    out["sites"] = keep
+    with open(path, "w") as f:
+        json.dump(out, f, separators=(",", ":"))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--config", choices=sorted(WORKLOADS), required=True)
-    ap.add_argument("--sources", type=int, nargs="+", default=[0],
+    ap.add_argument("--sources", type=int, nargs="*", default=[0],
                     help="spin-colour point sources k = 3 * spin + colour")
+    ap.add_argument("--trim", type=int, default=0,
+                    help="afterwards keep only the source neighbourhood and this many random sites")
     args = ap.parse_args()
     w = WORKLOADS[args.config]
     dims, masses = w["dims"], w["masses"]
     path = os.path.join(HERE, f"{args.config}_oracle_multimass.json")
+    if not args.sources and args.trim:
+        trim(path, args.trim)
+        return
     out = json.load(open(path)) if os.path.exists(path) else {
         "what": "FP64 oracle multi-mass scheme (Lagrange guess, even-odd BiCGstab) per point source and mass: "
                 "iterations at tol 1e-10 and the solution polished to 1e-13 at sampled sites",
@@ -99,6 +122,8 @@ def main():
         out["sources"][str(k)] = rec
         with open(path, "w") as f:
             json.dump(out, f, separators=(",", ":"))
+    if args.trim:
+        trim(path, args.trim)
 
 
 if __name__ == "__main__":
