@@ -53,12 +53,20 @@ CONFIGS = {
                dims=(16, 16, 16, 32), eps=0.5, seed=2, sources="z2"),
     "c1": dict(name="8^4, 1 point source x 4 masses (m0 0.5, 0.3, 0.2, 0.1), eps 0.3",
                dims=(8, 8, 8, 8), eps=0.3, seed=1, sources="point1", masses=[0.5, 0.3, 0.2, 0.1]),
-    # 10.6M sites: 16 solutions per source take 33 GB in canonical FP64 and
-    # as much again inside the solver, so the sources go two at a time
+    # 10.6M sites: 16 solutions per source take 33 GB in canonical FP64 and,
+    # with the guess through the last 8 masses, 18 GB inside the solver, so
+    # the sources go three at a time (229 GB on the device; four would take
+    # 292 of the 298 GB).  Measured on this workload: three sources per call
+    # 4.4% faster than two, 4 inner iterations per captured graph 2.5%
+    # faster than 8, the Lagrange guess through the last 8 masses 2.3%
+    # faster than through all of them (772 inner iterations against 796);
+    # FP16 inner solves refined in FP32 segments 7.5% faster than one FP16
+    # solve per outer step (228 outer steps against 289).  The end-to-end
+    # run writes the solutions of a call to 98 GB of page-locked host memory
     "c5": dict(name="48^3x96, 12 spin-colour point sources x 16 masses (m0 0.5*0.04^(i/15)), eps 0.7",
                dims=(48, 48, 48, 96), eps=0.7, seed=5, sources="points12",
-               masses=[0.5 * 0.04 ** (i / 15.0) for i in range(16)], inner="f16", source_batch=2,
-               baseline_sources=1, e2e_steps=3),
+               masses=[0.5 * 0.04 ** (i / 15.0) for i in range(16)], inner="f16", source_batch=3,
+               graph_iters=4, guess_max=8, inner_refine=1, pinned_gb=128, baseline_sources=1, e2e_steps=3),
 }
 # algorithmic bytes of one hop: per output site 8 links (12 reals: the
 # minimum the method must read), per output site and rhs one input spinor
@@ -417,7 +425,10 @@ def run_ours(args, cfg):
     # another when they run on a small grid (outer_blocks_per_sm)
     nw = max(1, min(len(batches), args.streams or cfg.get("streams", 1)))
     # links of the two precisions the solve uses
-    gs = [api.Gauge(lat, U_dev, precs=tuple(sorted({inner, outer}))) for _ in range(nw)]
+    refine = args.inner_refine if args.inner_refine is not None else cfg.get("inner_refine", 0)
+    refine = int(refine) if inner == "f16" else 0
+    gs = [api.Gauge(lat, U_dev, precs=tuple(sorted({inner, outer} | ({"f32"} if refine else set()))))
+          for _ in range(nw)]
     g = gs[0]
     bs = [torch.from_numpy(b).to(dev) for b in bs_h]
     # solution buffers for one batch of sources per worker, reused by its batches
@@ -425,10 +436,13 @@ def run_ours(args, cfg):
             for _ in range(nw)]
     xs = xs_w[0]
     ob = args.outer_blocks if args.outer_blocks >= 0 else cfg.get("outer_blocks", 0)
+    graph_iters = args.graph_iters if args.graph_iters is not None else cfg.get("graph_iters", 8)
+    guess_max = args.guess_max if args.guess_max is not None else cfg.get("guess_max", 0)
+    pinned_gb = args.pinned_gb if args.pinned_gb is not None else cfg.get("pinned_gb", 24.0)
     prm = api.params(inner_prec=inner, rhs_block=args.rhs_block, outer_prec=outer,
-                     inner_tol=args.inner_tol, reliable=int(args.reliable), guess_max=args.guess_max,
+                     inner_tol=args.inner_tol, reliable=int(args.reliable), guess_max=guess_max,
                      verify_full=int(args.verify_full), outer_blocks_per_sm=ob if outer == "f64" else 0,
-                     graph_iters=args.graph_iters,
+                     graph_iters=graph_iters, inner_refine=refine,
                      inner_solver=api.SOLVER_CG if args.inner_solver == "cg" else api.SOLVER_BICGSTAB,
                      mode={"graph": api.MODE_GRAPH, "persistent": api.MODE_PERSISTENT, "host": api.MODE_HOST}[args.mode])
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -580,7 +594,7 @@ def run_ours(args, cfg):
             times.append((time.perf_counter() - t0) * 1e3)
         return float(np.mean(times)) / 1e3
 
-    zero_copy = nw * nb * nm * x_bytes <= args.pinned_gb * (1 << 30)
+    zero_copy = nw * nb * nm * x_bytes <= pinned_gb * (1 << 30)
     t_e2e_copy = max_over_ranks(e2e_copy(), ws)
     t_e2e = max_over_ranks(e2e_zero_copy(), ws) if zero_copy else t_e2e_copy
 
@@ -633,8 +647,10 @@ def run_ours(args, cfg):
                                         "global reductions") if outer == "f64" else
                                        "double-float (about 48-bit) residual, accumulator and reconstruction",
                    "inner_tol": args.inner_tol or "library default", "mode": args.mode,
-                   "graph_iters": args.graph_iters,
-                   "guess_max": args.guess_max or "all earlier masses",
+                   "graph_iters": graph_iters,
+                   "inner_refine": ("FP16 segments, inner residual recomputed in FP32 between them, to 1e-6 "
+                                    "per outer step") if refine else None,
+                   "guess_max": guess_max or "all earlier masses",
                    "outer_loop": "reliable updates" if args.reliable else "restarted defect correction",
                    "inner_solver": "CG on the normal equations" if args.inner_solver == "cg" else "BiCGstab",
                    "full_residual": "recomputed with a hop D_eo x_o" if args.verify_full else
@@ -743,14 +759,18 @@ def main():
     ap.add_argument("--outer-blocks", type=int, default=-1,
                     help="FP64 residual hops as a grid-stride kernel of this many blocks per SM (0: full grid; "
                          "default: the workload's)")
-    ap.add_argument("--pinned-gb", type=float, default=24.0,
+    ap.add_argument("--pinned-gb", type=float, default=None,
                     help="page-locked host memory the end-to-end run may use for one batch's solutions: "
                          "within it the solver writes them to host memory itself, beyond it they are copied "
                          "out through an 8 GB ring")
-    ap.add_argument("--graph-iters", type=int, default=8,
-                    help="inner iterations per captured CUDA graph")
-    ap.add_argument("--guess-max", type=int, default=0,
-                    help="earlier masses the Lagrange guess uses (0: all, the paper's choice)")
+    ap.add_argument("--graph-iters", type=int, default=None,
+                    help="inner iterations per captured CUDA graph (default: the workload's, else 8)")
+    ap.add_argument("--guess-max", type=int, default=None,
+                    help="earlier masses the Lagrange guess uses (0: all, the paper's choice; default: the "
+                         "workload's, else 0)")
+    ap.add_argument("--inner-refine", type=int, choices=[0, 1], default=None,
+                    help="FP16 inner solves in FP16 segments with FP32 residual recomputation between them "
+                         "(default: the workload's, else 0)")
     ap.add_argument("--verify-full", action="store_true",
                     help="recompute the even half of the full residual with one more hop per mass")
     ap.add_argument("--rhs-block", type=int, default=0)

@@ -152,6 +152,15 @@ typedef struct {
                             the small grid leaves the rest of each SM to work on other
                             streams, such as the inner solve of another batch of
                             sources solved at the same time on another handle.      */
+    int    inner_refine; /* FP16 BiCGstab inner solves without reliable updates: 1
+                            runs each outer step's inner solve as FP16 segments with
+                            the inner residual recomputed in FP32 between them, so
+                            that one outer step reaches inner_tol (default 1e-6) of
+                            its residual instead of the FP16 limit near 3e-4 and the
+                            solve needs fewer outer (FP64) residual checks; the
+                            handle then needs FP32 links (else WL_ERR_ARG).  Other
+                            inner solves ignore it.  0 (default): one FP16 solve
+                            per outer step.                                          */
 } wl_solver_params;
 
 typedef struct {
@@ -169,7 +178,8 @@ typedef struct {
  * what the outer target needs), max_restarts 100,
  * WL_GUESS_POLY, WL_MODE_GRAPH, rhs_block 0, graph_iters 8, eo 1,
  * outer_prec WL_F64, shadow NULL, guess_max 0, reliable 0,
- * inner_solver WL_SOLVER_BICGSTAB, verify_full 0, outer_blocks_per_sm 0. */
+ * inner_solver WL_SOLVER_BICGSTAB, verify_full 0, outer_blocks_per_sm 0,
+ * inner_refine 0. */
 int wl_params_default(wl_solver_params *p);
 
 /* Thread-local message describing the last failing call on this thread. */

@@ -55,7 +55,7 @@ class SolverParams(ctypes.Structure):
                 ("max_restarts", _int), ("guess", _int), ("mode", _int), ("rhs_block", _int),
                 ("graph_iters", _int), ("eo", _int), ("outer_prec", _int), ("shadow", _vp),
                 ("guess_max", _int), ("reliable", _int), ("inner_solver", _int), ("verify_full", _int),
-                ("outer_blocks_per_sm", _int)]
+                ("outer_blocks_per_sm", _int), ("inner_refine", _int)]
 
 
 class SolverStats(ctypes.Structure):

@@ -276,6 +276,8 @@ int blas_p_update(const Geom &g, const Vec &r, const Vec &p, const Vec &v, BiSta
 // Per rhs, by active[r]:
 //   0: marked done, left untouched;
 //   1: restart: r = convert(r_outer); rhat = r; p = r; x = 0; rho = ||r||^2;
+//   3: as 1 but x is kept (a further segment of one inner solve whose
+//      residual r_outer was recomputed in a higher precision);
 //   2: reliable update: r = convert(r_outer), the true residual of the
 //      current outer solution; x = 0; rhat and p are kept, rho = <rhat, r>,
 //      and beta = (rho / rho_old)(alpha / omega) of the interrupted
@@ -305,7 +307,7 @@ __global__ void __launch_bounds__(kBlock) k_restart(Geom g, Vec r64, Vec r, Vec 
         for (int k = 0; k < 12; ++k) v[k] = cconv<R>(a[k]);
         SpinorIO<P>::store_rounded(r.rhs(q.r), g.stride, q.i, v);
         cx<R> h[12];
-        if (mode == 1) {
+        if (mode != 2) {
             st<P>(rhat, q.r, g.stride, q.i, v);
             st<P>(p, q.r, g.stride, q.i, v);
 #pragma unroll
@@ -313,10 +315,12 @@ __global__ void __launch_bounds__(kBlock) k_restart(Geom g, Vec r64, Vec r, Vec 
         } else {
             ld<P>(rhat, q.r, g.stride, q.i, h);
         }
-        cx<RT<PX>> z[12];
+        if (mode != 3) {
+            cx<RT<PX>> z[12];
 #pragma unroll
-        for (int k = 0; k < 12; ++k) z[k] = {RT<PX>(0), RT<PX>(0)};
-        SpinorIO<PX>::store(x.rhs(q.r), g.stride, q.i, z);
+            for (int k = 0; k < 12; ++k) z[k] = {RT<PX>(0), RT<PX>(0)};
+            SpinorIO<PX>::store(x.rhs(q.r), g.stride, q.i, z);
+        }
         cx<R> d = {R(0), R(0)};
         R n = R(0);
 #pragma unroll
@@ -391,6 +395,7 @@ int blas_restart(const Geom &g, const Vec &r64, const Vec &r, const Vec &rhat, c
                  BiState *state, double *partials, const int *active, const double *delta2, cudaStream_t s)
 {
     if (r64.prec == WL_DF) return restart_po<WL_DF>(g, r64, r, rhat, p, x, state, partials, active, delta2, s);
+    if (r64.prec == WL_F32) return restart_po<WL_F32>(g, r64, r, rhat, p, x, state, partials, active, delta2, s);
     return restart_po<WL_F64>(g, r64, r, rhat, p, x, state, partials, active, delta2, s);
 }
 

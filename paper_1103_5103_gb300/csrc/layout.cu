@@ -417,6 +417,7 @@ extern "C" int wl_params_default(wl_solver_params *p)
     p->inner_solver = WL_SOLVER_BICGSTAB;
     p->verify_full = 0;
     p->outer_blocks_per_sm = 0;
+    p->inner_refine = 0;
     return WL_OK;
 }
 

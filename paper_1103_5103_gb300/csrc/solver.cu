@@ -403,6 +403,36 @@ static int eo_defect_correction(wl_gauge *g, const Vec &bprec, const Vec &x64, d
     const int ohop = (prm.outer_blocks_per_sm > 0 && x64.prec == WL_F64)
                          ? -(7000 + 100 * (nrhs >= 2 ? 2 : 1) + prm.outer_blocks_per_sm)
                          : 0;
+    // Three levels for FP16 inner solves (prm.inner_refine): an FP16 BiCGstab
+    // stops near 3e-4 of its starting residual, where the FP16 rounding of its
+    // first iterations leaves the true residual; so one outer step runs FP16
+    // segments, recomputes the inner residual r_in - M e in FP32 between them
+    // (e is the FP32 accumulator, kept across segments) and stops at
+    // refine_tol (1e-6 by default) of the outer residual.  The FP64 check that
+    // follows then gains about 1e-6 instead of 3e-4.
+    const bool refine = prm.inner_refine && prec == WL_F16 && !prm.reliable &&
+                        prm.inner_solver == WL_SOLVER_BICGSTAB && (g->prec_mask & WL_F32);
+    Vec rin32, r32, tmp32;
+    int *mid_skip = nullptr;
+    double *h_rn32 = nullptr, *h_mdelta2 = nullptr;
+    int *h_mode = nullptr, *h_skip = nullptr;
+    if (refine) {
+        WL_TRY(make_vec(g, "dc_rin32", WL_F32, nrhs, &rin32));
+        WL_TRY(make_vec(g, "dc_r32", WL_F32, nrhs, &r32));
+        WL_TRY(make_vec(g, "dc_tmp32", WL_F32, nrhs, &tmp32));
+        void *pp = nullptr;
+        WL_TRY(g->ws.get("dc_mid_skip", sizeof(int) * nrhs, &pp));
+        mid_skip = static_cast<int *>(pp);
+        if (prm.rhs_block == 0) WL_TRY(autotune_hop(g, WL_F32, nrhs, s, nullptr));
+        void *pin2 = nullptr;
+        WL_TRY(g->pinned.get("dc_mid", nrhs * (sizeof(double) * 2 + sizeof(int) * 2), &pin2));
+        h_rn32 = static_cast<double *>(pin2);
+        h_mdelta2 = h_rn32 + nrhs;
+        h_mode = reinterpret_cast<int *>(h_mdelta2 + nrhs);
+        h_skip = h_mode + nrhs;
+    }
+    const double refine_tol = prm.inner_tol > 0 ? prm.inner_tol : 1e-6;
+    std::vector<double> d_outer(nrhs, 0.0), rn_outer(nrhs, 0.0);
     // live timing of the first residual hop of every check (wl_profile_enable)
     struct Ev {
         cudaEvent_t e[2] = {nullptr, nullptr};
@@ -464,6 +494,14 @@ static int eo_defect_correction(wl_gauge *g, const Vec &bprec, const Vec &x64, d
             const double need = 0.5 * prm.tol * bnorm[r] / rn;
             const double d = std::max(delta0, need);
             h_delta2[r] = d * d;
+            if (refine) {
+                // the outer step aims at refine_tol; its first FP16 segment at
+                // the FP16 tolerance
+                d_outer[r] = std::max(refine_tol, need);
+                rn_outer[r] = rn;
+                const double d16 = std::max(default_inner_tol(WL_F16), d_outer[r]);
+                h_delta2[r] = d16 * d16;
+            }
             h_active[r] = (prm.reliable && can_continue[r]) ? 2 : 1;
             fails[r] = rn >= 0.5 * last_rn[r] ? fails[r] + 1 : 0;  // stagnation guard
             last_rn[r] = rn;
@@ -491,10 +529,63 @@ static int eo_defect_correction(wl_gauge *g, const Vec &bprec, const Vec &x64, d
         for (int r = 0; r < nrhs; ++r)
             if (h_active[r]) cap = std::max(cap, prm.max_iter - iters[r]);
         WL_TRY(run_inner(in, prm, cap, hst, s));
+        for (int r = 0; r < nrhs; ++r)
+            if (h_active[r]) iters[r] += hst[r].iters;
+        if (refine) {
+            // FP32 copy of this outer step's right-hand side, then segments
+            WL_TRY(blas_convert(geo, r64, rin32, s));
+            std::vector<int> mid(nrhs, 0);
+            std::vector<double> seg_start(nrhs, 0.0);
+            for (int r = 0; r < nrhs; ++r) {
+                mid[r] = h_active[r] != 0;
+                seg_start[r] = rn_outer[r];
+            }
+            const int kMaxSegments = 8;
+            for (int seg = 1;; ++seg) {
+                // r32 = r_in - M_prec e in FP32 for the rhs still segmenting
+                for (int r = 0; r < nrhs; ++r) h_skip[r] = mid[r] ? 0 : 1;
+                WL_CUDA_TRY(cudaMemcpyAsync(mid_skip, h_skip, sizeof(int) * nrhs, cudaMemcpyHostToDevice, s));
+                WL_TRY(hop_ex(g, in.e, tmp32, nullptr, 0.0, nullptr, 0.0, 1.0, WL_ODD, 0, 0, mid_skip, 1, s));
+                WL_TRY(hop_ex(g, tmp32, r32, &rin32, 1.0, &in.e, -1.0, k2, WL_EVEN, 0, 0, mid_skip, 1, s));
+                WL_TRY(blas_norm2(geo, r32, in.sc.norms, in.sc.partials, in.sc.tickets, s));
+                WL_CUDA_TRY(cudaMemcpyAsync(h_rn32, in.sc.norms, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
+                WL_CUDA_TRY(cudaStreamSynchronize(s));
+                int n_mid = 0;
+                for (int r = 0; r < nrhs; ++r) {
+                    h_mode[r] = 0;
+                    if (!mid[r]) continue;
+                    const double rn32 = std::sqrt(h_rn32[r]);
+                    // done: at the outer step's target, no longer halving,
+                    // broken down, out of segments or iterations
+                    if (!(rn32 > d_outer[r] * rn_outer[r]) || !std::isfinite(rn32) || rn32 > 0.5 * seg_start[r] ||
+                        hst[r].breakdown || seg >= kMaxSegments || iters[r] >= prm.max_iter) {
+                        mid[r] = 0;
+                        continue;
+                    }
+                    const double d16 = std::max(default_inner_tol(WL_F16), 0.5 * d_outer[r] * rn_outer[r] / rn32);
+                    h_mdelta2[r] = d16 * d16;
+                    h_mode[r] = 3;   // restart from r32, keeping e
+                    seg_start[r] = rn32;
+                    ++n_mid;
+                }
+                if (n_mid == 0) break;
+                WL_CUDA_TRY(cudaMemcpyAsync(in.sc.active, h_mode, sizeof(int) * nrhs, cudaMemcpyHostToDevice, s));
+                WL_CUDA_TRY(cudaMemcpyAsync(in.sc.delta2, h_mdelta2, sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
+                WL_TRY(blas_restart(geo, r32, in.r, in.rhat, in.p, in.e, in.sc.state, in.sc.partials, in.sc.active,
+                                    in.sc.delta2, s));
+                int mcap = 0;
+                for (int r = 0; r < nrhs; ++r)
+                    if (h_mode[r]) mcap = std::max(mcap, prm.max_iter - iters[r]);
+                WL_TRY(run_inner(in, prm, mcap, hst, s));
+                for (int r = 0; r < nrhs; ++r)
+                    if (h_mode[r]) iters[r] += hst[r].iters;
+            }
+            // the outer step's active set for the accumulation
+            WL_CUDA_TRY(cudaMemcpyAsync(in.sc.active, h_active, sizeof(int) * nrhs, cudaMemcpyHostToDevice, s));
+        }
         WL_TRY(blas_accum(geo, in.e, x64, in.sc.active, s));
         for (int r = 0; r < nrhs; ++r)
             if (h_active[r]) {
-                iters[r] += hst[r].iters;
                 restarts[r] += 1;
                 can_continue[r] = hst[r].done && !hst[r].breakdown && hst[r].iters > 0;
             }
@@ -664,12 +755,17 @@ static int check_params(const wl_gauge *g, const wl_solver_params *p)
         (p->inner_solver != WL_SOLVER_BICGSTAB && p->inner_solver != WL_SOLVER_CG) ||
         (p->inner_solver == WL_SOLVER_CG && (p->reliable || p->mode == WL_MODE_PERSISTENT)) ||
         p->rhs_block < 0 || p->rhs_block > 4 || (p->outer_prec != WL_F64 && p->outer_prec != WL_DF) ||
-        (p->verify_full != 0 && p->verify_full != 1) || p->outer_blocks_per_sm < 0 || p->outer_blocks_per_sm > 2) {
+        (p->verify_full != 0 && p->verify_full != 1) || p->outer_blocks_per_sm < 0 || p->outer_blocks_per_sm > 2 ||
+        (p->inner_refine != 0 && p->inner_refine != 1)) {
         set_error("solver parameters out of range");
         return WL_ERR_ARG;
     }
     if (!(g->prec_mask & p->outer_prec) || !(g->prec_mask & p->inner_prec)) {
         set_error("gauge handle needs links of the outer and of the inner precision");
+        return WL_ERR_ARG;
+    }
+    if (p->inner_refine && p->inner_prec == WL_F16 && !(g->prec_mask & WL_F32)) {
+        set_error("inner_refine with an FP16 inner solve needs FP32 links on the gauge handle");
         return WL_ERR_ARG;
     }
     return WL_OK;

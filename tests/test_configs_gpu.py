@@ -136,19 +136,21 @@ def test_24c64_twelve_point_sources_batched(api, outer):
 
 
 @pytest.mark.parametrize("outer", ["f64", "df"])
-def test_48c96_fp16_inner_two_sources_sixteen_masses(api, outer):
-    """48^3x96 (10.6M sites), eps 0.7, two point sources per call as the
-    benchmark runs them (spin-colour 0 and 11), FP16-storage inner solves, 16
-    log-spaced masses 0.5 * 0.04^(i/15): every mass at 1e-10, checked by the
-    oracle at sampled sites, and the solutions against the oracle's stored
-    ones."""
+def test_48c96_fp16_inner_three_sources_sixteen_masses(api, outer):
+    """48^3x96 (10.6M sites), eps 0.7, three point sources per call in the
+    benchmark's solver configuration (spin-colour 0, 5 and 11; FP16-storage
+    inner solves refined in FP32 segments, 4 iterations per captured graph,
+    the Lagrange guess through the last 8 masses), 16 log-spaced masses
+    0.5 * 0.04^(i/15): every mass at 1e-10, checked by the oracle at sampled
+    sites, and the solutions against the oracle's stored ones."""
     dims = (48, 48, 48, 96)
     U = synth.gauge_field(dims, 0.7, seed=5)
-    ks = [0, 11]
+    ks = [0, 5, 11]
     bs = [synth.point_source(dims, k // 3, k % 3) for k in ks]
     lat = api.Lattice(dims)
-    g = api.Gauge(lat, _cuda(U), precs=(outer, "f16"))
-    xs, st = api.multimass_solve(g, [_cuda(b) for b in bs], MASSES16, api.params(inner_prec="f16", outer_prec=outer))
+    g = api.Gauge(lat, _cuda(U), precs=(outer, "f32", "f16"))
+    prm = api.params(inner_prec="f16", outer_prec=outer, inner_refine=1, graph_iters=4, guess_max=8)
+    xs, st = api.multimass_solve(g, [_cuda(b) for b in bs], MASSES16, prm)
     chk = SampledResidual(dims, U)
     for r, b in enumerate(bs):
         for i, m in enumerate(MASSES16):

@@ -572,3 +572,32 @@ def test_grid_stride_outer_hops_and_concurrent_handles(api):
                 assert st[r][i]["status"] == api.WL_OK and st[r][i]["true_relres"] <= 1e-10
                 assert rel(xs[r][i].cpu().numpy(), ref[k][r][i].cpu().numpy()) < 1e-14, (k, r, i)
                 assert O.true_relres(U, dims, bs[2 * k + r].cpu().numpy(), xs[r][i].cpu().numpy(), m) <= 1.02e-10
+
+
+def test_fp32_refined_fp16_inner_solve(api):
+    """FP16 inner solves run as FP16 segments with the inner residual
+    recomputed in FP32 between them (inner_refine): every mass still reaches
+    the 1e-10 true residual and the oracle's solution, with no more outer
+    (FP64) checks than one FP16 solve per outer step takes; without FP32
+    links on the handle the option is refused."""
+    dims = (8, 8, 8, 16)
+    U, lat, g = _gauge(api, dims, 0.5, 91, precs=("f64", "f32", "f16"))
+    bs = [synth.point_source(dims, 0, 2), synth.z2_source(dims, 92)]
+    masses = [0.4, 0.2, 0.1, 0.05]
+    res = {}
+    for rf in (0, 1):
+        res[rf] = api.multimass_solve(g, [_cuda(b) for b in bs], masses,
+                                      api.params(inner_prec="f16", inner_refine=rf))
+    refs = [O.multimass_solve(U, dims, b, masses, tol=1e-12)[0] for b in bs]
+    for r, b in enumerate(bs):
+        for i, m in enumerate(masses):
+            st0, st1 = res[0][1][r][i], res[1][1][r][i]
+            assert st1["status"] == api.WL_OK and st1["true_relres"] <= 1e-10, st1
+            assert st1["restarts"] <= st0["restarts"], (r, m, st0, st1)
+            x = res[1][0][r][i].cpu().numpy()
+            assert rel(x, refs[r][i]) < 1e-8, (r, m)
+            assert O.true_relres(U, dims, b, x, m) <= 1.02e-10
+    g16 = api.Gauge(lat, _cuda(U), precs=("f64", "f16"))
+    with pytest.raises(api.WilsonError) as e:
+        api.multimass_solve(g16, [_cuda(bs[0])], masses, api.params(inner_prec="f16", inner_refine=1))
+    assert e.value.status == api.WL_ERR_ARG
