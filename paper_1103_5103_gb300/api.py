@@ -391,9 +391,9 @@ def launch_count() -> int:
     return n.value
 
 
-HOP_VARIANTS = {"f32": [101, 105, 106, 108, 201, 204, 205, 401, 404, 301, 304, 305, 1104, 1106, 1202, 1203, 9001, 9002,
-                        9004, 9102, 9104],
-                "f16": [101, 105, 106, 108, 110, 201, 204, 206, 401, 404, 9001, 9002, 9004, 9102, 9104],
+HOP_VARIANTS = {"f32": [101, 105, 106, 108, 201, 204, 205, 401, 404, 301, 304, 305, 1104, 1106, 1202, 1203, 5006, 9001,
+                        9002, 9004, 9102, 9104],
+                "f16": [101, 105, 106, 108, 110, 201, 204, 206, 401, 404, 5006, 9001, 9002, 9004, 9102, 9104],
                 "f64": [101, 103, 201, 7101, 7102, 7201, 7202], "df": [101, 103, 104, 105, 106]}
 
 

@@ -562,7 +562,8 @@ template <> struct LinkIO<WL_F64> {
 template <> struct LinkIO<WL_F32> {
     using R = float;
     static constexpr int chunks = 3;
-    static __device__ __forceinline__ void load(const void *dirbase, int stride, int i, cx<R> (&u)[9])
+    // rows 0 and 1 only (u[0..5])
+    static __device__ __forceinline__ void load_rows(const void *dirbase, int stride, int i, cx<R> (&u)[9])
     {
         i = WL_LOAD_IDX(i, stride, 3);
         const float4 *p = static_cast<const float4 *>(dirbase);
@@ -572,13 +573,17 @@ template <> struct LinkIO<WL_F32> {
             u[2 * k] = {t.x, t.y};
             u[2 * k + 1] = {t.z, t.w};
         }
+    }
+    static __device__ __forceinline__ void load(const void *dirbase, int stride, int i, cx<R> (&u)[9])
+    {
+        load_rows(dirbase, stride, i, u);
         reconstruct_row2(u);
     }
 };
 template <> struct LinkIO<WL_F16> {
     using R = float;
     static constexpr int chunks = 3;
-    static __device__ __forceinline__ void load(const void *dirbase, int stride, int i, cx<R> (&u)[9])
+    static __device__ __forceinline__ void load_rows(const void *dirbase, int stride, int i, cx<R> (&u)[9])
     {
         i = WL_LOAD_IDX(i, stride, 3);
         const uint2 *p = static_cast<const uint2 *>(dirbase);
@@ -589,6 +594,10 @@ template <> struct LinkIO<WL_F16> {
             u[2 * k] = {a.x, a.y};
             u[2 * k + 1] = {b.x, b.y};
         }
+    }
+    static __device__ __forceinline__ void load(const void *dirbase, int stride, int i, cx<R> (&u)[9])
+    {
+        load_rows(dirbase, stride, i, u);
         reconstruct_row2(u);
     }
 };

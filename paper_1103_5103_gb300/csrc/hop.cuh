@@ -108,15 +108,15 @@ __device__ __forceinline__ bool rhs_done(const HopArgs &a, int r)
     return a.skip != nullptr && __ldcg(a.skip + (size_t)r * a.skip_stride) != 0;
 }
 
-// Accumulate the eight transporters of site i for NB right-hand sides.
-template <int P, bool DAG, int NB, int MU, bool CG = false>
-__device__ __forceinline__ void hop_dir(const HopArgs &a, int i, const Coord &c, int rowbase, int r0,
-                                        cx<typename PrecTraits<P>::R> (&acc)[NB][12])
+// Forward and backward neighbours of site i (coordinates c, first site of
+// its x row rowbase) in direction MU, and the antiperiodic sign flips of the
+// two hops.
+template <int MU>
+__device__ __forceinline__ void neighbours(const Geom &g, int i, const Coord &c, int rowbase, int &fwd, int &bwd,
+                                           bool &sf, bool &sb)
 {
-    using R = typename PrecTraits<P>::R;
-    const Geom &g = a.g;
-    int fwd, bwd;
-    bool sf = false, sb = false;  // antiperiodic sign flips
+    sf = false;
+    sb = false;
     if constexpr (MU == 0) {
         const int xf = c.x + 1 == g.X ? 0 : c.x + 1;
         const int xb = c.x == 0 ? g.X - 1 : c.x - 1;
@@ -139,6 +139,18 @@ __device__ __forceinline__ void hop_dir(const HopArgs &a, int i, const Coord &c,
             sb = firstt;
         }
     }
+}
+
+// Accumulate the eight transporters of site i for NB right-hand sides.
+template <int P, bool DAG, int NB, int MU, bool CG = false>
+__device__ __forceinline__ void hop_dir(const HopArgs &a, int i, const Coord &c, int rowbase, int r0,
+                                        cx<typename PrecTraits<P>::R> (&acc)[NB][12])
+{
+    using R = typename PrecTraits<P>::R;
+    const Geom &g = a.g;
+    int fwd, bwd;
+    bool sf, sb;  // antiperiodic sign flips
+    neighbours<MU>(g, i, c, rowbase, fwd, bwd, sf, sb);
     const size_t dir_off = (size_t)MU * link_dir_bytes(P, g.stride);
     cx<R> u[9];
     // forward: U_mu(n) psi_{n+mu} (1 - gamma_mu)   [dagger: (1 + gamma_mu)]
@@ -730,6 +742,220 @@ __global__ void __launch_bounds__(128, MINB) k_hop_gs(HopArgs a, EpiStore epi)
         hop_accumulate<P, DAG, NB>(a, i, r0, acc);
         epi.template operator()<P, NB>(a, i, true, r0, acc);
     }
+}
+
+// ------------------------------------------------ paired-site variant
+// Two output sites per thread, i and i + 64 of a 128-site tile (64-thread
+// blocks, one rhs per block), with every FP32 operation of the stencil done
+// on the pair at once by the packed sm_100+ instructions (__ffma2_rn,
+// __fadd2_rn, __fmul2_rn: one issue slot for two lanes of arithmetic).
+// Direction and projector phases are uniform over the pair; links,
+// neighbours, FP16 norms and time-boundary signs are per site, so no operand
+// is a broadcast.  Element .x of every float2 belongs to site a, .y to b.
+struct pcx {
+    float2 re, im;
+};
+
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+// b - a, exact as a single rounding: fma(-1, a, b)
+__device__ __forceinline__ float2 psub(float2 b, float2 a) { return __ffma2_rn(make_float2(-1.f, -1.f), a, b); }
+__device__ __forceinline__ float2 pneg(float2 a) { return __fmul2_rn(make_float2(-1.f, -1.f), a); }
+
+__device__ __forceinline__ pcx pair_of(cx<float> a, cx<float> b) { return {make_float2(a.re, b.re), make_float2(a.im, b.im)}; }
+
+// b + z * phase C (phase codes as in uphase)
+template <int C>
+__device__ __forceinline__ pcx padd_phase(pcx z, pcx b)
+{
+    if constexpr (C == 0) return {padd(b.re, z.re), padd(b.im, z.im)};
+    else if constexpr (C == 1) return {psub(b.re, z.im), padd(b.im, z.re)};   // i z = (-z.im, z.re)
+    else if constexpr (C == 2) return {psub(b.re, z.re), psub(b.im, z.im)};
+    else return {padd(b.re, z.im), psub(b.im, z.re)};                          // -i z = (z.im, -z.re)
+}
+
+// acc + s * phase_C(w) with the scale pair s and its negation ns
+template <int C>
+__device__ __forceinline__ pcx pexpand(float2 s, float2 ns, pcx w, pcx acc)
+{
+    if constexpr (C == 0) return {pfma(s, w.re, acc.re), pfma(s, w.im, acc.im)};
+    else if constexpr (C == 1) return {pfma(ns, w.im, acc.re), pfma(s, w.re, acc.im)};
+    else if constexpr (C == 2) return {pfma(ns, w.re, acc.re), pfma(ns, w.im, acc.im)};
+    else return {pfma(s, w.im, acc.re), pfma(ns, w.re, acc.im)};
+}
+
+// Row 2 of a pair of SU(3) links from rows 0 and 1: u[6+c] = conj(r0 x r1)_c.
+__device__ __forceinline__ void reconstruct_row2_pair(pcx (&u)[9])
+{
+    pcx n[3];   // negated row 0
+#pragma unroll
+    for (int c = 0; c < 3; ++c) n[c] = {pneg(u[c].re), pneg(u[c].im)};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
+        // a = u[c1] u[3+c2] - u[c2] u[3+c1];  row 2 = (a.re, -a.im)
+        const pcx p = u[c1], q = u[3 + c2], r = u[c2], t = u[3 + c1];
+        const pcx np = n[c1], nr = n[c2];
+        const float2 re = pfma(p.re, q.re, pfma(np.im, q.im, pfma(nr.re, t.re, pmul(r.im, t.im))));
+        const float2 im = pfma(np.re, q.im, pfma(np.im, q.re, pfma(r.re, t.im, pmul(r.im, t.re))));
+        u[6 + c] = {re, im};
+    }
+}
+
+// acc += s psi (1 -/+ gamma_MU) L for the pair, as transport() per site.
+template <int MU, int PLUS, bool ADJ>
+__device__ __forceinline__ void transport_pair(pcx (&acc)[12], const pcx (&psi)[12], const pcx (&u)[9], float2 s)
+{
+    constexpr int A1 = Proj<MU>::a1, A2 = Proj<MU>::a2;
+    constexpr int C1 = (Proj<MU>::c1 + 2 * PLUS) & 3, C2 = (Proj<MU>::c2 + 2 * PLUS) & 3;
+    constexpr int C1c = (4 - C1) & 3, C2c = (4 - C2) & 3;
+    pcx h1[3], h2[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        h1[c] = padd_phase<C1c>(psi[3 * A1 + c], psi[9 + c]);
+        h2[c] = padd_phase<C2c>(psi[3 * A2 + c], psi[6 + c]);
+    }
+    // u h:        re = sum u.re h.re - u.im h.im,  im = sum u.re h.im + u.im h.re
+    // u^dag h:    re = sum u.re h.re + u.im h.im,  im = sum u.re h.im - u.im h.re
+    float2 n1[3], n2[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        n1[b] = pneg(ADJ ? h1[b].re : h1[b].im);
+        n2[b] = pneg(ADJ ? h2[b].re : h2[b].im);
+    }
+    const float2 mz = make_float2(-0.f, -0.f);
+    pcx w1[3], w2[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        pcx s1 = {mz, mz}, s2 = {mz, mz};
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const pcx ub = ADJ ? u[3 * b + a] : u[3 * a + b];
+            if constexpr (!ADJ) {
+                s1 = {pfma(ub.re, h1[b].re, pfma(ub.im, n1[b], s1.re)), pfma(ub.re, h1[b].im, pfma(ub.im, h1[b].re, s1.im))};
+                s2 = {pfma(ub.re, h2[b].re, pfma(ub.im, n2[b], s2.re)), pfma(ub.re, h2[b].im, pfma(ub.im, h2[b].re, s2.im))};
+            } else {
+                s1 = {pfma(ub.re, h1[b].re, pfma(ub.im, h1[b].im, s1.re)), pfma(ub.re, h1[b].im, pfma(ub.im, n1[b], s1.im))};
+                s2 = {pfma(ub.re, h2[b].re, pfma(ub.im, h2[b].im, s2.re)), pfma(ub.re, h2[b].im, pfma(ub.im, n2[b], s2.im))};
+            }
+        }
+        w1[a] = s1;
+        w2[a] = s2;
+    }
+    const float2 ns = pneg(s);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        acc[3 * A1 + c] = pexpand<C1>(s, ns, w1[c], acc[3 * A1 + c]);
+        acc[9 + c] = pexpand<0>(s, ns, w1[c], acc[9 + c]);
+        acc[3 * A2 + c] = pexpand<C2>(s, ns, w2[c], acc[3 * A2 + c]);
+        acc[6 + c] = pexpand<0>(s, ns, w2[c], acc[6 + c]);
+    }
+}
+
+// Site and neighbour data of one site of a pair.
+struct PairSite {
+    int i, rowbase;
+    Coord c;
+};
+
+template <int P, bool DAG, int MU>
+__device__ __forceinline__ void hop_dir_pair(const HopArgs &a, const PairSite &sa, const PairSite &sb, pcx (&acc)[12])
+{
+    using R = float;
+    const Geom &g = a.g;
+    int fa, ba, fb, bb;
+    bool sfa, sba, sfb, sbb;
+    neighbours<MU>(g, sa.i, sa.c, sa.rowbase, fa, ba, sfa, sba);
+    neighbours<MU>(g, sb.i, sb.c, sb.rowbase, fb, bb, sfb, sbb);
+    const size_t dir_off = (size_t)MU * link_dir_bytes(P, g.stride);
+    const char *lo = static_cast<const char *>(a.links_out) + dir_off;
+    const char *li = static_cast<const char *>(a.links_in) + dir_off;
+    {
+        cx<R> ua[9], ub[9], pa[12], pb[12];
+        LinkIO<P>::load_rows(lo, g.stride, sa.i, ua);
+        LinkIO<P>::load_rows(lo, g.stride, sb.i, ub);
+        const R na = SpinorIO<P>::load_unscaled(a.in, g.stride, fa, pa);
+        const R nb = SpinorIO<P>::load_unscaled(a.in, g.stride, fb, pb);
+        pcx u[9], psi[12];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) u[k] = pair_of(ua[k], ub[k]);
+        reconstruct_row2_pair(u);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) psi[k] = pair_of(pa[k], pb[k]);
+        transport_pair<MU, DAG ? 1 : 0, false>(acc, psi, u, make_float2(sfa ? -na : na, sfb ? -nb : nb));
+    }
+    {
+        cx<R> ua[9], ub[9], pa[12], pb[12];
+        LinkIO<P>::load_rows(li, g.stride, ba, ua);
+        LinkIO<P>::load_rows(li, g.stride, bb, ub);
+        const R na = SpinorIO<P>::load_unscaled(a.in, g.stride, ba, pa);
+        const R nb = SpinorIO<P>::load_unscaled(a.in, g.stride, bb, pb);
+        pcx u[9], psi[12];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) u[k] = pair_of(ua[k], ub[k]);
+        reconstruct_row2_pair(u);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) psi[k] = pair_of(pa[k], pb[k]);
+        transport_pair<MU, DAG ? 0 : 1, true>(acc, psi, u, make_float2(sba ? -na : na, sbb ? -nb : nb));
+    }
+}
+
+// D applied at sites ia and ib of one rhs (a.in already offset to it);
+// the results in A (site a) and B (site b).
+template <int P, bool DAG>
+__device__ __forceinline__ void hop_accumulate_pair(const HopArgs &a, int ia, int ib, cx<float> (&A)[1][12],
+                                                    cx<float> (&B)[1][12])
+{
+    PairSite sa, sb;
+    sa.i = ia;
+    sa.c = site_coord(a.g, ia, a.out_parity);
+    sa.rowbase = ia - (sa.c.x >> 1);
+    sb.i = ib;
+    sb.c = site_coord(a.g, ib, a.out_parity);
+    sb.rowbase = ib - (sb.c.x >> 1);
+    const float2 mz = make_float2(-0.f, -0.f);
+    pcx acc[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = {mz, mz};
+    hop_dir_pair<P, DAG, 0>(a, sa, sb, acc);
+    hop_dir_pair<P, DAG, 1>(a, sa, sb, acc);
+    hop_dir_pair<P, DAG, 2>(a, sa, sb, acc);
+    hop_dir_pair<P, DAG, 3>(a, sa, sb, acc);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        A[0][k] = {acc[k].re.x, acc[k].im.x};
+        B[0][k] = {acc[k].re.y, acc[k].im.y};
+    }
+}
+
+constexpr int kPairThreads = 64;   // threads per block; 2 x 64 = 128 sites per tile
+
+template <int P, bool DAG, int MINB>
+__global__ void __launch_bounds__(kPairThreads, MINB) k_hop_pair(HopArgs a, EpiStore epi)
+{
+    const int r = blockIdx.x % a.ngroups;
+    const int sb = blockIdx.x / a.ngroups;
+    if (rhs_done(a, r)) return;
+    const int ia = sb * (2 * kPairThreads) + threadIdx.x;
+    if (ia >= a.g.Vh) return;
+    const int ib = ia + kPairThreads;
+    const bool has_b = ib < a.g.Vh;
+    HopArgs b = a;
+    b.in = static_cast<const char *>(a.in) + (size_t)r * a.rhs_bytes;
+    cx<float> A[1][12], B[1][12];
+    // past the end the second lane repeats site a and is not stored
+    hop_accumulate_pair<P, DAG>(b, ia, has_b ? ib : ia, A, B);
+    epi.template operator()<P, 1>(a, ia, true, r, A);
+    if (has_b) epi.template operator()<P, 1>(a, ib, true, r, B);
+}
+
+template <int P, bool DAG, int MINB>
+void launch_k_hop_pair(HopArgs a, const EpiStore &e, cudaStream_t s)
+{
+    a.ngroups = a.nrhs;
+    const int nsb = (a.g.Vh + 2 * kPairThreads - 1) / (2 * kPairThreads);
+    k_hop_pair<P, DAG, MINB><<<nsb * a.nrhs, kPairThreads, 0, s>>>(a, e);
 }
 
 int sm_count();

@@ -1,7 +1,9 @@
 // Hop kernel instantiations for F16 (one translation unit per precision so the
 // library builds in parallel).  Variant v = 100 * (rhs per thread) + (minimum resident
-// blocks per SM requested from the register allocator); 9000 + 100 b + R is the
-// TMA-staged hop with R rhs per tile and register budget b (hop_tma.cu).
+// blocks per SM requested from the register allocator); 5006 is the paired-site hop
+// (two sites per thread in packed FP32 arithmetic, 64-thread blocks, six resident per
+// SM: 168 registers; a tighter budget spills); 9000 + 100 b + R is the TMA-staged hop with R rhs per tile and
+// register budget b (hop_tma.cu).
 #include "hop.cuh"
 
 namespace wl {
@@ -24,6 +26,7 @@ int hop_launch_prec<WL_F16>(int v, int dagger, const HopArgs &a, const EpiStore 
         }
     } else {
         switch (v) {
+        case 5006: launch_k_hop_pair<WL_F16, false, 6>(a, e, s); break;
         case 101: launch_k_hop<WL_F16, false, 1, 1>(a, e, s); break;
         case 105: launch_k_hop<WL_F16, false, 1, 5>(a, e, s); break;
         case 106: launch_k_hop<WL_F16, false, 1, 6>(a, e, s); break;

@@ -238,9 +238,12 @@ def test_hop_multi_rhs(api, prec, rhs_block, nrhs):
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32", "f16", "df"])
-def test_every_hop_variant_and_autotune(api, prec):
-    """Every autotuner variant computes the same hop; wl_autotune picks one of them."""
-    dims = (8, 4, 4, 8)
+@pytest.mark.parametrize("dims", [(8, 4, 4, 8), (6, 4, 2, 10)])
+def test_every_hop_variant_and_autotune(api, prec, dims):
+    """Every autotuner variant computes the same hop; wl_autotune picks one of
+    them.  On 6x4x2x10 (120 sites per parity) the paired-site variants end on
+    a half-filled pair tile, and the TMA variants, which need X/2 a multiple
+    of 4, refuse the lattice."""
     U, lat, g = _setup(api, dims, "random")
     nrhs = 5
     odd = O.parity_mask(dims)
@@ -251,6 +254,11 @@ def test_every_hop_variant_and_autotune(api, prec):
         lat.spinor_import(_cuda(srcs[r]), a[r * stride:(r + 1) * stride], prec, 0)
     for v in api.HOP_VARIANTS[prec]:
         b = torch.zeros_like(a)
+        if v >= 9000 and (dims[0] // 2) % 4:
+            with pytest.raises(api.WilsonError) as e:
+                api.hop_batch(g, a, b, nrhs, stride, 1.0, prec, 1, -v)
+            assert e.value.status == api.WL_ERR_ARG
+            continue
         api.hop_batch(g, a, b, nrhs, stride, 1.0, prec, 1, -v)
         for r in range(nrhs):
             out = torch.zeros((lat.volume, 4, 3), dtype=torch.complex128, device="cuda")
