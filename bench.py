@@ -79,10 +79,13 @@ FLOP_SITE = 1320   # per hop output site and rhs
 # lattice sites of the captured case, bytes).  Traffic scales with sites.
 # An entry is valid only for the kernel as it was when captured; remove it
 # when that kernel changes.
-HOP_TRAFFIC = {("f16", 106, 2): (1048576, 406.04e6), ("f64", 103, 2): (442368, 850.72e6)}
+HOP_TRAFFIC = {("f16", 106, 3): (1048576, 515.86e6), ("f64", 101, 3): (442368, 1013.01e6),
+               ("f64", 103, 3): (442368, 1024.87e6)}
+# FP64 pipe utilisation of the FP64 hop in the same captures
+FP64_PIPE = {(101, 3): "92.6% busy in an ncu capture of this variant on 24^3x64, 3 rhs",
+             (103, 3): "92.6% busy in an ncu capture of this variant on 24^3x64, 3 rhs"}
 # FP64 FMA rate of one GB300 (TFLOP/s, 2 flops per FMA): 152 SMs x 2 FP64
-# FMA per clock x 2.07 GHz, the unit count and clock of the part; a probe
-# kernel of independent FMA chains measured 1.26 TFLOP/s
+# FMA per clock x 2.07 GHz, the unit count and clock of the part
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 GOLDEN = os.path.join(ROOT, "tests", "golden")
 
@@ -351,12 +354,12 @@ def roofline_entries(prof, inner, outer, V, peak, peak_kind, nb, hop_variant, ou
                 otraffic = bytes_cap * (V // 2) / sites_cap
             out["outer"] = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                             "frac": tf / FP64_PEAK_TFLOPS, "traffic": otraffic,
-                            "fp64_pipe": "92.5% busy in an ncu capture of this variant on 24^3x64, 2 rhs",
+                            "fp64_pipe": FP64_PIPE.get((outer_variant, nb)),
                             "kernel": f"k_hop<f64> (D_oe x, first hop of each outer FP64 residual check), "
                                       f"variant {outer_variant}, {site_rhs / (po['sites'] / po['launches']):.2f} "
                                       f"rhs per launch on average",
                             "peak_kind": "FP64 FMA rate from the unit count and clock (152 SMs x 2 FMA/clk "
-                                         "x 2.07 GHz; a probe measured 1.26)",
+                                         "x 2.07 GHz)",
                             "flops_per_site": FLOP_SITE, "avg_launch_us": avg * 1e6,
                             "timed_launches": po["launches"]}
         else:
