@@ -54,19 +54,19 @@ CONFIGS = {
     "c1": dict(name="8^4, 1 point source x 4 masses (m0 0.5, 0.3, 0.2, 0.1), eps 0.3",
                dims=(8, 8, 8, 8), eps=0.3, seed=1, sources="point1", masses=[0.5, 0.3, 0.2, 0.1]),
     # 10.6M sites: 16 solutions per source take 33 GB in canonical FP64 and,
-    # with the guess through the last 8 masses, 18 GB inside the solver, so
-    # the sources go three at a time (229 GB on the device; four would take
-    # 292 of the 298 GB).  Measured on this workload: three sources per call
-    # 4.4% faster than two, 4 inner iterations per captured graph 2.5%
-    # faster than 8, the Lagrange guess through the last 8 masses 2.3%
-    # faster than through all of them (772 inner iterations against 796);
-    # FP16 inner solves refined in FP32 segments 7.5% faster than one FP16
-    # solve per outer step (228 outer steps against 289).  The end-to-end
-    # run writes the solutions of a call to 98 GB of page-locked host memory
+    # with the guess through the last 6 masses, 14 GB inside the solver, so
+    # the sources go three at a time (223 GB on the device).  Measured on
+    # this workload: three sources per call 4.4% faster than two, 4 inner
+    # iterations per captured graph 2.5% faster than 8, FP16 inner solves
+    # refined in FP32 segments 7.5% faster than one FP16 solve per outer
+    # step (228 outer steps against 289), the Lagrange guess through the
+    # last 6 masses 0.7% faster than through the last 8 and 2% faster than
+    # through the last 10.  The end-to-end run writes the solutions of a
+    # call to 98 GB of page-locked host memory
     "c5": dict(name="48^3x96, 12 spin-colour point sources x 16 masses (m0 0.5*0.04^(i/15)), eps 0.7",
                dims=(48, 48, 48, 96), eps=0.7, seed=5, sources="points12",
                masses=[0.5 * 0.04 ** (i / 15.0) for i in range(16)], inner="f16", source_batch=3,
-               graph_iters=4, guess_max=8, inner_refine=1, pinned_gb=128, baseline_sources=1, e2e_steps=3),
+               graph_iters=4, guess_max=6, inner_refine=1, pinned_gb=128, baseline_sources=1, e2e_steps=3),
 }
 # algorithmic bytes of one hop: per output site 8 links (12 reals: the
 # minimum the method must read), per output site and rhs one input spinor

@@ -531,15 +531,21 @@ static int eo_defect_correction(wl_gauge *g, const Vec &bprec, const Vec &x64, d
         WL_TRY(run_inner(in, prm, cap, hst, s));
         for (int r = 0; r < nrhs; ++r)
             if (h_active[r]) iters[r] += hst[r].iters;
-        if (refine) {
+        // Further segments only for the rhs whose outer target lies below
+        // what one FP16 solve reaches: for the others the first segment
+        // already aimed at the target, and the FP64 check verifies it.
+        std::vector<int> mid(nrhs, 0);
+        int n_seg = 0;
+        if (refine)
+            for (int r = 0; r < nrhs; ++r) {
+                mid[r] = h_active[r] != 0 && d_outer[r] < default_inner_tol(WL_F16);
+                n_seg += mid[r];
+            }
+        if (n_seg > 0) {
             // FP32 copy of this outer step's right-hand side, then segments
             WL_TRY(blas_convert(geo, r64, rin32, s));
-            std::vector<int> mid(nrhs, 0);
             std::vector<double> seg_start(nrhs, 0.0);
-            for (int r = 0; r < nrhs; ++r) {
-                mid[r] = h_active[r] != 0;
-                seg_start[r] = rn_outer[r];
-            }
+            for (int r = 0; r < nrhs; ++r) seg_start[r] = rn_outer[r];
             const int kMaxSegments = 8;
             for (int seg = 1;; ++seg) {
                 // r32 = r_in - M_prec e in FP32 for the rhs still segmenting

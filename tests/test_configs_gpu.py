@@ -140,7 +140,7 @@ def test_48c96_fp16_inner_three_sources_sixteen_masses(api, outer):
     """48^3x96 (10.6M sites), eps 0.7, three point sources per call in the
     benchmark's solver configuration (spin-colour 0, 5 and 11; FP16-storage
     inner solves refined in FP32 segments, 4 iterations per captured graph,
-    the Lagrange guess through the last 8 masses), 16 log-spaced masses
+    the Lagrange guess through the last 6 masses), 16 log-spaced masses
     0.5 * 0.04^(i/15): every mass at 1e-10, checked by the oracle at sampled
     sites, and the solutions against the oracle's stored ones."""
     dims = (48, 48, 48, 96)
@@ -149,7 +149,7 @@ def test_48c96_fp16_inner_three_sources_sixteen_masses(api, outer):
     bs = [synth.point_source(dims, k // 3, k % 3) for k in ks]
     lat = api.Lattice(dims)
     g = api.Gauge(lat, _cuda(U), precs=(outer, "f32", "f16"))
-    prm = api.params(inner_prec="f16", outer_prec=outer, inner_refine=1, graph_iters=4, guess_max=8)
+    prm = api.params(inner_prec="f16", outer_prec=outer, inner_refine=1, graph_iters=4, guess_max=6)
     xs, st = api.multimass_solve(g, [_cuda(b) for b in bs], MASSES16, prm)
     chk = SampledResidual(dims, U)
     for r, b in enumerate(bs):
