@@ -56,13 +56,14 @@ CONFIGS = {
     # 10.6M sites: 16 solutions per source take 33 GB in canonical FP64 and,
     # with the guess through the last 6 masses, 14 GB inside the solver, so
     # the sources go three at a time (223 GB on the device).  Measured on
-    # this workload: three sources per call 4.4% faster than two, 4 inner
-    # iterations per captured graph 2.5% faster than 8, FP16 inner solves
-    # refined in FP32 segments 7.5% faster than one FP16 solve per outer
-    # step (228 outer steps against 289), the Lagrange guess through the
-    # last 6 masses 0.7% faster than through the last 8 and 2% faster than
-    # through the last 10.  The end-to-end run writes the solutions of a
-    # call to 98 GB of page-locked host memory
+    # this workload, FP64 outer loop: three sources per call 4.4% faster
+    # than two, 4 inner iterations per captured graph 2.5% faster than 8,
+    # the Lagrange guess through the last 6 masses 0.7% faster than through
+    # the last 8 and 2% faster than through the last 10; FP16 inner solves
+    # refined in FP32 segments to 1e-7 take 216 outer steps per step
+    # against 289 for one FP16 solve per outer step (7.29 s against 8.29 s
+    # with the guess through 8 masses).  The end-to-end run writes the
+    # solutions of a call to 98 GB of page-locked host memory
     "c5": dict(name="48^3x96, 12 spin-colour point sources x 16 masses (m0 0.5*0.04^(i/15)), eps 0.7",
                dims=(48, 48, 48, 96), eps=0.7, seed=5, sources="points12",
                masses=[0.5 * 0.04 ** (i / 15.0) for i in range(16)], inner="f16", source_batch=3,
@@ -651,7 +652,7 @@ def run_ours(args, cfg):
                                        "double-float (about 48-bit) residual, accumulator and reconstruction",
                    "inner_tol": args.inner_tol or "library default", "mode": args.mode,
                    "graph_iters": graph_iters,
-                   "inner_refine": ("FP16 segments, inner residual recomputed in FP32 between them, to 1e-6 "
+                   "inner_refine": ("FP16 segments, inner residual recomputed in FP32 between them, to 1e-7 "
                                     "per outer step") if refine else None,
                    "guess_max": guess_max or "all earlier masses",
                    "outer_loop": "reliable updates" if args.reliable else "restarted defect correction",

@@ -155,7 +155,7 @@ typedef struct {
     int    inner_refine; /* FP16 BiCGstab inner solves without reliable updates: 1
                             runs each outer step's inner solve as FP16 segments with
                             the inner residual recomputed in FP32 between them, so
-                            that one outer step reaches inner_tol (default 1e-6) of
+                            that one outer step reaches inner_tol (default 1e-7) of
                             its residual instead of the FP16 limit near 3e-4 and the
                             solve needs fewer outer (FP64) residual checks; the
                             handle then needs FP32 links (else WL_ERR_ARG).  Other

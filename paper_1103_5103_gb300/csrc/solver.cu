@@ -408,8 +408,10 @@ static int eo_defect_correction(wl_gauge *g, const Vec &bprec, const Vec &x64, d
     // first iterations leaves the true residual; so one outer step runs FP16
     // segments, recomputes the inner residual r_in - M e in FP32 between them
     // (e is the FP32 accumulator, kept across segments) and stops at
-    // refine_tol (1e-6 by default) of the outer residual.  The FP64 check that
-    // follows then gains about 1e-6 instead of 3e-4.
+    // refine_tol (1e-7 by default, near what an FP32 recomputation and an
+    // FP32 accumulator allow; segments that stop halving the residual end
+    // earlier) of the outer residual.  The FP64 check that follows then
+    // gains 1e-6 to 1e-7 instead of 3e-4.
     const bool refine = prm.inner_refine && prec == WL_F16 && !prm.reliable &&
                         prm.inner_solver == WL_SOLVER_BICGSTAB && (g->prec_mask & WL_F32);
     Vec rin32, r32, tmp32;
@@ -431,7 +433,7 @@ static int eo_defect_correction(wl_gauge *g, const Vec &bprec, const Vec &x64, d
         h_mode = reinterpret_cast<int *>(h_mdelta2 + nrhs);
         h_skip = h_mode + nrhs;
     }
-    const double refine_tol = prm.inner_tol > 0 ? prm.inner_tol : 1e-6;
+    const double refine_tol = prm.inner_tol > 0 ? prm.inner_tol : 1e-7;
     std::vector<double> d_outer(nrhs, 0.0), rn_outer(nrhs, 0.0);
     // live timing of the first residual hop of every check (wl_profile_enable)
     struct Ev {
@@ -665,11 +667,13 @@ struct AsyncExport {
     // 16 blocks against 8.76 s with 152; the device-memory export needs the
     // full grid).
     int blocks = 0;
+    int full_blocks = 0;   // the SM count: the last mass's export runs alone
     int init()
     {
         int dev = 0;
         WL_CUDA_TRY(cudaGetDevice(&dev));
         WL_CUDA_TRY(cudaDeviceGetAttribute(&blocks, cudaDevAttrMultiProcessorCount, dev));
+        full_blocks = blocks;
         int lo = 0, hi = 0;
         WL_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
         WL_CUDA_TRY(cudaStreamCreateWithPriority(&stream, cudaStreamNonBlocking, hi));
@@ -1143,6 +1147,8 @@ extern "C" int multimass_solve(wl_gauge *g, const void *const *b, void *const *x
             WL_TRY(blas_guess_residual(geo, sc.coef, sc.coef + 32 * n_rhs, ins.data(), kk, sol[k], r0, s, ssm));
         }
         for (int r = 0; r < n_rhs; ++r) std::memset(&st[r], 0, sizeof(wl_solver_stats));
+        // nothing overlaps the last mass's export: give it the whole GPU
+        if (axp && k == n_mass - 1) ax.blocks = ax.full_blocks;
         WL_TRY(solve_one_mass(g, be, bo, bprec, sol[k], m, *p, bn2, x + im, n_mass, st, s, &ys[k], true, axp));
         if (p->guess == WL_GUESS_SSM && k + 1 < n_mass) {
             // the Gram products read the canonical solutions: wait for their export
