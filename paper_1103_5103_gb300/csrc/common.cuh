@@ -250,7 +250,7 @@ __host__ __device__ constexpr int spinor_site_bytes(int prec)
 }
 __host__ __device__ constexpr int link_site_bytes(int prec)
 {
-    return prec == WL_F64 ? 144 : prec == WL_F32 ? 48 : prec == WL_DF ? 144 : 24;
+    return prec == WL_F64 ? 144 : prec == WL_F32 ? 48 : prec == WL_DF ? 144 : 36;
 }
 
 // Start value of every hop accumulator: -0.0.  x + (-0.0) == x exactly for
@@ -523,8 +523,10 @@ template <> struct SpinorIO<WL_DF> {
 };
 
 // Links: per parity, per direction (k = 3*row + col):
-//   F32: float4 [4][3][stride];  F16: uint2 [4][3][stride]  (rows 0-1, 6 complex;
-//        row 2 is rebuilt as conj(row0 x row1))
+//   F32: float4 [4][3][stride]  (rows 0-1, 6 complex; row 2 is rebuilt as
+//        conj(row0 x row1))
+//   F16: per direction uint2 [4][stride] (entries 0-7 as half2 pairs) then
+//        uint [stride] (entry 8): all three rows, 36 bytes per site
 //   F64: double2 [4][9][stride]  (all three rows)
 //   DF:  float4 [4][9][stride] (re.hi, re.lo, im.hi, im.lo), all three rows
 template <int P> struct LinkIO;
@@ -580,9 +582,13 @@ template <> struct LinkIO<WL_F32> {
         reconstruct_row2(u);
     }
 };
+// FP16 links keep row 2 as well (12 bytes more per link): the FP16 hop is
+// bound by instruction issue and the FMA pipe, where rebuilding row 2 costs
+// about a fifth of its FMA work, and not by memory.
 template <> struct LinkIO<WL_F16> {
     using R = float;
     static constexpr int chunks = 3;
+    // rows 0 and 1 only (u[0..5])
     static __device__ __forceinline__ void load_rows(const void *dirbase, int stride, int i, cx<R> (&u)[9])
     {
         i = WL_LOAD_IDX(i, stride, 3);
@@ -598,7 +604,13 @@ template <> struct LinkIO<WL_F16> {
     static __device__ __forceinline__ void load(const void *dirbase, int stride, int i, cx<R> (&u)[9])
     {
         load_rows(dirbase, stride, i, u);
-        reconstruct_row2(u);
+        i = WL_LOAD_IDX(i, stride, 3);
+        const uint2 t = __ldg(static_cast<const uint2 *>(dirbase) + (size_t)3 * stride + i);
+        const unsigned w = __ldg(reinterpret_cast<const unsigned *>(static_cast<const uint2 *>(dirbase) + (size_t)4 * stride) + i);
+        const float2 a = unpack_half2(t.x), b = unpack_half2(t.y), c = unpack_half2(w);
+        u[6] = {a.x, a.y};
+        u[7] = {b.x, b.y};
+        u[8] = {c.x, c.y};
     }
 };
 

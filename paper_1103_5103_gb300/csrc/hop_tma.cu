@@ -23,7 +23,8 @@
 // Views of the internal layouts as tensors (innermost first, 4-byte words):
 //   spinor  (4 Xh, Y, Z*T, chunk, rhs)   chunk = 16 bytes of one site
 //   norms   (Xh, Y, Z*T, rhs)            FP16 only
-//   links   (w Xh, Y, Z*T, 12)           12 = 4 directions x 3 chunks, w = 4 (FP32) or 2 (FP16)
+//   links   (w Xh, Y, Z*T, 3, 4)         the 3 chunks of rows 0-1 of each of 4 directions,
+//                                         w = 4 (FP32) or 2 (FP16); row 2 is rebuilt
 // Every box starts at x = 0 and spans whole rows, so each copy starts on a
 // 16-byte boundary.
 //
@@ -105,9 +106,9 @@ struct TmaMaps {
     CUtensorMap sp_row1;  // input spinors, box (4 Xh, 1, 1, C, R)
     CUtensorMap nm_rows;  // FP16 norms, box (Xh, TY, 1, R)
     CUtensorMap nm_row1;  // FP16 norms, box (Xh, 1, 1, R)
-    CUtensorMap lk_out;   // output-parity links, box (w Xh, TY, 1, 12)
-    CUtensorMap lk_in;    // input-parity links, box (w Xh, TY, 1, 3)
-    CUtensorMap lk_in1;   // input-parity links, box (w Xh, 1, 1, 3)
+    CUtensorMap lk_out;   // output-parity links, box (w Xh, TY, 1, 3, 4)
+    CUtensorMap lk_in;    // input-parity links, box (w Xh, TY, 1, 3, 1)
+    CUtensorMap lk_in1;   // input-parity links, box (w Xh, 1, 1, 3, 1)
 };
 
 // Byte offsets of the regions of one stage.
@@ -212,12 +213,12 @@ __device__ __forceinline__ void issue_tile(const TmaMaps &m, const TmaLayout &L,
     const int tm = z + g.Z * (t == 0 ? g.T - 1 : t - 1);
     const int r0 = c.grp * R;
     mbar_expect_tx(bar, L.tx_bytes);
-    tma_load_4d(smem_addr(st + L.lo), &m.lk_out, bar, 0, c.y0, c.zt, 0);
-    tma_load_4d(smem_addr(st + L.li0), &m.lk_in, bar, 0, c.y0, c.zt, 0);
-    tma_load_4d(smem_addr(st + L.li1a), &m.lk_in1, bar, 0, ym, c.zt, 3);
-    tma_load_4d(smem_addr(st + L.li1b), &m.lk_in, bar, 0, c.y0, c.zt, 3);
-    tma_load_4d(smem_addr(st + L.li2), &m.lk_in, bar, 0, c.y0, zm, 6);
-    tma_load_4d(smem_addr(st + L.li3), &m.lk_in, bar, 0, c.y0, tm, 9);
+    tma_load_5d(smem_addr(st + L.lo), &m.lk_out, bar, 0, c.y0, c.zt, 0, 0);
+    tma_load_5d(smem_addr(st + L.li0), &m.lk_in, bar, 0, c.y0, c.zt, 0, 0);
+    tma_load_5d(smem_addr(st + L.li1a), &m.lk_in1, bar, 0, ym, c.zt, 0, 1);
+    tma_load_5d(smem_addr(st + L.li1b), &m.lk_in, bar, 0, c.y0, c.zt, 0, 1);
+    tma_load_5d(smem_addr(st + L.li2), &m.lk_in, bar, 0, c.y0, zm, 0, 2);
+    tma_load_5d(smem_addr(st + L.li3), &m.lk_in, bar, 0, c.y0, tm, 0, 3);
     tma_load_5d(smem_addr(st + L.spc), &m.sp_rows, bar, 0, c.y0, c.zt, 0, r0);
     tma_load_5d(smem_addr(st + L.spm), &m.sp_row1, bar, 0, ym, c.zt, 0, r0);
     tma_load_5d(smem_addr(st + L.spp), &m.sp_row1, bar, 0, yp, c.zt, 0, r0);
@@ -438,15 +439,16 @@ int launch(const HopArgs &a, const EpiStore &e, cudaStream_t s)
         WL_TRY(encode(&m.nm_rows, nb, 4, dims, str, b1));
         WL_TRY(encode(&m.nm_row1, nb, 4, dims, str, b2));
     }
-    {   // links (w Xh, Y, Z T, 12 = direction x chunk)
-        const cuuint64_t dims[4] = {(cuuint64_t)IO::W * g.Xh, (cuuint64_t)g.Y, zt, 12};
-        const cuuint64_t str[3] = {(cuuint64_t)link_row, (cuuint64_t)link_row * g.Y, (cuuint64_t)g.stride * IO::CB};
-        const cuuint32_t bo[4] = {(cuuint32_t)IO::W * g.Xh, (cuuint32_t)L.TY, 1, 12};
-        const cuuint32_t bi[4] = {(cuuint32_t)IO::W * g.Xh, (cuuint32_t)L.TY, 1, 3};
-        const cuuint32_t b1[4] = {(cuuint32_t)IO::W * g.Xh, 1, 1, 3};
-        WL_TRY(encode(&m.lk_out, a.links_out, 4, dims, str, bo));
-        WL_TRY(encode(&m.lk_in, a.links_in, 4, dims, str, bi));
-        WL_TRY(encode(&m.lk_in1, a.links_in, 4, dims, str, b1));
+    {   // links (w Xh, Y, Z T, chunk of rows 0-1, direction)
+        const cuuint64_t dims[5] = {(cuuint64_t)IO::W * g.Xh, (cuuint64_t)g.Y, zt, 3, 4};
+        const cuuint64_t str[4] = {(cuuint64_t)link_row, (cuuint64_t)link_row * g.Y, (cuuint64_t)g.stride * IO::CB,
+                                   (cuuint64_t)link_dir_bytes(P, g.stride)};
+        const cuuint32_t bo[5] = {(cuuint32_t)IO::W * g.Xh, (cuuint32_t)L.TY, 1, 3, 4};
+        const cuuint32_t bi[5] = {(cuuint32_t)IO::W * g.Xh, (cuuint32_t)L.TY, 1, 3, 1};
+        const cuuint32_t b1[5] = {(cuuint32_t)IO::W * g.Xh, 1, 1, 3, 1};
+        WL_TRY(encode(&m.lk_out, a.links_out, 5, dims, str, bo));
+        WL_TRY(encode(&m.lk_in, a.links_in, 5, dims, str, bi));
+        WL_TRY(encode(&m.lk_in1, a.links_in, 5, dims, str, b1));
     }
     auto kern = k_hop_tma<P, DAG, R, NREG>;
     static int attr = 0;   // the dynamic shared memory opt-in, raised as needed

@@ -225,8 +225,8 @@ __global__ void __launch_bounds__(kFullSites) k_import_full(Geom g, const double
     }
 }
 
-// Pack U_mu at the sites of one parity: rows 0 and 1 for F32 and F16, all
-// three rows for F64 (as given) and DF (row 2 formed in FP64).
+// Pack U_mu at the sites of one parity: rows 0 and 1 for F32, all three
+// rows for F64 and F16 (as given) and DF (row 2 formed in FP64).
 template <int P>
 __global__ void k_pack_links(Geom g, const double2 *__restrict__ U, void *out, int parity)
 {
@@ -265,13 +265,14 @@ __global__ void k_pack_links(Geom g, const double2 *__restrict__ U, void *out, i
         }
     } else {
         uint2 *p = reinterpret_cast<uint2 *>(dir);
-        for (int k = 0; k < 3; ++k) {
+        for (int k = 0; k < 4; ++k) {
             double2 a = u[2 * k], b = u[2 * k + 1];
             uint2 t;
             t.x = pack_half2((float)a.x, (float)a.y);
             t.y = pack_half2((float)b.x, (float)b.y);
             p[(size_t)k * g.stride + i] = t;
         }
+        reinterpret_cast<unsigned *>(p + (size_t)4 * g.stride)[i] = pack_half2((float)u[8].x, (float)u[8].y);
     }
 }
 
