@@ -92,7 +92,8 @@ def test_reference_other_ranks_print_nothing(monkeypatch, capsys):
 
 def test_reference_without_iteration_count_is_unavailable():
     """The 16^3x32 workload has no recorded step iteration count: the arm
-    prints its unavailable line and exits 0 (run as the driver runs it)."""
+    prints its unavailable line and exits 0 (run as a separate process,
+    the way the command line launches it)."""
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--config", "c2"],
                        capture_output=True, text=True, timeout=600, cwd=ROOT)
     assert r.returncode == 0, r.stderr
