@@ -157,10 +157,11 @@ typedef struct {
                             the inner residual recomputed in FP32 between them, so
                             that one outer step reaches inner_tol (default 1e-7) of
                             its residual instead of the FP16 limit near 3e-4 and the
-                            solve needs fewer outer (FP64) residual checks; the
-                            handle then needs FP32 links (else WL_ERR_ARG).  Other
-                            inner solves ignore it.  0 (default): one FP16 solve
-                            per outer step.                                          */
+                            solve needs fewer outer (FP64) residual checks.  An outer
+                            step whose target lies above the FP16 limit runs one
+                            segment, unchecked in FP32.  The handle then needs FP32
+                            links (else WL_ERR_ARG).  Other inner solves ignore it.
+                            0 (default): one FP16 solve per outer step.              */
 } wl_solver_params;
 
 typedef struct {
