@@ -652,8 +652,8 @@ def run_ours(args, cfg):
                                        "double-float (about 48-bit) residual, accumulator and reconstruction",
                    "inner_tol": args.inner_tol or "library default", "mode": args.mode,
                    "graph_iters": graph_iters,
-                   "inner_refine": ("FP16 segments, inner residual recomputed in FP32 between them, to 1e-7 "
-                                    "per outer step") if refine else None,
+                   "inner_refine": ("FP16 segments, inner residual recomputed in FP32 between them, to "
+                                    f"{args.inner_tol or 1e-7:g} of each outer residual") if refine else None,
                    "guess_max": guess_max or "all earlier masses",
                    "outer_loop": "reliable updates" if args.reliable else "restarted defect correction",
                    "inner_solver": "CG on the normal equations" if args.inner_solver == "cg" else "BiCGstab",
