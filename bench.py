@@ -80,8 +80,8 @@ FLOP_SITE = 1320   # per hop output site and rhs
 # lattice sites of the captured case, bytes).  Traffic scales with sites.
 # An entry is valid only for the kernel as it was when captured; remove it
 # when that kernel changes.
-HOP_TRAFFIC = {("f16", 106, 3): (1048576, 617.32e6), ("f64", 101, 3): (442368, 1013.01e6),
-               ("f64", 103, 3): (442368, 1024.87e6)}
+HOP_TRAFFIC = {("f16", 105, 3): (1048576, 617.48e6), ("f16", 106, 3): (1048576, 617.32e6),
+               ("f64", 101, 3): (442368, 1013.01e6), ("f64", 103, 3): (442368, 1024.87e6)}
 # FP64 pipe utilisation of the FP64 hop in the same captures
 FP64_PIPE = {(101, 3): "92.6% busy in an ncu capture of this variant on 24^3x64, 3 rhs",
              (103, 3): "92.6% busy in an ncu capture of this variant on 24^3x64, 3 rhs"}

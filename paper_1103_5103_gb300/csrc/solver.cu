@@ -1096,7 +1096,9 @@ extern "C" int multimass_solve(wl_gauge *g, const void *const *b, void *const *x
             host = cudaPointerGetAttributes(&pa, x[k]) == cudaSuccess && pa.type == cudaMemoryTypeHost;
         }
         cudaGetLastError();
-        if (host) ax.blocks = std::max(1, (ax.blocks + 9) / 10);
+        // (double-float solutions are converted to FP64 on the way out, which
+        // loads the FP64 pipe: their export keeps the full grid)
+        if (host && PO == WL_F64) ax.blocks = std::max(1, (ax.blocks + 9) / 10);
     }
     int worst = WL_OK;
     for (int k = 0; k < n_mass; ++k) {
