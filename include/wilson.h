@@ -39,9 +39,9 @@
  *    internal.  Site parity = (x+y+z+t) mod 2; site 0 is even.
  *  - Precisions: WL_F64, WL_F32, WL_F16 (FP16 storage with one FP32 norm
  *    per site, arithmetic in FP32) and WL_DF (double-float, see below).
- *    FP32 and FP16 links are stored as their first two rows (12 reals) and
- *    the third row is rebuilt as conj(row0 x row1), which is exact for SU(3)
- *    links; FP64 links keep all three rows as given and double-float links
+ *    FP32 links are stored as their first two rows (12 reals) and the third
+ *    row is rebuilt as conj(row0 x row1), which is exact for SU(3) links;
+ *    FP64 and FP16 links keep all three rows as given and double-float links
  *    all three rows with row 2 formed in FP64 when the handle is created.
  */
 #ifndef WILSON_H
@@ -209,10 +209,11 @@ int wl_spinor_export(const wl_lattice *lat, const void *internal, void *canon_c1
                      int parity, void *stream);
 
 /* Pack canonical complex128 links (device, [4][V][3][3]) into the internal
- * per-parity layouts (Section 4, Eq. 8; FP32 and FP16 compressed to two
- * rows, FP64 and double-float with all three) for every precision set in
+ * per-parity layouts (Section 4, Eq. 8; FP32 compressed to two rows, FP64,
+ * FP16 and double-float with all three) for every precision set in
  * prec_mask (WL_F64 | WL_F32 | WL_F16 | WL_DF).  The links must be SU(3):
- * the 12-real formats rebuild the third row from the first two.  Links whose U U^dag - 1 or det U - 1 has an entry (real or
+ * the FP32 format and the TMA-staged FP16 hop rebuild the third row from
+ * the first two.  Links whose U U^dag - 1 or det U - 1 has an entry (real or
  * imaginary part) above 1e-6 in magnitude, or a NaN, are rejected with
  * WL_ERR_ARG.  The gauge handle keeps a reference to lat, which must
  * outlive it.  Synchronises the stream before returning. */
