@@ -742,6 +742,21 @@ def run_ours(args, cfg):
                                           f"BiCGstab iteration ({t_iter:.2f} s: two M_prec and the vector "
                                           f"updates) on {threads} host threads, {spent:.1f} s in all; scaled by "
                                           f"{src} plus the per-mass operator applications"}
+        if threads > 1:
+            # the same estimate on one thread: one application of M_prec
+            # timed there; an iteration's two applications take that time,
+            # its vector updates (not threaded in the oracle) the time above
+            from oracle import oracle as O
+            O.set_threads(1)
+            t1 = oracle_sample(cfg, U, bs_h[0], iteration=False)[0]
+            O.set_threads(threads)
+            t_iter1 = t_iter + 2.0 * (t1 - t_mprec)
+            v1 = (oracle_workload_seconds(counts, nr, t1, t_iter1) if counts is not None
+                  else iters * t_iter1 + nr * nm * 4.5 * t1)
+            line["cpu_baseline"]["single_thread"] = {
+                "value": v1, "unit": UNIT, "cores": 1, "mprec_s": t1,
+                "sample": f"one M_prec application on one thread ({t1:.2f} s); a BiCGstab iteration "
+                          f"{t_iter1:.2f} s; the workload scaled as above"}
     if rank == 0:
         print(json.dumps(line))
 
