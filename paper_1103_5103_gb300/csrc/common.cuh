@@ -681,27 +681,29 @@ __device__ __forceinline__ float warp_sum(float v)
 }
 
 // Block-wide sum of NV FP32 values per thread, result in FP64 (valid in
-// thread 0): FP32 inside each warp, FP64 across the warps.  The per-thread
-// values are FP32 partials over one site, so 32 of them summed in FP32 stay
-// in the same accuracy class, and GB300 runs FP64 adds at 1/57 of the FP32
-// rate: a warp sum of doubles costs each thread five of them per value.
+// thread 0): FP32 inside the block, converted once (blocks then combine in
+// FP64).  The per-thread values are FP32 partials over one site, so the
+// block's few hundred of them summed in FP32 stay in the same accuracy
+// class, and GB300 runs FP64 arithmetic at 1/57 of the FP32 rate: a warp
+// sum of doubles costs each thread five FP64 adds per value, and with them
+// the FP64 pipe of the reduction-fused hops was 15% busy.
 template <int NV>
 __device__ __forceinline__ void block_sum(float (&vf)[NV], double (&v)[NV])
 {
-    __shared__ double sh[32][NV];
+    __shared__ float sh[32][NV];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int k = 0; k < NV; ++k) vf[k] = warp_sum(vf[k]);
     __syncthreads();
     if (lane == 0)
 #pragma unroll
-        for (int k = 0; k < NV; ++k) sh[warp][k] = (double)vf[k];
+        for (int k = 0; k < NV; ++k) sh[warp][k] = vf[k];
     __syncthreads();
     if (warp == 0) {
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
-            double t = lane < nw ? sh[lane][k] : 0.0;
-            v[k] = warp_sum(t);
+            const float t = lane < nw ? sh[lane][k] : 0.f;
+            v[k] = (double)warp_sum(t);
         }
     }
     __syncthreads();
